@@ -1,0 +1,162 @@
+"""Oracle: plain, slow, FP64 CPU reference for the periodic N-body sum.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` leg of ``bench.py`` may import or run anything here.  The
+CUDA library never calls it and shares no code with it.
+
+What it computes (Sec. 2.2, Eq. (pfmmDef)):
+
+    q_t = sum_s sum_{p in P} K(x_t, y_s + p) phi_s,
+
+with the (s, p) term whose source image coincides with x_t excluded, for the
+Laplace kernel 1/r and the Stokes velocity kernel
+(1/8pi)(I/r + r r^T/r^3) of Eq. (kexamples).  P is the lattice of periodic
+vectors of the cubic box [0,L)^3 along the periodic axes.  The sums over P
+are made absolutely convergent with the conventions that fix the result
+(Sec. 2.2 compatibility conditions; Sec. 3.4 for Stokes TP):
+
+* free space: plain double loop;
+* Laplace TP: Ewald, k = 0 removed (requires neutral charges);
+* Stokes TP: Hasimoto split, k = 0 removed (zero mean flow; a net force is
+  allowed);
+* Laplace SP: direct symmetric image sum with an Euler-Maclaurin tail
+  (requires neutral charges).
+
+Functions with no closed-form or brute-force pin say so in their docstring
+("parity unpinned").
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+LAPLACE = 0
+STOKES = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle/ewald.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    src = os.path.join(_HERE, "ewald.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-o", tmp, src, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            d, l, i, P = ctypes.c_double, ctypes.c_long, ctypes.c_int, ctypes.c_void_p
+            lib.orc_free.argtypes = [i, l, P, P, l, P, P]
+            lib.orc_laplace_tp.argtypes = [l, P, P, l, P, d, d, d, i, d, P]
+            lib.orc_stokes_tp.argtypes = [l, P, P, l, P, d, d, d, i, d, P]
+            lib.orc_laplace_sp.argtypes = [l, P, P, l, P, i, d, l, P]
+            _lib = lib
+    return _lib
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def kdim(kernel: int) -> int:
+    return 1 if kernel == LAPLACE else 3
+
+
+def free_space(kernel: int, src, dens, trg) -> np.ndarray:
+    """Free-space direct sum sum_s K(x_t, y_s) phi_s (coincident pairs skipped)."""
+    y, x = _c(src), _c(trg)
+    phi = _c(dens).reshape(len(y), kdim(kernel))
+    out = np.zeros((len(x), kdim(kernel)))
+    _load().orc_free(kernel, len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), _ptr(out))
+    return out[:, 0] if kernel == LAPLACE else out
+
+
+def ewald_params(xi: float | None = None, rc: float | None = None, tol_exp: float = 6.2):
+    """Splitting parameter and cutoffs for ~1e-15 relative truncation error.
+
+    Real space: xi*rc = 6.2 (erfc(6.2) ~ 5e-19); Fourier: kc = 2*6.5*xi.
+    """
+    if xi is None and rc is None:
+        rc = 1.0
+    if xi is None:
+        xi = tol_exp / rc
+    if rc is None:
+        rc = tol_exp / xi
+    kc = 13.0 * xi
+    mmax = int(np.ceil(kc / (2 * np.pi)))
+    return xi, rc, mmax, kc
+
+
+def laplace_tp(src, q, trg, L: float = 1.0, xi=None, rc=None) -> np.ndarray:
+    """Laplace, triply periodic, Ewald (k = 0 removed) at targets trg."""
+    xi, rc, mmax, kc = ewald_params(xi, rc)
+    y, x, phi = _c(src), _c(trg), _c(q)
+    out = np.zeros(len(x))
+    _load().orc_laplace_tp(len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), L, xi, rc, mmax, kc, _ptr(out))
+    return out
+
+
+def stokes_tp(src, f, trg, L: float = 1.0, xi=None, rc=None) -> np.ndarray:
+    """Stokes velocity, triply periodic, Hasimoto Ewald (zero mean flow)."""
+    xi, rc, mmax, kc = ewald_params(xi, rc)
+    y, x, phi = _c(src), _c(trg), _c(f).reshape(-1, 3)
+    out = np.zeros((len(x), 3))
+    _load().orc_stokes_tp(len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), L, xi, rc, mmax, kc, _ptr(out))
+    return out
+
+
+def laplace_sp(src, q, trg, axis: int = 0, L: float = 1.0, M: int = 200) -> np.ndarray:
+    """Laplace, singly periodic along ``axis``: image sum |n|<=M + Euler-Maclaurin tail."""
+    y, x, phi = _c(src), _c(trg), _c(q)
+    out = np.zeros(len(x))
+    _load().orc_laplace_sp(len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), axis, L, M, _ptr(out))
+    return out
+
+
+def periodic_sum(kernel: int, periodic_axes: int, src, dens, trg, L: float = 1.0) -> np.ndarray:
+    """Dispatch on (kernel, periodicity bitmask: bit0=x, bit1=y, bit2=z).
+
+    Returns [T] for Laplace and [T][3] for Stokes, in the coordinates given
+    (box [0,L)^3).
+    """
+    if periodic_axes == 0:
+        return free_space(kernel, src, dens, trg)
+    if periodic_axes == 7:
+        return laplace_tp(src, dens, trg, L) if kernel == LAPLACE else stokes_tp(src, dens, trg, L)
+    if kernel == LAPLACE and periodic_axes in (1, 2, 4):
+        return laplace_sp(src, dens, trg, axis={1: 0, 2: 1, 4: 2}[periodic_axes], L=L)
+    raise NotImplementedError(f"oracle: kernel {kernel} periodicity {periodic_axes}")
+
+
+def error_metrics(u, ref) -> dict:
+    """Sec. 3.3 error measures, per velocity component: max abs, mean abs, RMS, relative L2."""
+    d = (np.asarray(u) - np.asarray(ref)).ravel()
+    r = np.asarray(ref).ravel()
+    return {
+        "max_abs": float(np.max(np.abs(d))) if d.size else 0.0,
+        "mean_abs": float(np.mean(np.abs(d))) if d.size else 0.0,
+        "rms": float(np.sqrt(np.mean(d * d))) if d.size else 0.0,
+        "rel_l2": float(np.linalg.norm(d) / np.linalg.norm(r)) if d.size else 0.0,
+    }
