@@ -1,0 +1,171 @@
+/*
+ * pkifmm — periodic kernel-independent FMM on one GB300 (sm_103a).
+ *
+ * C ABI of the evaluation path of "Flexibly imposing periodicity in kernel
+ * independent FMM: a Multipole-To-Local operator approach" (Yan & Shelley).
+ *
+ * The problem (Sec. 2.2, Eq. (pfmmDef)): given S sources y_s with densities
+ * phi_s and T targets x_t in the cubic box B0 = [lo, lo+L)^3, evaluate
+ *     q_t = sum_s sum_{p in P} K(x_t, y_s + p) phi_s
+ * where P is the lattice of periodic vectors along the periodic axes and K is
+ * the Laplace kernel 1/r (k = 1) or the Stokes velocity kernel
+ * (1/8pi)(I/r + r r^T/r^3) (k = 3, viscosity 1) of Eq. (kexamples).  The
+ * source image that coincides with a target (the p = 0, s = t term) is
+ * excluded.  The sum is split (Eq. (pfmmSplit)) into a near field over B0 and
+ * its adjacent images, evaluated by KIFMM on one octree of B0, and a far
+ * field carried by one precomputed operator applied to the root's upward
+ * equivalent density (Algorithm 2, Stage 2 c), folded into the downward pass
+ * (the L2L option of Sec. 4).
+ *
+ * Conventions that make the periodic sum unique (Sec. 2.2 Eq.
+ * (compatcondition), Sec. 3.3, Sec. 3.4):
+ *   Laplace, any periodicity: charges must be neutral;
+ *   Stokes SP/DP: net force must be zero;
+ *   Stokes TP: a net force is allowed, zero mean flow (Hasimoto, k = 0 removed).
+ *   Laplace TP: k = 0 removed (zero mean potential).
+ *
+ * Memory: every array argument of pkifmm_evaluate is a DEVICE pointer owned
+ * by the caller, contiguous, binary64.  pkifmm_evaluate_host takes HOST
+ * pointers instead and copies inside the call.  The library owns its
+ * operators (allocated by pkifmm_plan_create) and its workspace (grown on
+ * demand by evaluate, freed by pkifmm_plan_destroy).
+ *
+ * Threading: a plan may be used by one host thread at a time.
+ * Errors: every int-returning call returns PKIFMM_OK (0) or a negative code;
+ * pkifmm_strerror gives a message.  A failed evaluate leaves pot undefined
+ * and the plan usable.
+ */
+#ifndef PKIFMM_H
+#define PKIFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pkifmm_plan_s *pkifmm_plan;
+
+/* Kernels, Eq. (kexamples): source/target dimension k = 1 and 3 (Sec. 2.3). */
+enum { PKIFMM_LAPLACE = 0, PKIFMM_STOKES = 1 };
+
+/* Arithmetic of the evaluation:
+ * FP64  — every stage in binary64 (accuracy reference path);
+ * MIXED — kernel sums (P2P, S2M, L2T, W, X) in binary32 on leaf-local
+ *         coordinates with compensated accumulation; M2L on the tensor cores
+ *         as split-bf16 (three products) accumulated in binary32; the other
+ *         translations in binary32; the root periodic operator and its
+ *         check-to-equivalent solve in binary64. */
+enum { PKIFMM_FP64 = 0, PKIFMM_MIXED = 1 };
+
+enum {
+    PKIFMM_OK = 0,
+    PKIFMM_ERR_INVALID_ARG = -1,  /* bad argument (sizes, NULL, NaN coordinate) */
+    PKIFMM_ERR_OUT_OF_BOX = -2,   /* a point outside [lo, lo+L) along a free axis */
+    PKIFMM_ERR_NOT_NEUTRAL = -3,  /* compatibility condition violated */
+    PKIFMM_ERR_CUDA = -4,         /* a CUDA runtime call failed */
+    PKIFMM_ERR_OOM = -5,          /* device or host allocation failed */
+    PKIFMM_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
+    PKIFMM_ERR_CACHE = -7,        /* operator cache unreadable / unwritable */
+    PKIFMM_ERR_UNSUPPORTED = -8   /* combination not built (e.g. DP kernel) */
+};
+
+/* Build a plan: Algorithm 2, Stage 1 (precompute), Sec. 2.2-2.3.
+ *   kernel         PKIFMM_LAPLACE or PKIFMM_STOKES
+ *   periodic_axes  bit 0 = x, bit 1 = y, bit 2 = z; 0 = free space.
+ *                  Built: 0 (any kernel), 7 (TP, both kernels),
+ *                  one axis (SP, Laplace).  Others return UNSUPPORTED.
+ *   box_lo, box_len  B0 = [box_lo, box_lo + box_len)^3 (host pointer, 3 doubles)
+ *   p              points per edge of the equivalent/check surfaces (Sec. 2.2,
+ *                  n = 6(p-1)^2 + 2), 4 <= p <= 16
+ *   ell            near-field layers of images (Eq. (pfmmSplit)), >= 1
+ *   leaf_max       s: a box splits while it holds more than s sources or
+ *                  more than s targets (Sec. 2.2 notation)
+ *   depth_max      deepest octree level, 1..16
+ *   precision      PKIFMM_FP64 or PKIFMM_MIXED
+ *   nrhs           density vectors evaluated together on one geometry (>= 1)
+ *   cache_dir      directory for the operator cache (NULL: no cache)
+ * Runs on the host (SVD, Ewald sums; seconds) and uploads the operators to
+ * the current CUDA device.  On success *out owns them. */
+int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes,
+                       const double box_lo[3], double box_len, int p, int ell,
+                       int leaf_max, int depth_max, int precision, int nrhs,
+                       const char *cache_dir);
+
+/* Evaluate potentials (Algorithm 2, Stage 2) on `cuda_stream` (a
+ * cudaStream_t, NULL = legacy default stream).  Device pointers:
+ *   src_xyz [S][3]            source positions
+ *   dens    [nrhs][S][k]      source densities phi
+ *   trg_xyz [T][3]            target positions (may equal src_xyz)
+ *   pot     [nrhs][T][k]      output potentials q, overwritten
+ * Positions along periodic axes may lie anywhere (they are wrapped); along
+ * free axes they must lie in [lo, lo+L).  S, T >= 0 (S = 0 or T = 0 gives
+ * zeros).  The call synchronises with the stream a few times while it sizes
+ * the octree; it returns after enqueuing the last kernel. */
+int pkifmm_evaluate(pkifmm_plan plan, int64_t S, const double *src_xyz,
+                    const double *dens, int64_t T, const double *trg_xyz,
+                    double *pot, void *cuda_stream);
+
+/* Same as pkifmm_evaluate with HOST arrays: copies inputs to the device,
+ * evaluates, copies pot back and synchronises the stream before returning. */
+int pkifmm_evaluate_host(pkifmm_plan plan, int64_t S, const double *src_xyz,
+                         const double *dens, int64_t T, const double *trg_xyz,
+                         double *pot, void *cuda_stream);
+
+/* Per-stage device times (ms) of the last evaluate, in this order:
+ * 0 keys+sort, 1 tree+lists, 2 upward (S2M, M2M), 3 root periodic operator,
+ * 4 M2L (V list), 5 X list + downward (C2E, L2L), 6 leaves (L2T, W, P2P),
+ * 7 total.  Writes min(max, 8) values; returns that count (or an error). */
+int pkifmm_last_stage_times(pkifmm_plan plan, double *ms, int max);
+
+/* Counts describing the octree of the last evaluate:
+ * 0 boxes, 1 leaves, 2 depth, 3 |U| entries, 4 |V| entries, 5 |W|, 6 |X|,
+ * 7 source-target pairs of the U list.  Writes min(max, 8) values. */
+int pkifmm_tree_stats(pkifmm_plan plan, int64_t *out, int max);
+
+/* Copy the octree and interaction lists of the last evaluate to host arrays
+ * (for verification).  Boxes are numbered level by level, Morton order within
+ * a level (octant bits x = 1, y = 2, z = 4).  Any pointer may be NULL.
+ *   level[nbox], pos[nbox][3] (integer position at its level), parent[nbox]
+ *   (-1 for the root), src_range[nbox][2], trg_range[nbox][2] (into the
+ *   sorted order), src_perm[S] / trg_perm[T] (sorted -> input index).
+ * Lists (name 'U','V','W','X'): list_ptr[nbox+1] CSR offsets, list_box[n]
+ * source box, list_shift[n][3] periodic image in {-1,0,1}.  pkifmm_list_export
+ * returns n (>= 0, the entry count; call with NULL arrays to size them) or a
+ * negative error. */
+int pkifmm_tree_export(pkifmm_plan plan, int32_t *level, int32_t *pos, int32_t *parent,
+                       int64_t *src_range, int64_t *trg_range, int64_t *src_perm,
+                       int64_t *trg_perm);
+int pkifmm_list_export(pkifmm_plan plan, char name, int64_t *list_ptr, int32_t *list_box,
+                       int8_t *list_shift);
+
+/* Singular values (descending) of the check-to-equivalent matrix
+ * A_ij = K(x_i^{B0,d}, y_j^{B0,d}) of Sec. 2.3 / Table 1: check points on a
+ * cube of edge 1.05, equivalent points on a cube of edge 2.95, p points per
+ * edge.  Host-only (no GPU); s_out has k*(6(p-1)^2+2) entries. */
+int pkifmm_surface_singular_values(int kernel, int p, double *s_out);
+
+/* Max |A x - b| of the backward-stable solve x = V (S^+ (U^T b)) of Sec. 3.1
+ * and Appendix B for b = 1 (all ones), A as above.  Host-only. */
+int pkifmm_backward_error(int kernel, int p, double *err_out);
+
+/* Root far-field operator (host-only, row-major [kn][kn], unit box):
+ * M = K^{P,F}_ell(x^{B0,d}, y^{B0,u}) + sum_{1 < |p|_inf <= ell} K(x^{B0,d}, y^{B0,u} + p)
+ * i.e. the right-hand side of Eq. (M2Lsolve) with the images of layers
+ * 2..ell folded in, so it maps the root's upward equivalent density to the
+ * far-field check potential on the root's downward check surface (edge
+ * 1.05).  K^{P,F} = K^P - sum_{|p|<=ell} K(., . + p) (Sec. 2.2).  Same
+ * periodicities as pkifmm_plan_create (non-zero). */
+int pkifmm_root_operator(int kernel, unsigned periodic_axes, int p, int ell, double *m_out);
+
+void pkifmm_plan_destroy(pkifmm_plan plan);
+const char *pkifmm_strerror(int code);
+
+/* Detail message of the last failed call on this host thread (library-owned
+ * string, valid until the next failing call on the thread). */
+const char *pkifmm_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PKIFMM_H */

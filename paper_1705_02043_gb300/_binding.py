@@ -1,0 +1,214 @@
+"""ctypes binding of the C ABI (include/pkifmm.h).  Argument marshalling only:
+every step of the evaluation runs in the CUDA library."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+ERR = {-1: "INVALID_ARG", -2: "OUT_OF_BOX", -3: "NOT_NEUTRAL", -4: "CUDA", -5: "OOM",
+       -6: "TIMEOUT", -7: "CACHE", -8: "UNSUPPORTED"}
+
+
+class PKIFMMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pkifmm error {code} ({ERR.get(code, '?')}): {msg}")
+        self.code = code
+        self.name = ERR.get(code, "?")
+
+
+def load_library():
+    """Load _build/libpkifmm.so (building it if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("pkifmm CUDA library missing: " + path)
+            lib = ctypes.CDLL(path)
+            P, i, u, d, i64, c = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double,
+                                  ctypes.c_int64, ctypes.c_char)
+            lib.pkifmm_plan_create.argtypes = [ctypes.POINTER(P), i, u, P, d, i, i, i, i, i, i, ctypes.c_char_p]
+            lib.pkifmm_evaluate.argtypes = [P, i64, P, P, i64, P, P, P]
+            lib.pkifmm_evaluate_host.argtypes = [P, i64, P, P, i64, P, P, P]
+            lib.pkifmm_last_stage_times.argtypes = [P, P, i]
+            lib.pkifmm_tree_stats.argtypes = [P, P, i]
+            lib.pkifmm_tree_export.argtypes = [P, P, P, P, P, P, P, P]
+            lib.pkifmm_list_export.argtypes = [P, c, P, P, P]
+            lib.pkifmm_surface_singular_values.argtypes = [i, i, P]
+            lib.pkifmm_backward_error.argtypes = [i, i, P]
+            lib.pkifmm_root_operator.argtypes = [i, u, i, i, P]
+            lib.pkifmm_plan_destroy.argtypes = [P]
+            lib.pkifmm_plan_destroy.restype = None
+            lib.pkifmm_strerror.argtypes = [i]
+            lib.pkifmm_strerror.restype = ctypes.c_char_p
+            lib.pkifmm_last_error_message.argtypes = []
+            lib.pkifmm_last_error_message.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc < 0:
+        lib = load_library()
+        raise PKIFMMError(rc, lib.pkifmm_last_error_message().decode())
+    return rc
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())  # torch tensor
+
+
+# ---- C-ABI functions, same names ----
+
+def pkifmm_plan_create(kernel, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max,
+                       precision, nrhs, cache_dir=None):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64)
+    _check(lib.pkifmm_plan_create(ctypes.byref(h), kernel, periodic_axes, _ptr(lo), float(box_len), p, ell,
+                                  leaf_max, depth_max, precision, nrhs,
+                                  cache_dir.encode() if cache_dir else None))
+    return h
+
+
+def pkifmm_evaluate(plan, S, src, dens, T, trg, pot, stream=None):
+    return _check(load_library().pkifmm_evaluate(plan, S, _ptr(src), _ptr(dens), T, _ptr(trg), _ptr(pot),
+                                                 stream))
+
+
+def pkifmm_evaluate_host(plan, S, src, dens, T, trg, pot, stream=None):
+    return _check(load_library().pkifmm_evaluate_host(plan, S, _ptr(src), _ptr(dens), T, _ptr(trg), _ptr(pot),
+                                                      stream))
+
+
+def pkifmm_last_stage_times(plan):
+    out = np.zeros(8)
+    _check(load_library().pkifmm_last_stage_times(plan, _ptr(out), 8))
+    return out
+
+
+def pkifmm_tree_stats(plan):
+    out = np.zeros(8, dtype=np.int64)
+    _check(load_library().pkifmm_tree_stats(plan, _ptr(out), 8))
+    return out
+
+
+def pkifmm_tree_export(plan, S, T):
+    nbox = int(pkifmm_tree_stats(plan)[0])
+    level = np.zeros(nbox, np.int32)
+    pos = np.zeros((nbox, 3), np.int32)
+    parent = np.zeros(nbox, np.int32)
+    sr = np.zeros((nbox, 2), np.int64)
+    tr = np.zeros((nbox, 2), np.int64)
+    sp = np.zeros(S, np.int64)
+    tp = np.zeros(T, np.int64)
+    _check(load_library().pkifmm_tree_export(plan, _ptr(level), _ptr(pos), _ptr(parent), _ptr(sr), _ptr(tr),
+                                             _ptr(sp), _ptr(tp)))
+    return dict(level=level, pos=pos, parent=parent, src_range=sr, trg_range=tr, src_perm=sp, trg_perm=tp)
+
+
+def pkifmm_list_export(plan, name):
+    lib = load_library()
+    nbox = int(pkifmm_tree_stats(plan)[0])
+    n = _check(lib.pkifmm_list_export(plan, name.encode(), None, None, None))
+    ptr = np.zeros(nbox + 1, np.int64)
+    box = np.zeros(max(n, 1), np.int32)
+    sh = np.zeros((max(n, 1), 3), np.int8)
+    _check(lib.pkifmm_list_export(plan, name.encode(), _ptr(ptr), _ptr(box), _ptr(sh)))
+    return ptr, box[:n], sh[:n]
+
+
+def pkifmm_surface_singular_values(kernel, p):
+    n = 6 * (p - 1) ** 2 + 2
+    out = np.zeros(n * (1 if kernel == 0 else 3))
+    _check(load_library().pkifmm_surface_singular_values(kernel, p, _ptr(out)))
+    return out
+
+
+def pkifmm_backward_error(kernel, p):
+    out = np.zeros(1)
+    _check(load_library().pkifmm_backward_error(kernel, p, _ptr(out)))
+    return float(out[0])
+
+
+def pkifmm_root_operator(kernel, periodic_axes, p, ell):
+    kn = (6 * (p - 1) ** 2 + 2) * (1 if kernel == 0 else 3)
+    out = np.zeros((kn, kn))
+    _check(load_library().pkifmm_root_operator(kernel, periodic_axes, p, ell, _ptr(out)))
+    return out
+
+
+def pkifmm_plan_destroy(plan):
+    if plan:
+        load_library().pkifmm_plan_destroy(plan)
+
+
+def pkifmm_strerror(code):
+    return load_library().pkifmm_strerror(code).decode()
+
+
+class PeriodicKIFMM:
+    """Owns a plan; evaluate() passes torch CUDA tensors' device pointers."""
+
+    def __init__(self, kernel, periodic_axes, box_lo=(0.0, 0.0, 0.0), box_len=1.0, p=6, ell=2,
+                 leaf_max=64, depth_max=10, precision=0, nrhs=1, cache_dir=None):
+        self.kernel, self.k, self.nrhs = kernel, (1 if kernel == 0 else 3), nrhs
+        self.n = 6 * (p - 1) ** 2 + 2
+        self.kn = self.n * self.k
+        self.handle = pkifmm_plan_create(kernel, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max,
+                                         precision, nrhs, cache_dir)
+
+    def evaluate(self, src, dens, trg, pot=None, stream=None):
+        """src [S,3], dens [nrhs,S,k], trg [T,3] float64 CUDA tensors -> pot [nrhs,T,k]."""
+        import torch
+        S, T = src.shape[0], trg.shape[0]
+        for t in (src, dens, trg):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("inputs must be contiguous float64 CUDA tensors")
+        if pot is None:
+            pot = torch.empty((self.nrhs, T, self.k), dtype=torch.float64, device=src.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(src.device).cuda_stream
+        pkifmm_evaluate(self.handle, S, src, dens, T, trg, pot, ctypes.c_void_p(stream))
+        return pot
+
+    def evaluate_host(self, src, dens, trg, pot=None):
+        """Host (numpy) arrays in and out; copies happen inside the library call."""
+        src, dens, trg = (np.ascontiguousarray(a, dtype=np.float64) for a in (src, dens, trg))
+        if pot is None:
+            pot = np.zeros((self.nrhs, trg.shape[0], self.k))
+        pkifmm_evaluate_host(self.handle, src.shape[0], src, dens, trg.shape[0], trg, pot, None)
+        return pot
+
+    def stage_times(self):
+        return pkifmm_last_stage_times(self.handle)
+
+    def tree_stats(self):
+        return pkifmm_tree_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            pkifmm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,511 @@
+// C ABI of the periodic KIFMM library (declarations and contracts in
+// include/pkifmm.h).  Orchestrates Algorithm 2: Stage 1 in
+// pkifmm_plan_create, Stage 2 in pkifmm_evaluate.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace pk;
+
+struct pkifmm_plan_s {
+    Plan P;
+};
+
+namespace pk {
+void sort_points(Plan &P, const double *src, const double *dens, const double *trg, cudaStream_t s);
+}
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+template <typename F>
+int guarded(F &&f) {
+    try {
+        return f();
+    } catch (const Error &e) {
+        return fail(e.code, e.what());
+    } catch (const std::bad_alloc &) {
+        return fail(PKIFMM_ERR_OOM, "host allocation failed");
+    } catch (const std::exception &e) {
+        std::string m = e.what();
+        return fail(m.rfind("cache", 0) == 0 ? PKIFMM_ERR_CACHE : PKIFMM_ERR_INVALID_ARG, m);
+    }
+}
+
+__global__ void k_unpermute(const double *__restrict__ pot_s, const int *__restrict__ idx, long long T, int nrhs,
+                            int k, double invL, double *__restrict__ pot) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= T * nrhs * k) return;
+    long long t = i / (nrhs * k);
+    int rem = (int)(i % (nrhs * k)), r = rem / k, a = rem % k;
+    pot[((long long)r * T + idx[t]) * k + a] = pot_s[i] * invL;
+}
+
+// sums[2*c] += phi, sums[2*c+1] += |phi| per (rhs, component) c
+__global__ void k_dens_sums(const double *__restrict__ dens, long long S, int nk, double *sums) {
+    extern __shared__ double sh[];
+    int c = blockIdx.y;
+    double a = 0, b = 0;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < S; s += (long long)gridDim.x * blockDim.x) {
+        double v = dens[s * nk + c];
+        a += v;
+        b += fabs(v);
+    }
+    sh[threadIdx.x] = a;
+    sh[blockDim.x + threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+            sh[blockDim.x + threadIdx.x] += sh[blockDim.x + threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&sums[2 * c], sh[0]);
+        atomicAdd(&sums[2 * c + 1], sh[blockDim.x]);
+    }
+}
+
+bool needs_neutral(const Plan &P) {
+    if (!P.periodic) return false;
+    if (P.kernel == PKIFMM_LAPLACE) return true;
+    return P.periodic != 7;  // Stokes SP/DP: zero net force; TP allows a net force
+}
+
+void record(Plan &P, int i, cudaStream_t s) {
+    if (P.events) PK_CUDA(cudaEventRecord(P.ev[i], s));
+}
+
+int evaluate_impl(Plan &P, int64_t S, const double *src, const double *dens, int64_t T, const double *trg,
+                  double *pot, cudaStream_t s) {
+    if (S < 0 || T < 0 || S > (1LL << 30) || T > (1LL << 30)) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
+    if ((S && (!src || !dens)) || (T && (!trg || !pot))) return fail(PKIFMM_ERR_INVALID_ARG, "NULL array");
+    PK_CUDA(cudaSetDevice(P.device));
+    P.S = S;
+    P.T = T;
+    std::fill(P.stage_ms, P.stage_ms + 8, 0.0);
+    if (T == 0) return PKIFMM_OK;
+    if (S == 0) {
+        PK_CUDA(cudaMemsetAsync(pot, 0, sizeof(double) * T * P.nrhs * P.k, s));
+        return PKIFMM_OK;
+    }
+    record(P, 0, s);
+    sort_points(P, src, dens, trg, s);
+    int err[4] = {0, 0, 0, 0};
+    PK_CUDA(cudaMemcpy(err, P.err.p, sizeof err, cudaMemcpyDeviceToHost));
+    if (err[0]) return fail(PKIFMM_ERR_INVALID_ARG, "non-finite coordinate");
+    if (err[1]) return fail(PKIFMM_ERR_OUT_OF_BOX, "point outside the box along a free axis");
+    if (needs_neutral(P)) {
+        int nk = P.nrhs * P.k;
+        P.sums.reserve(2 * nk);
+        PK_CUDA(cudaMemsetAsync(P.sums.p, 0, sizeof(double) * 2 * nk, s));
+        dim3 grid((unsigned)std::min<long long>(1024, (S + 255) / 256), nk);
+        k_dens_sums<<<grid, 256, 2 * 256 * sizeof(double), s>>>(P.dens_s.p, S, nk, P.sums.p);
+        std::vector<double> h(2 * nk);
+        PK_CUDA(cudaMemcpyAsync(h.data(), P.sums.p, sizeof(double) * 2 * nk, cudaMemcpyDeviceToHost, s));
+        PK_CUDA(cudaStreamSynchronize(s));
+        for (int c = 0; c < nk; c++)
+            if (std::fabs(h[2 * c]) > 1e-12 * h[2 * c + 1])
+                return fail(PKIFMM_ERR_NOT_NEUTRAL, "densities violate the compatibility condition (net charge / force)");
+    }
+    record(P, 1, s);
+    build_tree(P, s);
+    build_lists(P, s);
+    build_tasks(P, s);
+    record(P, 2, s);
+    run_upward(P, s);
+    record(P, 3, s);
+    run_root(P, s);
+    record(P, 4, s);
+    run_m2l(P, s);
+    record(P, 5, s);
+    run_downward(P, s);
+    record(P, 6, s);
+    run_leaves(P, s);
+    long long n = T * P.nrhs * P.k;
+    k_unpermute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.pot_s.p, P.idxT.p, T, P.nrhs, P.k, 1.0 / P.L, pot);
+    record(P, 7, s);
+    PK_CUDA(cudaGetLastError());
+    return PKIFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, const double box_lo[3],
+                       double box_len, int p, int ell, int leaf_max, int depth_max, int precision, int nrhs,
+                       const char *cache_dir) {
+    if (!out) return fail(PKIFMM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (kernel != PKIFMM_LAPLACE && kernel != PKIFMM_STOKES) return fail(PKIFMM_ERR_INVALID_ARG, "kernel");
+    if (periodic_axes > 7) return fail(PKIFMM_ERR_INVALID_ARG, "periodic_axes");
+    if (!box_lo || !(box_len > 0) || !std::isfinite(box_len)) return fail(PKIFMM_ERR_INVALID_ARG, "box");
+    if (p < 4 || p > 16 || ell < 1 || ell > 8 || leaf_max < 1 || depth_max < 1 || depth_max > kMaxLevel - 1 ||
+        nrhs < 1 || nrhs > 64 || (precision != PKIFMM_FP64 && precision != PKIFMM_MIXED))
+        return fail(PKIFMM_ERR_INVALID_ARG, "p / ell / leaf_max / depth_max / nrhs / precision out of range");
+    bool sp = periodic_axes == 1 || periodic_axes == 2 || periodic_axes == 4;
+    if (!(periodic_axes == 0 || periodic_axes == 7 || (sp && kernel == PKIFMM_LAPLACE)))
+        return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built for this kernel");
+    return guarded([&]() {
+        auto *h = new pkifmm_plan_s;
+        Plan &P = h->P;
+        P.kernel = kernel;
+        P.k = kernel == 0 ? 1 : 3;
+        P.p = p;
+        P.n = surface_count(p);
+        P.kn = P.n * P.k;
+        P.ell = ell;
+        P.leaf_max = leaf_max;
+        P.depth_max = depth_max;
+        P.precision = precision;
+        P.nrhs = nrhs;
+        P.periodic = periodic_axes;
+        for (int a = 0; a < 3; a++) P.lo[a] = box_lo[a];
+        P.L = box_len;
+        try {
+            PK_CUDA(cudaGetDevice(&P.device));
+            // FP64: singular values <= eps_m * s_max dropped (Appendix B).
+            // MIXED: cut at the binary32 rounding level, since the operators
+            // are applied in binary32.
+            double eps = precision == PKIFMM_FP64 ? std::ldexp(1.0, -52) : std::ldexp(1.0, -24);
+            if (const char *e = std::getenv("PKIFMM_EPS_MIXED"); e && precision == PKIFMM_MIXED) eps = std::atof(e);
+            build_host_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
+            upload_operators(P);
+            for (auto &e : P.ev) PK_CUDA(cudaEventCreate(&e));
+            P.events = true;
+        } catch (...) {
+            delete h;
+            throw;
+        }
+        *out = h;
+        return PKIFMM_OK;
+    });
+}
+
+int pkifmm_evaluate(pkifmm_plan plan, int64_t S, const double *src_xyz, const double *dens, int64_t T,
+                    const double *trg_xyz, double *pot, void *cuda_stream) {
+    if (!plan) return fail(PKIFMM_ERR_INVALID_ARG, "plan is NULL");
+    return guarded([&]() {
+        return evaluate_impl(plan->P, S, src_xyz, dens, T, trg_xyz, pot, (cudaStream_t)cuda_stream);
+    });
+}
+
+int pkifmm_evaluate_host(pkifmm_plan plan, int64_t S, const double *src_xyz, const double *dens, int64_t T,
+                         const double *trg_xyz, double *pot, void *cuda_stream) {
+    if (!plan) return fail(PKIFMM_ERR_INVALID_ARG, "plan is NULL");
+    return guarded([&]() {
+        Plan &P = plan->P;
+        cudaStream_t s = (cudaStream_t)cuda_stream;
+        PK_CUDA(cudaSetDevice(P.device));
+        size_t bs = sizeof(double) * 3 * S, bd = sizeof(double) * S * P.nrhs * P.k;
+        size_t bt = sizeof(double) * 3 * T, bp = sizeof(double) * T * P.nrhs * P.k;
+        DBuf<char> buf;
+        buf.reserve(bs + bd + bt + bp + 64);
+        double *ds = (double *)buf.p, *dd = (double *)(buf.p + bs), *dt = (double *)(buf.p + bs + bd),
+               *dp = (double *)(buf.p + bs + bd + bt);
+        if (S) {
+            PK_CUDA(cudaMemcpyAsync(ds, src_xyz, bs, cudaMemcpyHostToDevice, s));
+            PK_CUDA(cudaMemcpyAsync(dd, dens, bd, cudaMemcpyHostToDevice, s));
+        }
+        if (T) PK_CUDA(cudaMemcpyAsync(dt, trg_xyz, bt, cudaMemcpyHostToDevice, s));
+        int rc = evaluate_impl(P, S, ds, dd, T, dt, dp, s);
+        if (rc == PKIFMM_OK && T) PK_CUDA(cudaMemcpyAsync(pot, dp, bp, cudaMemcpyDeviceToHost, s));
+        PK_CUDA(cudaStreamSynchronize(s));
+        buf.release();
+        return rc;
+    });
+}
+
+int pkifmm_last_stage_times(pkifmm_plan plan, double *ms, int max) {
+    if (!plan || !ms || max < 0) return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
+    return guarded([&]() {
+        Plan &P = plan->P;
+        if (P.events && P.T > 0 && P.S > 0) {
+            PK_CUDA(cudaEventSynchronize(P.ev[7]));
+            for (int i = 0; i < 7; i++) {
+                float t = 0;
+                PK_CUDA(cudaEventElapsedTime(&t, P.ev[i], P.ev[i + 1]));
+                P.stage_ms[i] = t;
+            }
+            float t = 0;
+            PK_CUDA(cudaEventElapsedTime(&t, P.ev[0], P.ev[7]));
+            P.stage_ms[7] = t;
+        }
+        int m = std::min(max, 8);
+        for (int i = 0; i < m; i++) ms[i] = P.stage_ms[i];
+        return m;
+    });
+}
+
+int pkifmm_tree_stats(pkifmm_plan plan, int64_t *out, int max) {
+    if (!plan || !out || max < 0) return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
+    Tree &t = plan->P.tree;
+    int64_t v[8] = {t.nbox, t.nleaf, t.depth, t.nU, t.nV, t.nW, t.nX, t.p2p_pairs};
+    int m = std::min(max, 8);
+    for (int i = 0; i < m; i++) out[i] = v[i];
+    return m;
+}
+
+int pkifmm_tree_export(pkifmm_plan plan, int32_t *level, int32_t *pos, int32_t *parent, int64_t *src_range,
+                       int64_t *trg_range, int64_t *src_perm, int64_t *trg_perm) {
+    if (!plan) return fail(PKIFMM_ERR_INVALID_ARG, "plan is NULL");
+    return guarded([&]() {
+        Plan &P = plan->P;
+        Tree &t = P.tree;
+        int nb = t.nbox;
+        std::vector<int4> bp(nb);
+        std::vector<int> par(nb);
+        std::vector<int2> sr(nb), tr(nb);
+        if (nb) {
+            PK_CUDA(cudaMemcpy(bp.data(), t.bpos.p, sizeof(int4) * nb, cudaMemcpyDeviceToHost));
+            PK_CUDA(cudaMemcpy(par.data(), t.parent.p, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+            PK_CUDA(cudaMemcpy(sr.data(), t.srange.p, sizeof(int2) * nb, cudaMemcpyDeviceToHost));
+            PK_CUDA(cudaMemcpy(tr.data(), t.trange.p, sizeof(int2) * nb, cudaMemcpyDeviceToHost));
+        }
+        for (int b = 0; b < nb; b++) {
+            if (level) level[b] = bp[b].w;
+            if (pos) {
+                pos[3 * b] = bp[b].x;
+                pos[3 * b + 1] = bp[b].y;
+                pos[3 * b + 2] = bp[b].z;
+            }
+            if (parent) parent[b] = par[b];
+            if (src_range) {
+                src_range[2 * b] = sr[b].x;
+                src_range[2 * b + 1] = sr[b].y;
+            }
+            if (trg_range) {
+                trg_range[2 * b] = tr[b].x;
+                trg_range[2 * b + 1] = tr[b].y;
+            }
+        }
+        auto perm = [&](int64_t *dst, const DBuf<int> &src, int64_t n) {
+            if (!dst || !n) return;
+            std::vector<int> h(n);
+            PK_CUDA(cudaMemcpy(h.data(), src.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < n; i++) dst[i] = h[i];
+        };
+        perm(src_perm, P.idxS, P.S);
+        perm(trg_perm, P.idxT, P.T);
+        return PKIFMM_OK;
+    });
+}
+
+int pkifmm_list_export(pkifmm_plan plan, char name, int64_t *list_ptr, int32_t *list_box, int8_t *list_shift) {
+    if (!plan) return fail(PKIFMM_ERR_INVALID_ARG, "plan is NULL");
+    return guarded([&]() {
+        Plan &P = plan->P;
+        Tree &t = P.tree;
+        int nb = t.nbox;
+        std::vector<int64_t> ptr(nb + 1, 0);
+        std::vector<int> box;
+        std::vector<int8_t> sh;
+        auto csr = [&](const DBuf<int> &dp, const DBuf<int> &db, const DBuf<unsigned char> &ds, long long n) {
+            std::vector<int> p32(nb + 1);
+            PK_CUDA(cudaMemcpy(p32.data(), dp.p, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost));
+            box.resize(n);
+            std::vector<unsigned char> c(n);
+            if (n) {
+                PK_CUDA(cudaMemcpy(box.data(), db.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+                PK_CUDA(cudaMemcpy(c.data(), ds.p, n, cudaMemcpyDeviceToHost));
+            }
+            for (int b = 0; b <= nb; b++) ptr[b] = p32[b];
+            sh.resize(3 * n);
+            for (long long i = 0; i < n; i++) {
+                sh[3 * i] = (int8_t)(c[i] / 9 - 1);
+                sh[3 * i + 1] = (int8_t)((c[i] / 3) % 3 - 1);
+                sh[3 * i + 2] = (int8_t)(c[i] % 3 - 1);
+            }
+        };
+        if (name == 'U') csr(t.u_ptr, t.u_box, t.u_sh, t.nU);
+        else if (name == 'W') csr(t.w_ptr, t.w_box, t.w_sh, t.nW);
+        else if (name == 'X') csr(t.x_ptr, t.x_box, t.x_sh, t.nX);
+        else if (name == 'V') {
+            std::vector<int> vs((size_t)nb * kVSlots);
+            std::vector<int4> bp(nb);
+            if (nb) {
+                PK_CUDA(cudaMemcpy(vs.data(), t.v_slot.p, sizeof(int) * vs.size(), cudaMemcpyDeviceToHost));
+                PK_CUDA(cudaMemcpy(bp.data(), t.bpos.p, sizeof(int4) * nb, cudaMemcpyDeviceToHost));
+            }
+            // slot -> offset per octant class (same enumeration as the device tables)
+            std::vector<int> soff(8 * kVSlots * 3);
+            for (int c = 0; c < 8; c++) {
+                int cb[3] = {c & 1, c >> 1 & 1, c >> 2 & 1}, s = 0;
+                for (int x = -2 - cb[0]; x <= 3 - cb[0]; x++)
+                    for (int y = -2 - cb[1]; y <= 3 - cb[1]; y++)
+                        for (int z = -2 - cb[2]; z <= 3 - cb[2]; z++) {
+                            if (std::max(std::abs(x), std::max(std::abs(y), std::abs(z))) <= 1) continue;
+                            soff[(c * kVSlots + s) * 3] = x;
+                            soff[(c * kVSlots + s) * 3 + 1] = y;
+                            soff[(c * kVSlots + s) * 3 + 2] = z;
+                            s++;
+                        }
+            }
+            for (int b = 0; b < nb; b++) {
+                ptr[b] = (int64_t)box.size();
+                int pp[3] = {bp[b].x, bp[b].y, bp[b].z}, l = bp[b].w, n = 1 << l;
+                int c = (pp[0] & 1) | (pp[1] & 1) << 1 | (pp[2] & 1) << 2;
+                for (int s = 0; s < kVSlots; s++) {
+                    int a = vs[(size_t)b * kVSlots + s];
+                    if (a < 0) continue;
+                    box.push_back(a);
+                    for (int q = 0; q < 3; q++) {
+                        int e = pp[q] + soff[(c * kVSlots + s) * 3 + q];
+                        sh.push_back((int8_t)(e >= 0 ? e / n : -((-e + n - 1) / n)));
+                    }
+                }
+            }
+            ptr[nb] = (int64_t)box.size();
+        } else {
+            return fail(PKIFMM_ERR_INVALID_ARG, "list name must be U, V, W or X");
+        }
+        if (list_ptr) std::copy(ptr.begin(), ptr.end(), list_ptr);
+        if (list_box) std::copy(box.begin(), box.end(), list_box);
+        if (list_shift) std::copy(sh.begin(), sh.end(), list_shift);
+        return (int)std::min<size_t>(box.size(), 0x7fffffff);
+    });
+}
+
+int pkifmm_surface_singular_values(int kernel, int p, double *s_out) {
+    if ((kernel != 0 && kernel != 1) || p < 2 || p > 16 || !s_out) return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
+    return guarded([&]() {
+        int n = surface_count(p);
+        auto g = surface_grid(p);
+        std::vector<double> x(3 * n), y(3 * n);
+        for (int i = 0; i < 3 * n; i++) {
+            x[i] = kInnerHalf * g[i];
+            y[i] = kOuterHalf * g[i];
+        }
+        auto A = kernel_matrix(kernel, x, y);
+        std::vector<double> U, S, V;
+        jacobi_svd(n * (kernel ? 3 : 1), A, U, S, V);
+        std::copy(S.begin(), S.end(), s_out);
+        return PKIFMM_OK;
+    });
+}
+
+int pkifmm_backward_error(int kernel, int p, double *err_out) {
+    if ((kernel != 0 && kernel != 1) || p < 2 || p > 16 || !err_out) return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
+    return guarded([&]() {
+        int n = surface_count(p), m = n * (kernel ? 3 : 1);
+        auto g = surface_grid(p);
+        std::vector<double> x(3 * n), y(3 * n);
+        for (int i = 0; i < 3 * n; i++) {
+            x[i] = kInnerHalf * g[i];
+            y[i] = kOuterHalf * g[i];
+        }
+        auto A = kernel_matrix(kernel, x, y);
+        std::vector<double> U, S, V;
+        jacobi_svd(m, A, U, S, V);
+        double cut = std::ldexp(1.0, -52) * S[0];
+        std::vector<double> t(m, 0.0), sol(m, 0.0);
+        for (int j = 0; j < m; j++) {  // t = S+ (U^T b), b = 1
+            double acc = 0;
+            for (int i = 0; i < m; i++) acc += U[(size_t)i * m + j];
+            t[j] = S[j] > cut ? acc / S[j] : 0.0;
+        }
+        for (int i = 0; i < m; i++) {  // x = V t
+            double acc = 0;
+            for (int j = 0; j < m; j++) acc += V[(size_t)i * m + j] * t[j];
+            sol[i] = acc;
+        }
+        double e = 0;
+        for (int i = 0; i < m; i++) {
+            double acc = 0;
+            for (int j = 0; j < m; j++) acc += A[(size_t)i * m + j] * sol[j];
+            e = std::max(e, std::fabs(acc - 1.0));
+        }
+        *err_out = e;
+        return PKIFMM_OK;
+    });
+}
+
+int pkifmm_root_operator(int kernel, unsigned periodic_axes, int p, int ell, double *m_out) {
+    bool sp = periodic_axes == 1 || periodic_axes == 2 || periodic_axes == 4;
+    if ((kernel != 0 && kernel != 1) || p < 2 || p > 16 || ell < 1 || ell > 8 || !m_out)
+        return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
+    if (!(periodic_axes == 7 || (sp && kernel == 0))) return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built");
+    return guarded([&]() {
+        auto M = root_operator(kernel, p, periodic_axes, ell, surface_grid(p));
+        std::copy(M.begin(), M.end(), m_out);
+        return PKIFMM_OK;
+    });
+}
+
+void pkifmm_plan_destroy(pkifmm_plan plan) {
+    if (!plan) return;
+    Plan &P = plan->P;
+    cudaSetDevice(P.device);
+    cudaDeviceSynchronize();
+    for (auto &e : P.ev)
+        if (P.events && e) cudaEventDestroy(e);
+    DBuf<double> *d64[] = {&P.g64, &P.uc2e_a, &P.uc2e_b, &P.dc2e_a, &P.dc2e_b, &P.m2m, &P.l2l, &P.m2l, &P.root,
+                           &P.xs, &P.xt, &P.dens_s, &P.pot_s, &P.ysrel64, &P.xtrel64, &P.sums, &P.up64, &P.chk64,
+                           &P.dn64, &P.tmp64};
+    for (auto *b : d64) b->release();
+    DBuf<float> *d32[] = {&P.g32, &P.uc2e_a32, &P.uc2e_b32, &P.dc2e_a32, &P.dc2e_b32, &P.m2m32, &P.l2l32, &P.m2l32,
+                          &P.ysrel32, &P.xtrel32, &P.dens32, &P.pot32, &P.up32, &P.chk32, &P.dn32, &P.tmp32};
+    for (auto *b : d32) b->release();
+    DBuf<int> *di[] = {&P.class_slot_op, &P.idxS, &P.idxT, &P.idxS2, &P.idxT2, &P.hist, &P.err, &P.cnt, &P.off,
+                       &P.gather_idx, &P.leaves_src, &P.leaves_trg, &P.xboxes, &P.tree.parent, &P.tree.child,
+                       &P.tree.lvl_begin_d, &P.tree.u_ptr, &P.tree.u_box, &P.tree.w_ptr, &P.tree.w_box,
+                       &P.tree.x_ptr, &P.tree.x_box, &P.tree.v_slot};
+    for (auto *b : di) b->release();
+    P.keyS.release();
+    P.keyT.release();
+    P.keyS2.release();
+    P.keyT2.release();
+    P.tree.key.release();
+    P.tree.bpos.release();
+    P.tree.srange.release();
+    P.tree.trange.release();
+    P.tree.u_sh.release();
+    P.tree.w_sh.release();
+    P.tree.x_sh.release();
+    P.slot_of.release();
+    P.csr.release();
+    P.ctr.release();
+    Task *ts[] = {&P.t_uc2e, &P.t_m2l, &P.t_dc2e, &P.t_root};
+    for (auto *t : ts) {
+        t->boxes.release();
+        t->tiles.release();
+        t->class_ops.release();
+    }
+    for (auto *v : {&P.t_m2m, &P.t_l2l})
+        for (auto &t : *v) {
+            t.boxes.release();
+            t.tiles.release();
+            t.class_ops.release();
+        }
+    delete plan;
+}
+
+const char *pkifmm_strerror(int code) {
+    switch (code) {
+        case PKIFMM_OK: return "ok";
+        case PKIFMM_ERR_INVALID_ARG: return "invalid argument";
+        case PKIFMM_ERR_OUT_OF_BOX: return "point outside the box along a free axis";
+        case PKIFMM_ERR_NOT_NEUTRAL: return "compatibility condition violated (net charge or net force)";
+        case PKIFMM_ERR_CUDA: return "CUDA error";
+        case PKIFMM_ERR_OOM: return "out of memory";
+        case PKIFMM_ERR_TIMEOUT: return "bounded device wait gave up";
+        case PKIFMM_ERR_CACHE: return "operator cache unreadable or unwritable";
+        case PKIFMM_ERR_UNSUPPORTED: return "combination not built";
+        default: return "unknown error";
+    }
+}
+
+const char *pkifmm_last_error_message(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

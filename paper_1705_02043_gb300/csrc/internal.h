@@ -1,0 +1,156 @@
+// Internal declarations shared by the CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/pkifmm.h"
+#include "precompute.h"
+
+namespace pk {
+
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define PK_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            throw ::pk::Error(e_ == cudaErrorMemoryAllocation ? PKIFMM_ERR_OOM : PKIFMM_ERR_CUDA, \
+                              std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+constexpr int kMaxLevel = 16;
+constexpr int kVSlots = 189;     // V-list slots per target octant class
+constexpr int kM2LOps = 316;     // offsets o in [-3,3]^3 with |o|_inf >= 2
+
+// Device buffer that only grows.
+template <typename T>
+struct DBuf {
+    T *p = nullptr;
+    size_t cap = 0;
+    void reserve(size_t n) {
+        if (n <= cap) return;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t m = n + n / 4 + 64;
+        PK_CUDA(cudaMalloc(&p, m * sizeof(T)));
+        cap = m;
+    }
+    // grow keeping contents (first `keep` elements)
+    void grow_keep(size_t n, size_t keep, cudaStream_t s) {
+        if (n <= cap) return;
+        T *q = nullptr;
+        size_t m = n + n / 2 + 64;
+        PK_CUDA(cudaMalloc(&q, m * sizeof(T)));
+        if (p && keep) PK_CUDA(cudaMemcpyAsync(q, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        if (p) {
+            PK_CUDA(cudaStreamSynchronize(s));
+            cudaFree(p);
+        }
+        p = q;
+        cap = m;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+// Octree on the device.  Boxes are numbered level by level; within a level
+// they are in Morton order (octant bits x = 1, y = 2, z = 4).
+struct Tree {
+    int nbox = 0, depth = 0;
+    std::vector<int> lvl_begin;        // host: boxes of level l in [lvl_begin[l], lvl_begin[l+1])
+    DBuf<unsigned long long> key;      // Morton key at the box's level
+    DBuf<int4> bpos;                   // (x, y, z, level)
+    DBuf<int> parent;                  // -1 for the root
+    DBuf<int> child;                   // [nbox][8], -1 if absent
+    DBuf<int2> srange, trange;         // point ranges in sorted order
+    DBuf<int> lvl_begin_d;             // device copy of lvl_begin
+    // lists: CSR over target boxes; entries (box, shift code 0..26)
+    DBuf<int> u_ptr, u_box, w_ptr, w_box, x_ptr, x_box;
+    DBuf<unsigned char> u_sh, w_sh, x_sh;
+    DBuf<int> v_slot;                  // [nbox][189] source box or -1
+    long long nU = 0, nW = 0, nX = 0, nV = 0, p2p_pairs = 0;
+    int nleaf = 0;
+};
+
+// A batch of dense translations dst[row] (+)= sum_s OP[class, s] src[slot(row, s)].
+struct Task {
+    int nrows = 0;            // rows = boxes * nrhs
+    int nclass = 1, nslots = 1;
+    DBuf<int> boxes;          // dst box per task box (class-major order)
+    DBuf<int4> tiles;         // (class, row0, nrows, 0)
+    int ntiles = 0;
+    DBuf<int> class_ops;      // [nclass][nslots]
+    std::vector<int> h_boxes; // host copies used to build tiles
+};
+
+struct Plan {
+    int kernel = 0, k = 1, p = 0, n = 0, kn = 0, ell = 2, leaf_max = 64, depth_max = 10;
+    int precision = 0, nrhs = 1, device = 0;
+    unsigned periodic = 0;
+    double lo[3] = {0, 0, 0}, L = 1;
+    HostOps host;
+
+    // operators on the device (FP64 master copies; FP32 copies for MIXED)
+    DBuf<double> g64;                           // [n][3]
+    DBuf<float> g32;
+    DBuf<double> uc2e_a, uc2e_b, dc2e_a, dc2e_b, m2m, l2l, m2l, root;
+    DBuf<float> uc2e_a32, uc2e_b32, dc2e_a32, dc2e_b32, m2m32, l2l32, m2l32;
+    DBuf<int> class_slot_op;                    // [8][189] M2L op index per class slot
+    DBuf<signed char> slot_of;                  // [8][343] slot of offset o, -1 if none
+
+    // evaluation workspace
+    int64_t S = 0, T = 0;
+    DBuf<unsigned long long> keyS, keyT, keyS2, keyT2;
+    DBuf<int> idxS, idxT, idxS2, idxT2;
+    DBuf<int> hist;
+    DBuf<int> err;                              // [4] device error flags
+    DBuf<double> xs, xt;                        // sorted unit coordinates [N][3]
+    DBuf<double> dens_s;                        // sorted densities [S][nrhs*k]
+    DBuf<double> pot_s;                         // sorted potentials [T][nrhs*k]
+    DBuf<double> ysrel64, xtrel64;              // leaf-relative coordinates [N][4]
+    DBuf<float> ysrel32, xtrel32;
+    DBuf<float> dens32, pot32;
+    DBuf<double> sums;                          // neutrality sums
+    // equivalent densities [nbox][nrhs][kn]
+    DBuf<double> up64, chk64, dn64, tmp64;
+    DBuf<float> up32, chk32, dn32, tmp32;
+    // tree build scratch
+    DBuf<int> cnt, off;
+    DBuf<int2> csr, ctr;                        // [nlevel boxes][8] child ranges
+    DBuf<int> gather_idx;
+    Tree tree;
+    Task t_uc2e, t_m2l, t_dc2e, t_root;
+    std::vector<Task> t_m2m, t_l2l;             // per level
+    DBuf<int> leaves_src, leaves_trg, xboxes;   // task lists for kernel sums
+    int n_leaves_src = 0, n_leaves_trg = 0, n_xboxes = 0;
+    double stage_ms[8] = {0};
+    cudaEvent_t ev[9] = {};
+    bool events = false;
+};
+
+// ---- tree.cu ----
+void build_tree(Plan &P, cudaStream_t s);
+void build_lists(Plan &P, cudaStream_t s);
+// ---- translate.cu ----
+void upload_operators(Plan &P);
+void build_tasks(Plan &P, cudaStream_t s);
+void run_upward(Plan &P, cudaStream_t s);
+void run_root(Plan &P, cudaStream_t s);
+void run_m2l(Plan &P, cudaStream_t s);
+void run_downward(Plan &P, cudaStream_t s);
+void run_leaves(Plan &P, cudaStream_t s);
+
+inline int shift_code(int sx, int sy, int sz) { return (sx + 1) * 9 + (sy + 1) * 3 + (sz + 1); }
+
+}  // namespace pk

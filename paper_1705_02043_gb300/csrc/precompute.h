@@ -1,0 +1,61 @@
+// Host-side operator precompute (Algorithm 2, Stage 1; Sec. 2.2-2.3, 3.1).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace pk {
+
+// Surface radii as multiples of the box edge (Sec. 2.2): the upward
+// equivalent and downward check surfaces are cubes of edge 1.05, the upward
+// check and downward equivalent surfaces cubes of edge 2.95, all centred on
+// the box.  Half-widths:
+constexpr double kInnerHalf = 0.525;
+constexpr double kOuterHalf = 1.475;
+
+int surface_count(int p);                       // 6(p-1)^2 + 2
+std::vector<double> surface_grid(int p);        // [n][3] on the cube [-1,1]^3
+
+// k x k block K(x, y) of the free-space kernel (row-major).
+void kernel_block(int kernel, const double *x, const double *y, double *out);
+
+// Dense kernel matrix [n_x*k][n_y*k] (row-major).
+std::vector<double> kernel_matrix(int kernel, const std::vector<double> &x,
+                                  const std::vector<double> &y);
+
+// One-sided Jacobi SVD of a square m x m row-major matrix A = U S V^T.
+// U, V row-major m x m, S descending.
+void jacobi_svd(int m, const std::vector<double> &A, std::vector<double> &U,
+                std::vector<double> &S, std::vector<double> &V);
+
+struct HostOps {
+    int kernel = 0, k = 1, p = 0, n = 0, kn = 0;
+    unsigned periodic = 0;
+    int ell = 0;
+    double eps_rel = 0;             // singular values <= eps_rel * s_max are dropped
+    std::vector<double> g;          // [n][3] unit surface grid
+    std::vector<double> U, S, V;    // SVD of A_up1 = K(1.475 g, 0.525 g)
+    // check-to-equivalent factors, applied as two products (Sec. 3.1):
+    //   upward:   phi = (V S+) (U^T q)      downward: phi = (U S+) (V^T q)
+    std::vector<double> uc2e_a, uc2e_b, dc2e_a, dc2e_b;
+    std::vector<double> m2m;        // [8][kn][kn] child octant -> parent up density
+    std::vector<double> l2l;        // [8][kn][kn] parent down density -> child octant
+    std::vector<double> root;       // [kn][kn] far-field check operator (periodic)
+};
+
+// Build all host operators; throws std::runtime_error on failure.
+// cache_dir may be empty.
+void build_host_ops(HostOps &ops, int kernel, int p, unsigned periodic, int ell,
+                    double eps_rel, const std::string &cache_dir);
+
+// K^{P,F}_ell(r) block for a unit periodic box, r a difference vector with
+// |r_a| <= ~1.1; periodic in the axes of `periodic`.
+void far_kernel_block(int kernel, unsigned periodic, int ell, const double *r, double *out);
+
+// Root operator M[kn][kn] = K^{P,F}_ell(x^d, y^u) + sum_{1<|p|<=ell} K(x^d, y^u + p).
+std::vector<double> root_operator(int kernel, int p, unsigned periodic, int ell,
+                                  const std::vector<double> &g);
+
+void matmul(int m, int n, int kk, const double *A, const double *B, double *C);  // C = A B
+
+}  // namespace pk

@@ -1,0 +1,817 @@
+// Translations of the KIFMM passes (Sec. 2.2) on the device.
+//
+// Densities live per box as rows [box][nrhs][kn] (kn = k * n equivalent
+// values).  With q~ = h q (check potential times box edge) every operator is
+// level independent (both kernels are homogeneous of degree -1):
+//   S2M   q~u  = h sum_s K(c + 1.475 h g_i, y_s) phi_s            (leaf kernel sum)
+//   UC2E  phi_u = (V S+)(U^T q~u)                                  (two products, Sec. 3.1)
+//   M2M   phi_u(P) = sum_children T_M2M[oct] phi_u(C)
+//   root  q~d(B0) = M_root phi_u(B0)                               (Algorithm 2 step c)
+//   M2L   q~d(B) = sum_{V} K(0.525 g_i, o + 0.525 g_j) phi_u(A)    (o = offset in boxes)
+//   S2L   q~d(B) += h sum_{X} K(c + 0.525 h g_i, y_s + p) phi_s
+//   DC2E  phi_d = (U S+)(V^T q~d)
+//   L2L   phi_d(C) += T_L2L[oct] phi_d(P)                          (carries the far field down)
+//   leaf  q_t = L2T + W-list M2T + U-list P2P (incl. periodic images)
+// Dense translations share one "slot GEMM": each destination row gathers
+// its source rows through a slot table and multiplies by the operator its
+// (class, slot) selects; boxes are grouped by class so a tile of rows shares
+// every operator load.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace pk {
+
+void sort_points(Plan &P, const double *src, const double *dens, const double *trg, cudaStream_t s);
+void m2l_tc_prepare(Plan &P);
+bool m2l_tc_run(Plan &P, cudaStream_t s);
+
+static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------- operator upload ----------------
+
+// K_o[i*k+a][j*k+b] = K(0.525 g_i, o + 0.525 g_j) for the 316 M2L offsets.
+template <typename T>
+__global__ void k_m2l_ops(int kernel, int n, const double *__restrict__ g, const int *__restrict__ offs,
+                          T *__restrict__ out) {
+    int kk = kernel == 0 ? 1 : 3, kn = n * kk;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (long long)kM2LOps * n * n;
+    if (i >= total) return;
+    int m = (int)(i / ((long long)n * n)), rem = (int)(i % ((long long)n * n)), a = rem / n, b = rem % n;
+    double d[3];
+    for (int c = 0; c < 3; c++) d[c] = 0.525 * g[3 * a + c] - (offs[3 * m + c] + 0.525 * g[3 * b + c]);
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double ir = 1.0 / sqrt(r2);
+    T *o = out + (long long)m * kn * kn;
+    if (kernel == 0) {
+        o[(long long)a * kn + b] = (T)ir;
+    } else {
+        double c8 = 1.0 / (8.0 * 3.14159265358979323846), ir3 = ir * ir * ir;
+        for (int p = 0; p < 3; p++)
+            for (int q = 0; q < 3; q++)
+                o[(long long)(a * 3 + p) * kn + b * 3 + q] = (T)(c8 * ((p == q ? ir : 0.0) + d[p] * d[q] * ir3));
+    }
+}
+
+template <typename T>
+static void upload(DBuf<T> &d, const std::vector<double> &h) {
+    d.reserve(h.size() + 1);
+    std::vector<T> t(h.begin(), h.end());
+    PK_CUDA(cudaMemcpy(d.p, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice));
+}
+
+void upload_operators(Plan &P) {
+    HostOps &H = P.host;
+    upload(P.g64, H.g);
+    upload(P.g32, H.g);
+    // M2L offset enumeration and per-class slot tables
+    std::vector<int> offs;
+    std::vector<int> op_of(343, -1);
+    for (int x = -3; x <= 3; x++)
+        for (int y = -3; y <= 3; y++)
+            for (int z = -3; z <= 3; z++) {
+                if (std::max(std::abs(x), std::max(std::abs(y), std::abs(z))) <= 1) continue;
+                op_of[((x + 3) * 7 + (y + 3)) * 7 + (z + 3)] = (int)offs.size() / 3;
+                offs.push_back(x);
+                offs.push_back(y);
+                offs.push_back(z);
+            }
+    std::vector<signed char> slot_of(8 * 343, -1);
+    std::vector<int> cls_op(8 * kVSlots, -1);
+    for (int c = 0; c < 8; c++) {
+        int cb[3] = {c & 1, c >> 1 & 1, c >> 2 & 1}, s = 0;
+        for (int x = -2 - cb[0]; x <= 3 - cb[0]; x++)
+            for (int y = -2 - cb[1]; y <= 3 - cb[1]; y++)
+                for (int z = -2 - cb[2]; z <= 3 - cb[2]; z++) {
+                    if (std::max(std::abs(x), std::max(std::abs(y), std::abs(z))) <= 1) continue;
+                    int oi = ((x + 3) * 7 + (y + 3)) * 7 + (z + 3);
+                    slot_of[c * 343 + oi] = (signed char)s;
+                    cls_op[c * kVSlots + s] = op_of[oi];
+                    s++;
+                }
+    }
+    P.slot_of.reserve(slot_of.size());
+    PK_CUDA(cudaMemcpy(P.slot_of.p, slot_of.data(), slot_of.size(), cudaMemcpyHostToDevice));
+    P.class_slot_op.reserve(cls_op.size());
+    PK_CUDA(cudaMemcpy(P.class_slot_op.p, cls_op.data(), sizeof(int) * cls_op.size(), cudaMemcpyHostToDevice));
+    DBuf<int> doffs;
+    doffs.reserve(offs.size());
+    PK_CUDA(cudaMemcpy(doffs.p, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice));
+
+    const size_t kn2 = (size_t)P.kn * P.kn;
+    long long tot = (long long)kM2LOps * P.n * P.n;
+    if (P.precision == PKIFMM_FP64) {
+        upload(P.uc2e_a, H.uc2e_a);
+        upload(P.uc2e_b, H.uc2e_b);
+        upload(P.dc2e_a, H.dc2e_a);
+        upload(P.dc2e_b, H.dc2e_b);
+        upload(P.m2m, H.m2m);
+        upload(P.l2l, H.l2l);
+        P.m2l.reserve(kM2LOps * kn2);
+        k_m2l_ops<double><<<nblk(tot, 256), 256>>>(P.kernel, P.n, P.g64.p, doffs.p, P.m2l.p);
+    } else {
+        upload(P.uc2e_a32, H.uc2e_a);
+        upload(P.uc2e_b32, H.uc2e_b);
+        upload(P.dc2e_a32, H.dc2e_a);
+        upload(P.dc2e_b32, H.dc2e_b);
+        upload(P.m2m32, H.m2m);
+        upload(P.l2l32, H.l2l);
+        P.m2l32.reserve(kM2LOps * kn2);
+        k_m2l_ops<float><<<nblk(tot, 256), 256>>>(P.kernel, P.n, P.g64.p, doffs.p, P.m2l32.p);
+        // the root far field and its solve stay in binary64
+        upload(P.dc2e_a, H.dc2e_a);
+        upload(P.dc2e_b, H.dc2e_b);
+    }
+    if (P.periodic) upload(P.root, H.root);
+    PK_CUDA(cudaGetLastError());
+    PK_CUDA(cudaDeviceSynchronize());
+    doffs.release();
+    if (P.precision == PKIFMM_MIXED) m2l_tc_prepare(P);
+}
+
+// ---------------- slot GEMM ----------------
+
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16, G_TM = 4, G_TN = 4;  // 256 threads
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_slot_gemm(const int *__restrict__ tboxes, const int4 *__restrict__ tiles,
+                                                   const int *__restrict__ slot_table, int slot_stride, int nslots,
+                                                   const int *__restrict__ class_ops, const T *__restrict__ ops,
+                                                   long long op_stride, const T *__restrict__ src,
+                                                   T *__restrict__ dst, int kn, int nrhs, int beta) {
+    __shared__ T As[GB_K][GB_M + 1];
+    __shared__ T Bs[GB_K][GB_N + 1];
+    __shared__ long long srow[GB_M], drow[GB_M];
+    __shared__ int sbox[GB_M];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int4 tile = tiles[blockIdx.x];
+    const int cls = tile.x, row0 = tile.y, nr = tile.z, n0 = blockIdx.y * GB_N;
+    if (tid < GB_M) {
+        if (tid < nr) {
+            int row = row0 + tid, tb = row / nrhs, rhs = row % nrhs, box = tboxes[tb];
+            drow[tid] = (long long)box * nrhs + rhs;
+            sbox[tid] = box;
+        } else {
+            drow[tid] = -1;
+            sbox[tid] = -1;
+        }
+    }
+    __syncthreads();
+    T acc[G_TM][G_TN];
+#pragma unroll
+    for (int i = 0; i < G_TM; i++)
+#pragma unroll
+        for (int j = 0; j < G_TN; j++) acc[i][j] = (T)0;
+    const int lm = tid / 4, lk = (tid % 4) * 4;
+    for (int s = 0; s < nslots; s++) {
+        int op = class_ops[cls * nslots + s];
+        if (op < 0) continue;
+        __syncthreads();
+        int any = 0;
+        if (tid < GB_M) {
+            long long sr = -1;
+            if (drow[tid] >= 0) {
+                int b = sbox[tid];
+                int sb = slot_table ? slot_table[(long long)b * slot_stride + s] : b;
+                if (sb >= 0) sr = (long long)sb * nrhs + (drow[tid] - (long long)b * nrhs);
+            }
+            srow[tid] = sr;
+            any = sr >= 0;
+        }
+        if (!__syncthreads_or(any)) continue;
+        const T *Op = ops + (long long)op * op_stride;
+        const long long sr = srow[lm];
+        for (int k0 = 0; k0 < kn; k0 += GB_K) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                int kk = k0 + lk + q;
+                As[lk + q][lm] = (sr >= 0 && kk < kn) ? src[sr * kn + kk] : (T)0;
+                int nn = n0 + lm;
+                Bs[lk + q][lm] = (nn < kn && kk < kn) ? Op[(long long)nn * kn + kk] : (T)0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < GB_K; kk++) {
+                T a[G_TM], b[G_TN];
+#pragma unroll
+                for (int i = 0; i < G_TM; i++) a[i] = As[kk][ty * G_TM + i];
+#pragma unroll
+                for (int j = 0; j < G_TN; j++) b[j] = Bs[kk][tx * G_TN + j];
+#pragma unroll
+                for (int i = 0; i < G_TM; i++)
+#pragma unroll
+                    for (int j = 0; j < G_TN; j++) acc[i][j] += a[i] * b[j];
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < G_TM; i++) {
+        long long dr = drow[ty * G_TM + i];
+        if (dr < 0) continue;
+#pragma unroll
+        for (int j = 0; j < G_TN; j++) {
+            int nn = n0 + tx * G_TN + j;
+            if (nn >= kn) continue;
+            T *d = dst + dr * kn + nn;
+            *d = beta ? *d + acc[i][j] : acc[i][j];
+        }
+    }
+}
+
+// ---------------- tasks ----------------
+
+struct HostTree {
+    std::vector<int4> bpos;
+    std::vector<int> child, parent;
+    std::vector<int2> sr, tr;
+    bool leaf(int b) const {
+        for (int c = 0; c < 8; c++)
+            if (child[8 * (size_t)b + c] >= 0) return false;
+        return true;
+    }
+    bool has_src(int b) const { return sr[b].y > sr[b].x; }
+    bool has_trg(int b) const { return tr[b].y > tr[b].x; }
+    int octant(int b) const { return (bpos[b].x & 1) | (bpos[b].y & 1) << 1 | (bpos[b].z & 1) << 2; }
+};
+
+// boxes: per class list of dst boxes
+static void make_task(Task &t, const std::vector<std::vector<int>> &by_class, int nslots,
+                      const std::vector<int> &class_ops, int nrhs, cudaStream_t s) {
+    t.nclass = (int)by_class.size();
+    t.nslots = nslots;
+    t.h_boxes.clear();
+    std::vector<int4> tiles;
+    for (int c = 0; c < t.nclass; c++) {
+        int row0 = (int)t.h_boxes.size() * nrhs;
+        int nrows = (int)by_class[c].size() * nrhs;
+        for (int r = 0; r < nrows; r += GB_M) tiles.push_back(make_int4(c, row0 + r, std::min(GB_M, nrows - r), 0));
+        t.h_boxes.insert(t.h_boxes.end(), by_class[c].begin(), by_class[c].end());
+    }
+    t.nrows = (int)t.h_boxes.size() * nrhs;
+    t.ntiles = (int)tiles.size();
+    t.boxes.reserve(t.h_boxes.size() + 1);
+    t.tiles.reserve(tiles.size() + 1);
+    t.class_ops.reserve(class_ops.size() + 1);
+    if (!t.h_boxes.empty())
+        PK_CUDA(cudaMemcpyAsync(t.boxes.p, t.h_boxes.data(), sizeof(int) * t.h_boxes.size(), cudaMemcpyHostToDevice, s));
+    if (!tiles.empty())
+        PK_CUDA(cudaMemcpyAsync(t.tiles.p, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
+    PK_CUDA(cudaMemcpyAsync(t.class_ops.p, class_ops.data(), sizeof(int) * class_ops.size(), cudaMemcpyHostToDevice, s));
+    PK_CUDA(cudaStreamSynchronize(s));  // host vectors are about to go out of scope
+}
+
+static void upload_list(DBuf<int> &d, const std::vector<int> &v, cudaStream_t s) {
+    d.reserve(v.size() + 1);
+    if (!v.empty()) PK_CUDA(cudaMemcpyAsync(d.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
+}
+
+void build_tasks(Plan &P, cudaStream_t s) {
+    Tree &t = P.tree;
+    int nb = t.nbox;
+    HostTree H;
+    H.bpos.resize(nb);
+    H.child.resize((size_t)nb * 8);
+    H.parent.resize(nb);
+    H.sr.resize(nb);
+    H.tr.resize(nb);
+    PK_CUDA(cudaMemcpyAsync(H.bpos.data(), t.bpos.p, sizeof(int4) * nb, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaMemcpyAsync(H.child.data(), t.child.p, sizeof(int) * 8 * (size_t)nb, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaMemcpyAsync(H.parent.data(), t.parent.p, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaMemcpyAsync(H.sr.data(), t.srange.p, sizeof(int2) * nb, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaMemcpyAsync(H.tr.data(), t.trange.p, sizeof(int2) * nb, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaStreamSynchronize(s));
+    const int nr = P.nrhs;
+    std::vector<int> leaves_src, leaves_trg;
+    t.nleaf = 0;
+    for (int b = 0; b < nb; b++) {
+        if (!H.leaf(b)) continue;
+        t.nleaf++;
+        if (H.has_src(b)) leaves_src.push_back(b);
+        if (H.has_trg(b)) leaves_trg.push_back(b);
+    }
+    P.n_leaves_src = (int)leaves_src.size();
+    P.n_leaves_trg = (int)leaves_trg.size();
+    upload_list(P.leaves_src, leaves_src, s);
+    upload_list(P.leaves_trg, leaves_trg, s);
+    // X-list boxes (with targets and a non-empty X list)
+    std::vector<int> xptr(nb + 1);
+    PK_CUDA(cudaMemcpyAsync(xptr.data(), t.x_ptr.p, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> xb;
+    for (int b = 0; b < nb; b++)
+        if (xptr[b + 1] > xptr[b] && H.has_trg(b)) xb.push_back(b);
+    P.n_xboxes = (int)xb.size();
+    upload_list(P.xboxes, xb, s);
+
+    bool mixed = P.precision == PKIFMM_MIXED;
+    // UC2E over leaves with sources
+    make_task(P.t_uc2e, {leaves_src}, 1, {0}, nr, s);
+    // M2M per level: non-leaf boxes with sources
+    int depth = (int)t.lvl_begin.size() - 1;
+    P.t_m2m.resize(depth);
+    std::vector<int> ops8(8);
+    for (int c = 0; c < 8; c++) ops8[c] = c;
+    for (int l = 0; l < depth; l++) {
+        std::vector<int> v;
+        for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
+            if (!H.leaf(b) && H.has_src(b)) v.push_back(b);
+        make_task(P.t_m2m[l], {v}, 8, ops8, nr, s);
+    }
+    // root
+    make_task(P.t_root, {{0}}, 1, {0}, nr, s);
+    // M2L: boxes of level >= 1 with targets, by octant class
+    std::vector<std::vector<int>> byc(8);
+    for (int b = 1; b < nb; b++)
+        if (H.has_trg(b)) byc[H.octant(b)].push_back(b);
+    std::vector<int> cls_op(8 * kVSlots);
+    PK_CUDA(cudaMemcpy(cls_op.data(), P.class_slot_op.p, sizeof(int) * cls_op.size(), cudaMemcpyDeviceToHost));
+    make_task(P.t_m2l, byc, kVSlots, cls_op, nr, s);
+    // DC2E over boxes with targets (root separately in binary64 for MIXED)
+    std::vector<int> dc;
+    for (int b = (mixed ? 1 : 0); b < nb; b++)
+        if (H.has_trg(b)) dc.push_back(b);
+    make_task(P.t_dc2e, {dc}, 1, {0}, nr, s);
+    // L2L per level >= 1, by octant class
+    P.t_l2l.resize(depth);
+    for (int l = 1; l < depth; l++) {
+        std::vector<std::vector<int>> bc(8);
+        for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
+            if (H.has_trg(b)) bc[H.octant(b)].push_back(b);
+        make_task(P.t_l2l[l], bc, 1, ops8, nr, s);
+    }
+}
+
+template <typename T>
+static void gemm(const Task &t, const int *slot_table, int slot_stride, const T *ops, long long op_stride,
+                 const T *src, T *dst, int kn, int nrhs, int beta, cudaStream_t s) {
+    if (t.ntiles == 0) return;
+    dim3 grid(t.ntiles, (kn + GB_N - 1) / GB_N);
+    k_slot_gemm<T><<<grid, 256, 0, s>>>(t.boxes.p, t.tiles.p, slot_table, slot_stride, t.nslots, t.class_ops.p,
+                                        ops, op_stride, src, dst, kn, nrhs, beta);
+}
+
+// ---------------- kernel sums ----------------
+
+template <typename T>
+struct V4 { T x, y, z, w; };
+
+__device__ __forceinline__ double exp2i(int l) { return ldexp(1.0, -l); }
+
+// leaf-relative coordinates: rel[i] = x[i] - centre(leaf)
+template <typename T>
+__global__ void k_relcoords(const int *__restrict__ leaves, const int4 *__restrict__ bpos,
+                            const int2 *__restrict__ range, const double *__restrict__ x, V4<T> *__restrict__ rel) {
+    int b = leaves[blockIdx.x];
+    int4 p = bpos[b];
+    double h = exp2i(p.w), c[3] = {(p.x + 0.5) * h, (p.y + 0.5) * h, (p.z + 0.5) * h};
+    int2 r = range[b];
+    for (int i = r.x + threadIdx.x; i < r.y; i += blockDim.x) {
+        V4<T> v;
+        v.x = (T)(x[3 * (long long)i] - c[0]);
+        v.y = (T)(x[3 * (long long)i + 1] - c[1]);
+        v.z = (T)(x[3 * (long long)i + 2] - c[2]);
+        v.w = (T)0;
+        rel[i] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_cast(const double *__restrict__ a, T *__restrict__ b, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (T)a[i];
+}
+
+constexpr int KS_T = 128;  // threads of the kernel-sum blocks
+
+// S2M: q~u[B][rhs][i] = h sum_{s in B} K(1.475 h g_i - yrel_s) phi_s
+template <typename T, int K>
+__global__ void __launch_bounds__(KS_T) k_s2m(const int *__restrict__ leaves, const int4 *__restrict__ bpos,
+                                              const int2 *__restrict__ srange, const V4<T> *__restrict__ yrel,
+                                              const T *__restrict__ dens, int nrhs, int rhs,
+                                              const T *__restrict__ g, int n, T *__restrict__ chk) {
+    __shared__ T sy[KS_T][3], sphi[KS_T][K];
+    const int b = leaves[blockIdx.x];
+    const int4 p = bpos[b];
+    const T h = (T)exp2i(p.w), sc = (T)1.475 * h;
+    const int2 r = srange[b];
+    const int kn = n * K;
+    for (int i0 = 0; i0 < n; i0 += KS_T) {
+        int i = i0 + threadIdx.x;
+        T x[3] = {0, 0, 0};
+        if (i < n) {
+            x[0] = sc * g[3 * i];
+            x[1] = sc * g[3 * i + 1];
+            x[2] = sc * g[3 * i + 2];
+        }
+        T acc[K];
+#pragma unroll
+        for (int a = 0; a < K; a++) acc[a] = 0;
+        for (int s0 = r.x; s0 < r.y; s0 += KS_T) {
+            __syncthreads();
+            int s = s0 + threadIdx.x;
+            if (s < r.y) {
+                V4<T> v = yrel[s];
+                sy[threadIdx.x][0] = v.x;
+                sy[threadIdx.x][1] = v.y;
+                sy[threadIdx.x][2] = v.z;
+#pragma unroll
+                for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = dens[(long long)s * nrhs * K + rhs * K + a];
+            }
+            __syncthreads();
+            int m = min(KS_T, r.y - s0);
+            for (int j = 0; j < m; j++) Kern<T, K>::add(acc, x[0] - sy[j][0], x[1] - sy[j][1], x[2] - sy[j][2], sphi[j]);
+        }
+        if (i < n) {
+#pragma unroll
+            for (int a = 0; a < K; a++) chk[((long long)b * nrhs + rhs) * kn + i * K + a] = h * acc[a];
+        }
+    }
+}
+
+__device__ __forceinline__ void decode_shift(unsigned char c, int sh[3]) {
+    sh[0] = c / 9 - 1;
+    sh[1] = (c / 3) % 3 - 1;
+    sh[2] = c % 3 - 1;
+}
+
+// offset (c_B - c_A - p) between box centres, exact dyadic
+__device__ __forceinline__ void centre_offset(int4 B, int4 A, const int sh[3], double off[3]) {
+    double hb = exp2i(B.w), ha = exp2i(A.w);
+    off[0] = (B.x + 0.5) * hb - (A.x + 0.5) * ha - sh[0];
+    off[1] = (B.y + 0.5) * hb - (A.y + 0.5) * ha - sh[1];
+    off[2] = (B.z + 0.5) * hb - (A.z + 0.5) * ha - sh[2];
+}
+
+// X list: q~d[B][rhs][i] += h_B sum_{(A,p) in X(B)} sum_{s in A} K(0.525 h_B g_i - yrel_s + off) phi_s
+template <typename T, int K>
+__global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, const int4 *__restrict__ bpos,
+                                              const int2 *__restrict__ srange, const int *__restrict__ xptr,
+                                              const int *__restrict__ xbox, const unsigned char *__restrict__ xsh,
+                                              const V4<T> *__restrict__ yrel, const T *__restrict__ dens, int nrhs,
+                                              int rhs, const T *__restrict__ g, int n, T *__restrict__ chk) {
+    __shared__ T sy[KS_T][3], sphi[KS_T][K];
+    const int b = boxes[blockIdx.x];
+    const int4 B = bpos[b];
+    const T h = (T)exp2i(B.w), sc = (T)0.525 * h;
+    const int kn = n * K;
+    for (int i0 = 0; i0 < n; i0 += KS_T) {
+        int i = i0 + threadIdx.x;
+        T x[3] = {0, 0, 0};
+        if (i < n) {
+            x[0] = sc * g[3 * i];
+            x[1] = sc * g[3 * i + 1];
+            x[2] = sc * g[3 * i + 2];
+        }
+        T acc[K];
+#pragma unroll
+        for (int a = 0; a < K; a++) acc[a] = 0;
+        for (int e = xptr[b]; e < xptr[b + 1]; e++) {
+            int A = xbox[e], sh[3];
+            decode_shift(xsh[e], sh);
+            double off[3];
+            centre_offset(B, bpos[A], sh, off);
+            T o0 = (T)off[0], o1 = (T)off[1], o2 = (T)off[2];
+            int2 r = srange[A];
+            for (int s0 = r.x; s0 < r.y; s0 += KS_T) {
+                __syncthreads();
+                int s = s0 + threadIdx.x;
+                if (s < r.y) {
+                    V4<T> v = yrel[s];
+                    sy[threadIdx.x][0] = v.x;
+                    sy[threadIdx.x][1] = v.y;
+                    sy[threadIdx.x][2] = v.z;
+#pragma unroll
+                    for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = dens[(long long)s * nrhs * K + rhs * K + a];
+                }
+                __syncthreads();
+                int m = min(KS_T, r.y - s0);
+                for (int j = 0; j < m; j++)
+                    Kern<T, K>::add(acc, x[0] - sy[j][0] + o0, x[1] - sy[j][1] + o1, x[2] - sy[j][2] + o2, sphi[j]);
+            }
+        }
+        if (i < n) {
+#pragma unroll
+            for (int a = 0; a < K; a++) chk[((long long)b * nrhs + rhs) * kn + i * K + a] += h * acc[a];
+        }
+    }
+}
+
+// Leaf: L2T + W-list M2T + U-list P2P for the targets of one leaf.
+// Each source tile's partial sum is added to the running total with
+// Kahan compensation.
+template <typename T, int K>
+__global__ void __launch_bounds__(KS_T) k_leaf(
+    const int *__restrict__ leaves, const int4 *__restrict__ bpos, const int2 *__restrict__ srange,
+    const int2 *__restrict__ trange, const int *__restrict__ uptr, const int *__restrict__ ubox,
+    const unsigned char *__restrict__ ush, const int *__restrict__ wptr, const int *__restrict__ wbox,
+    const unsigned char *__restrict__ wsh, const V4<T> *__restrict__ yrel, const V4<T> *__restrict__ xrel,
+    const T *__restrict__ dens, const T *__restrict__ up, const T *__restrict__ dn, int nrhs, int rhs,
+    const T *__restrict__ g, int n, double *__restrict__ pot) {
+    __shared__ T sy[KS_T][3], sphi[KS_T][K];
+    const int b = leaves[blockIdx.x];
+    const int4 B = bpos[b];
+    const T h = (T)exp2i(B.w);
+    const int2 tr = trange[b];
+    const int kn = n * K;
+    for (int t0 = tr.x; t0 < tr.y; t0 += KS_T) {
+        int t = t0 + threadIdx.x;
+        T x[3] = {0, 0, 0};
+        if (t < tr.y) {
+            V4<T> v = xrel[t];
+            x[0] = v.x;
+            x[1] = v.y;
+            x[2] = v.z;
+        }
+        T tot[K], cmp[K], acc[K];
+#pragma unroll
+        for (int a = 0; a < K; a++) tot[a] = cmp[a] = 0;
+        auto flush = [&]() {
+#pragma unroll
+            for (int a = 0; a < K; a++) {
+                T y = acc[a] - cmp[a], s = tot[a] + y;
+                cmp[a] = (s - tot[a]) - y;
+                tot[a] = s;
+                acc[a] = 0;
+            }
+        };
+#pragma unroll
+        for (int a = 0; a < K; a++) acc[a] = 0;
+        // L2T from the downward equivalent surface (edge 2.95 h)
+        {
+            const T sc = (T)1.475 * h;
+            const T *phi = dn + ((long long)b * nrhs + rhs) * kn;
+            for (int j0 = 0; j0 < n; j0 += KS_T) {
+                __syncthreads();
+                int j = j0 + threadIdx.x;
+                if (j < n) {
+                    sy[threadIdx.x][0] = sc * g[3 * j];
+                    sy[threadIdx.x][1] = sc * g[3 * j + 1];
+                    sy[threadIdx.x][2] = sc * g[3 * j + 2];
+#pragma unroll
+                    for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = phi[j * K + a];
+                }
+                __syncthreads();
+                int m = min(KS_T, n - j0);
+                for (int jj = 0; jj < m; jj++)
+                    Kern<T, K>::add(acc, x[0] - sy[jj][0], x[1] - sy[jj][1], x[2] - sy[jj][2], sphi[jj]);
+                flush();
+            }
+        }
+        // W list: upward equivalent surfaces (edge 1.05 h_A) of finer boxes
+        for (int e = wptr[b]; e < wptr[b + 1]; e++) {
+            int A = wbox[e], sh[3];
+            decode_shift(wsh[e], sh);
+            int4 Ap = bpos[A];
+            double off[3];
+            centre_offset(B, Ap, sh, off);
+            const T o0 = (T)off[0], o1 = (T)off[1], o2 = (T)off[2];
+            const T sc = (T)(0.525 * exp2i(Ap.w));
+            const T *phi = up + ((long long)A * nrhs + rhs) * kn;
+            for (int j0 = 0; j0 < n; j0 += KS_T) {
+                __syncthreads();
+                int j = j0 + threadIdx.x;
+                if (j < n) {
+                    sy[threadIdx.x][0] = sc * g[3 * j];
+                    sy[threadIdx.x][1] = sc * g[3 * j + 1];
+                    sy[threadIdx.x][2] = sc * g[3 * j + 2];
+#pragma unroll
+                    for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = phi[j * K + a];
+                }
+                __syncthreads();
+                int m = min(KS_T, n - j0);
+                for (int jj = 0; jj < m; jj++)
+                    Kern<T, K>::add(acc, x[0] - sy[jj][0] + o0, x[1] - sy[jj][1] + o1, x[2] - sy[jj][2] + o2,
+                                    sphi[jj]);
+                flush();
+            }
+        }
+        // U list: direct sums, periodic images through the shift
+        for (int e = uptr[b]; e < uptr[b + 1]; e++) {
+            int A = ubox[e], sh[3];
+            decode_shift(ush[e], sh);
+            double off[3];
+            centre_offset(B, bpos[A], sh, off);
+            const T o0 = (T)off[0], o1 = (T)off[1], o2 = (T)off[2];
+            int2 r = srange[A];
+            for (int s0 = r.x; s0 < r.y; s0 += KS_T) {
+                __syncthreads();
+                int s = s0 + threadIdx.x;
+                if (s < r.y) {
+                    V4<T> v = yrel[s];
+                    sy[threadIdx.x][0] = v.x;
+                    sy[threadIdx.x][1] = v.y;
+                    sy[threadIdx.x][2] = v.z;
+#pragma unroll
+                    for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = dens[(long long)s * nrhs * K + rhs * K + a];
+                }
+                __syncthreads();
+                int m = min(KS_T, r.y - s0);
+                for (int j = 0; j < m; j++)
+                    Kern<T, K>::add(acc, x[0] - sy[j][0] + o0, x[1] - sy[j][1] + o1, x[2] - sy[j][2] + o2, sphi[j]);
+                flush();
+            }
+        }
+        if (t < tr.y) {
+#pragma unroll
+            for (int a = 0; a < K; a++) pot[(long long)t * nrhs * K + rhs * K + a] = (double)tot[a] - (double)cmp[a];
+        }
+    }
+}
+
+// ---------------- passes ----------------
+
+template <typename T>
+struct Bufs;
+template <>
+struct Bufs<double> {
+    static DBuf<double> &up(Plan &P) { return P.up64; }
+    static DBuf<double> &chk(Plan &P) { return P.chk64; }
+    static DBuf<double> &dn(Plan &P) { return P.dn64; }
+    static DBuf<double> &tmp(Plan &P) { return P.tmp64; }
+    static DBuf<double> &yrel(Plan &P) { return P.ysrel64; }
+    static DBuf<double> &xrel(Plan &P) { return P.xtrel64; }
+    static DBuf<double> &g(Plan &P) { return P.g64; }
+    static const double *dens(Plan &P) { return P.dens_s.p; }
+    static const double *uc2e_a(Plan &P) { return P.uc2e_a.p; }
+    static const double *uc2e_b(Plan &P) { return P.uc2e_b.p; }
+    static const double *dc2e_a(Plan &P) { return P.dc2e_a.p; }
+    static const double *dc2e_b(Plan &P) { return P.dc2e_b.p; }
+    static const double *m2m(Plan &P) { return P.m2m.p; }
+    static const double *l2l(Plan &P) { return P.l2l.p; }
+    static const double *m2l(Plan &P) { return P.m2l.p; }
+};
+template <>
+struct Bufs<float> {
+    static DBuf<float> &up(Plan &P) { return P.up32; }
+    static DBuf<float> &chk(Plan &P) { return P.chk32; }
+    static DBuf<float> &dn(Plan &P) { return P.dn32; }
+    static DBuf<float> &tmp(Plan &P) { return P.tmp32; }
+    static DBuf<float> &yrel(Plan &P) { return P.ysrel32; }
+    static DBuf<float> &xrel(Plan &P) { return P.xtrel32; }
+    static DBuf<float> &g(Plan &P) { return P.g32; }
+    static const float *dens(Plan &P) { return P.dens32.p; }
+    static const float *uc2e_a(Plan &P) { return P.uc2e_a32.p; }
+    static const float *uc2e_b(Plan &P) { return P.uc2e_b32.p; }
+    static const float *dc2e_a(Plan &P) { return P.dc2e_a32.p; }
+    static const float *dc2e_b(Plan &P) { return P.dc2e_b32.p; }
+    static const float *m2m(Plan &P) { return P.m2m32.p; }
+    static const float *l2l(Plan &P) { return P.l2l32.p; }
+    static const float *m2l(Plan &P) { return P.m2l32.p; }
+};
+
+template <typename T>
+static void prepare_points(Plan &P, cudaStream_t s) {
+    using B = Bufs<T>;
+    B::yrel(P).reserve(4 * (P.S + 1));  // V4<T>: 4 values per point
+    B::xrel(P).reserve(4 * (P.T + 1));
+    auto *yr = reinterpret_cast<V4<T> *>(B::yrel(P).p);
+    auto *xr = reinterpret_cast<V4<T> *>(B::xrel(P).p);
+    if (P.n_leaves_src)
+        k_relcoords<T><<<P.n_leaves_src, 128, 0, s>>>(P.leaves_src.p, P.tree.bpos.p, P.tree.srange.p, P.xs.p, yr);
+    if (P.n_leaves_trg)
+        k_relcoords<T><<<P.n_leaves_trg, 128, 0, s>>>(P.leaves_trg.p, P.tree.bpos.p, P.tree.trange.p, P.xt.p, xr);
+    if (sizeof(T) == 4) {
+        long long nd = P.S * P.nrhs * P.k;
+        P.dens32.reserve(nd + 1);
+        if (nd) k_cast<float><<<nblk(nd, 256), 256, 0, s>>>(P.dens_s.p, P.dens32.p, nd);
+    }
+    size_t rows = (size_t)P.tree.nbox * P.nrhs * P.kn;
+    B::up(P).reserve(rows);
+    B::chk(P).reserve(rows);
+    B::dn(P).reserve(rows);
+    B::tmp(P).reserve(rows);
+    PK_CUDA(cudaMemsetAsync(B::up(P).p, 0, sizeof(T) * rows, s));
+    PK_CUDA(cudaMemsetAsync(B::chk(P).p, 0, sizeof(T) * (size_t)P.nrhs * P.kn, s));  // root check
+}
+
+template <typename T, int K>
+static void upward_t(Plan &P, cudaStream_t s) {
+    using B = Bufs<T>;
+    prepare_points<T>(P, s);
+    const int kn = P.kn, nr = P.nrhs;
+    const long long kn2 = (long long)kn * kn;
+    auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
+    if (P.n_leaves_src)
+        for (int r = 0; r < nr; r++)
+            k_s2m<T, K><<<P.n_leaves_src, KS_T, 0, s>>>(P.leaves_src.p, P.tree.bpos.p, P.tree.srange.p, yr, B::dens(P), nr,
+                                                         r, B::g(P).p, P.n, B::chk(P).p);
+    // UC2E: tmp = U^T q~u ; up = (V S+) tmp
+    gemm<T>(P.t_uc2e, nullptr, 1, B::uc2e_b(P), 0, B::chk(P).p, B::tmp(P).p, kn, nr, 0, s);
+    gemm<T>(P.t_uc2e, nullptr, 1, B::uc2e_a(P), 0, B::tmp(P).p, B::up(P).p, kn, nr, 0, s);
+    for (int l = (int)P.t_m2m.size() - 1; l >= 0; l--)
+        gemm<T>(P.t_m2m[l], P.tree.child.p, 8, B::m2m(P), kn2, B::up(P).p, B::up(P).p, kn, nr, 0, s);
+}
+
+void run_upward(Plan &P, cudaStream_t s) {
+    if (P.precision == PKIFMM_FP64) {
+        if (P.k == 1) upward_t<double, 1>(P, s);
+        else upward_t<double, 3>(P, s);
+    } else {
+        if (P.k == 1) upward_t<float, 1>(P, s);
+        else upward_t<float, 3>(P, s);
+    }
+}
+
+template <typename T>
+__global__ void k_f2d(const T *__restrict__ a, double *__restrict__ b, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+// MIXED: the root far field (Algorithm 2 step c) and its check-to-equivalent
+// solve run in binary64 on a binary64 copy of the root's upward density.
+void root_mixed(Plan &P, cudaStream_t s) {
+    const int kn = P.kn, nr = P.nrhs;
+    long long rows = (long long)nr * kn;
+    P.chk64.reserve(rows);
+    P.tmp64.reserve(rows);
+    P.dn64.reserve(rows);
+    P.up64.reserve(rows);
+    if (!P.periodic) {
+        PK_CUDA(cudaMemsetAsync(P.dn32.p, 0, sizeof(float) * rows, s));
+        return;
+    }
+    k_f2d<float><<<nblk(rows, 256), 256, 0, s>>>(P.up32.p, P.up64.p, rows);
+    gemm<double>(P.t_root, nullptr, 1, P.root.p, 0, P.up64.p, P.chk64.p, kn, nr, 0, s);
+    gemm<double>(P.t_root, nullptr, 1, P.dc2e_b.p, 0, P.chk64.p, P.tmp64.p, kn, nr, 0, s);
+    gemm<double>(P.t_root, nullptr, 1, P.dc2e_a.p, 0, P.tmp64.p, P.dn64.p, kn, nr, 0, s);
+    k_cast<float><<<nblk(rows, 256), 256, 0, s>>>(P.dn64.p, P.dn32.p, rows);
+}
+
+void run_root(Plan &P, cudaStream_t s) {
+    if (P.precision == PKIFMM_FP64) {
+        if (P.periodic)
+            gemm<double>(P.t_root, nullptr, 1, P.root.p, 0, P.up64.p, P.chk64.p, P.kn, P.nrhs, 0, s);
+        return;
+    }
+    root_mixed(P, s);
+}
+
+void run_m2l(Plan &P, cudaStream_t s) {
+    const int kn = P.kn, nr = P.nrhs;
+    const long long kn2 = (long long)kn * kn;
+    if (P.precision == PKIFMM_FP64) {
+        gemm<double>(P.t_m2l, P.tree.v_slot.p, kVSlots, P.m2l.p, kn2, P.up64.p, P.chk64.p, kn, nr, 0, s);
+    } else {
+        if (!m2l_tc_run(P, s))
+            gemm<float>(P.t_m2l, P.tree.v_slot.p, kVSlots, P.m2l32.p, kn2, P.up32.p, P.chk32.p, kn, nr, 0, s);
+    }
+}
+
+template <typename T, int K>
+static void downward_t(Plan &P, cudaStream_t s) {
+    using B = Bufs<T>;
+    const int kn = P.kn, nr = P.nrhs;
+    const long long kn2 = (long long)kn * kn;
+    auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
+    if (P.n_xboxes)
+        for (int r = 0; r < nr; r++)
+            k_s2l<T, K><<<P.n_xboxes, KS_T, 0, s>>>(P.xboxes.p, P.tree.bpos.p, P.tree.srange.p, P.tree.x_ptr.p,
+                                                     P.tree.x_box.p, P.tree.x_sh.p, yr, B::dens(P), nr, r, B::g(P).p,
+                                                     P.n, B::chk(P).p);
+    gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_b(P), 0, B::chk(P).p, B::tmp(P).p, kn, nr, 0, s);
+    gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_a(P), 0, B::tmp(P).p, B::dn(P).p, kn, nr, 0, s);
+    for (size_t l = 1; l < P.t_l2l.size(); l++)
+        gemm<T>(P.t_l2l[l], P.tree.parent.p, 1, B::l2l(P), kn2, B::dn(P).p, B::dn(P).p, kn, nr, 1, s);
+}
+
+void run_downward(Plan &P, cudaStream_t s) {
+    if (P.precision == PKIFMM_FP64) {
+        if (P.k == 1) downward_t<double, 1>(P, s);
+        else downward_t<double, 3>(P, s);
+    } else {
+        if (P.k == 1) downward_t<float, 1>(P, s);
+        else downward_t<float, 3>(P, s);
+    }
+}
+
+template <typename T, int K>
+static void leaves_t(Plan &P, cudaStream_t s) {
+    using B = Bufs<T>;
+    const int nr = P.nrhs;
+    P.pot_s.reserve((size_t)P.T * nr * K + 1);
+    auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
+    auto *xr = reinterpret_cast<const V4<T> *>(B::xrel(P).p);
+    if (P.n_leaves_trg)
+        for (int r = 0; r < nr; r++)
+            k_leaf<T, K><<<P.n_leaves_trg, KS_T, 0, s>>>(
+                P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
+                P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
+                B::dn(P).p, nr, r, B::g(P).p, P.n, P.pot_s.p);
+}
+
+void run_leaves(Plan &P, cudaStream_t s) {
+    if (P.precision == PKIFMM_FP64) {
+        if (P.k == 1) leaves_t<double, 1>(P, s);
+        else leaves_t<double, 3>(P, s);
+    } else {
+        if (P.k == 1) leaves_t<float, 1>(P, s);
+        else leaves_t<float, 3>(P, s);
+    }
+}
+
+}  // namespace pk

@@ -1,0 +1,650 @@
+// Octree and interaction lists on the device (Sec. 2.2).
+//
+// Points are normalised to the unit box, wrapped along periodic axes, and
+// given a Morton key of 3*depth_max bits (cell floor(x' 2^D) per axis,
+// octant bits x = 1, y = 2, z = 4).  A stable LSD radix sort orders sources
+// and targets leaf-contiguously with ties in input order.  The adaptive tree
+// is built top down one level at a time: a box splits while it holds more
+// than s sources or more than s targets (s = leaf_max) and its level is
+// below depth_max; empty children are not created.  The same tree serves
+// B0 and its periodic images ("copy-and-paste", Sec. 2.2): list entries are
+// (box, shift) pairs, the shift in {-1,0,1}^3 naming the image.
+//
+// Lists (standard KIFMM definitions; the paper defers to them):
+//   U(B), B leaf: leaves A with A+p adjacent to B, and B itself;
+//   V(B): children of colleagues of parent(B) not adjacent to B, stored as a
+//         dense table of 189 slots per box (slot = offset within the octant
+//         class of B);
+//   W(B), B leaf: boxes A+p finer than B, not adjacent, parent(A)+p adjacent;
+//   X(B): leaves A+p coarser than B, adjacent to parent(B), not adjacent to B.
+#include "internal.h"
+
+namespace pk {
+
+// ---------------- helpers ----------------
+
+__host__ __device__ inline unsigned long long spread3(unsigned v) {
+    unsigned long long x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffULL;
+    x = (x | x << 16) & 0x1f0000ff0000ffULL;
+    x = (x | x << 8) & 0x100f00f00f00f00fULL;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+    x = (x | x << 2) & 0x1249249249249249ULL;
+    return x;
+}
+
+__host__ __device__ inline unsigned long long morton3(int x, int y, int z) {
+    return spread3((unsigned)x) | spread3((unsigned)y) << 1 | spread3((unsigned)z) << 2;
+}
+
+__device__ inline int floor_div(int a, int n) {  // n > 0
+    return a >= 0 ? a / n : -((-a + n - 1) / n);
+}
+
+static inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------- scan (exclusive, out[n] = total) ----------------
+
+__global__ void k_scan_block(const int *in, int *out, int *bsum, int n) {
+    __shared__ int s[1024];
+    int i = blockIdx.x * 1024 + threadIdx.x;
+    int v = i < n ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = s[threadIdx.x] - v;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = s[1023];
+}
+
+__global__ void k_scan_add(int *out, const int *boff, int n, int *total_out) {
+    int i = blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) out[i] += boff[blockIdx.x];
+    if (i == n - 1 && total_out) *total_out = out[i];
+}
+
+__global__ void k_scan_fix_total(int *out, const int *in, int n) {
+    out[n] = (n ? out[n - 1] + in[n - 1] : 0);
+}
+
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total.  Returns the
+// total (synchronises the stream).
+int exclusive_scan(const int *in, int *out, int n, cudaStream_t s) {
+    if (n <= 0) {
+        PK_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
+        return 0;
+    }
+    int nb = (n + 1023) / 1024;
+    int *bsum = nullptr, *boff = nullptr;
+    PK_CUDA(cudaMallocAsync(&bsum, sizeof(int) * (nb + 1), s));
+    PK_CUDA(cudaMallocAsync(&boff, sizeof(int) * (nb + 1), s));
+    k_scan_block<<<nb, 1024, 0, s>>>(in, out, bsum, n);
+    if (nb > 1) {
+        exclusive_scan(bsum, boff, nb, s);
+        k_scan_add<<<nb, 1024, 0, s>>>(out, boff, n, nullptr);
+    }
+    k_scan_fix_total<<<1, 1, 0, s>>>(out, in, n);
+    int total = 0;
+    PK_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaFreeAsync(bsum, s));
+    PK_CUDA(cudaFreeAsync(boff, s));
+    PK_CUDA(cudaStreamSynchronize(s));
+    return total;
+}
+
+// ---------------- keys ----------------
+
+// err[0]: NaN/inf coordinate, err[1]: point outside [0,1) along a free axis.
+__global__ void k_keys(const double *__restrict__ xyz, long long n, double lo0, double lo1, double lo2,
+                       double L, unsigned per, int D, double *__restrict__ xn,
+                       unsigned long long *__restrict__ key, int *__restrict__ idx, int *err) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double lo[3] = {lo0, lo1, lo2};
+    int c[3];
+    double sc = (double)(1 << D);
+    for (int a = 0; a < 3; a++) {
+        double x = __ddiv_rn(__dsub_rn(xyz[3 * i + a], lo[a]), L);
+        if (!isfinite(x)) {
+            err[0] = 1;
+            x = 0.0;
+        }
+        if (per >> a & 1) {
+            x = __dsub_rn(x, floor(x));
+            if (x >= 1.0) x = 0.0;
+        } else if (x < 0.0 || x >= 1.0) {
+            err[1] = 1;
+            x = fmin(fmax(x, 0.0), 0.0);
+        }
+        xn[3 * i + a] = x;
+        int v = (int)floor(__dmul_rn(x, sc));
+        c[a] = min(max(v, 0), (1 << D) - 1);
+    }
+    key[i] = morton3(c[0], c[1], c[2]);
+    idx[i] = (int)i;
+}
+
+// ---------------- stable LSD radix sort, 4-bit digits ----------------
+
+constexpr int RS_T = 256, RS_I = 16, RS_TILE = RS_T * RS_I;
+
+__global__ void k_rs_count(const unsigned long long *__restrict__ key, int n, int shift, int *hist, int nb) {
+    __shared__ int c[16];
+    if (threadIdx.x < 16) c[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * RS_TILE;
+    for (int j = threadIdx.x; j < RS_TILE; j += RS_T) {
+        int i = base + j;
+        if (i < n) atomicAdd(&c[(key[i] >> shift) & 15], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) hist[threadIdx.x * nb + blockIdx.x] = c[threadIdx.x];
+}
+
+__global__ void k_rs_scatter(const unsigned long long *__restrict__ kin, const int *__restrict__ vin,
+                             unsigned long long *__restrict__ kout, int *__restrict__ vout, int n, int shift,
+                             const int *__restrict__ hoff, int nb) {
+    __shared__ int tc[16][RS_T + 1];
+    int t = threadIdx.x, base = blockIdx.x * RS_TILE + t * RS_I;
+    int cnt[16];
+#pragma unroll
+    for (int d = 0; d < 16; d++) cnt[d] = 0;
+    for (int j = 0; j < RS_I; j++) {
+        int i = base + j;
+        if (i < n) cnt[(kin[i] >> shift) & 15]++;
+    }
+#pragma unroll
+    for (int d = 0; d < 16; d++) tc[d][t] = cnt[d];
+    __syncthreads();
+    if (t < 16) {
+        int run = hoff[t * nb + blockIdx.x];
+        for (int u = 0; u < RS_T; u++) {
+            int v = tc[t][u];
+            tc[t][u] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int d = 0; d < 16; d++) cnt[d] = tc[d][t];
+    for (int j = 0; j < RS_I; j++) {
+        int i = base + j;
+        if (i < n) {
+            unsigned long long k = kin[i];
+            int d = (k >> shift) & 15, pos = 0;
+#pragma unroll
+            for (int e = 0; e < 16; e++)
+                if (e == d) pos = cnt[e]++;
+            kout[pos] = k;
+            vout[pos] = vin[i];
+        }
+    }
+}
+
+// Sort (key, idx) by key (bits [0, bits)), stable.  Result in (k, v).
+static void radix_sort(DBuf<unsigned long long> &k, DBuf<int> &v, DBuf<unsigned long long> &k2, DBuf<int> &v2,
+                       DBuf<int> &hist, int n, int bits, cudaStream_t s) {
+    if (n <= 1) return;
+    int nb = (n + RS_TILE - 1) / RS_TILE;
+    hist.reserve((size_t)16 * nb * 2 + 2);
+    k2.reserve(n);
+    v2.reserve(n);
+    unsigned long long *ka = k.p, *kb = k2.p;
+    int *va = v.p, *vb = v2.p;
+    int *h = hist.p, *ho = hist.p + 16 * nb + 1;
+    for (int sh = 0; sh < bits; sh += 4) {
+        k_rs_count<<<nb, RS_T, 0, s>>>(ka, n, sh, h, nb);
+        exclusive_scan(h, ho, 16 * nb, s);
+        k_rs_scatter<<<nb, RS_T, 0, s>>>(ka, va, kb, vb, n, sh, ho, nb);
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != k.p) {
+        PK_CUDA(cudaMemcpyAsync(k.p, ka, sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, s));
+        PK_CUDA(cudaMemcpyAsync(v.p, va, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    }
+}
+
+__global__ void k_gather3(const double *__restrict__ xn, const int *__restrict__ idx, long long n,
+                          double *__restrict__ out) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int j = idx[i];
+    out[3 * i] = xn[3 * (long long)j];
+    out[3 * i + 1] = xn[3 * (long long)j + 1];
+    out[3 * i + 2] = xn[3 * (long long)j + 2];
+}
+
+// dens [nrhs][S][k] (input order) -> dens_s [S][nrhs*k] (sorted)
+__global__ void k_gather_dens(const double *__restrict__ dens, const int *__restrict__ idx, long long S,
+                              int nrhs, int k, double *__restrict__ out) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= S * nrhs * k) return;
+    long long s = i / (nrhs * k);
+    int rem = (int)(i % (nrhs * k)), r = rem / k, a = rem % k;
+    out[i] = dens[((long long)r * S + idx[s]) * k + a];
+}
+
+// ---------------- tree ----------------
+
+__device__ inline int lower_bound_key(const unsigned long long *key, int lo, int hi, unsigned long long v) {
+    while (lo < hi) {
+        int m = (lo + hi) >> 1;
+        if (key[m] < v) lo = m + 1;
+        else hi = m;
+    }
+    return lo;
+}
+
+__global__ void k_root(unsigned long long *key, int4 *bpos, int *parent, int2 *sr, int2 *tr, int S, int T) {
+    key[0] = 0;
+    bpos[0] = make_int4(0, 0, 0, 0);
+    parent[0] = -1;
+    sr[0] = make_int2(0, S);
+    tr[0] = make_int2(0, T);
+}
+
+__global__ void k_split(int lb, int le, int level, int D, int smax, const unsigned long long *__restrict__ bkey,
+                        const int2 *__restrict__ srange, const int2 *__restrict__ trange,
+                        const unsigned long long *__restrict__ keyS, const unsigned long long *__restrict__ keyT,
+                        int2 *csr, int2 *ctr, int *cnt) {
+    int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= le) return;
+    int2 sr = srange[b], tr = trange[b];
+    int count = 0;
+    if ((sr.y - sr.x > smax || tr.y - tr.x > smax) && level < D) {
+        int sh = 3 * (D - level - 1);
+        unsigned long long pk = bkey[b];
+        for (int c = 0; c < 8; c++) {
+            unsigned long long ck = pk * 8 + c;
+            unsigned long long lo = ck << sh, hi = (ck + 1) << sh;
+            int s0 = lower_bound_key(keyS, sr.x, sr.y, lo), s1 = lower_bound_key(keyS, s0, sr.y, hi);
+            int t0 = lower_bound_key(keyT, tr.x, tr.y, lo), t1 = lower_bound_key(keyT, t0, tr.y, hi);
+            csr[(b - lb) * 8 + c] = make_int2(s0, s1);
+            ctr[(b - lb) * 8 + c] = make_int2(t0, t1);
+            if (s1 > s0 || t1 > t0) count++;
+        }
+    }
+    cnt[b - lb] = count;
+}
+
+__global__ void k_emit(int lb, int le, const int *__restrict__ cnt, const int *__restrict__ off,
+                       const int2 *__restrict__ csr, const int2 *__restrict__ ctr, unsigned long long *bkey,
+                       int4 *bpos, int *parent, int *child, int2 *srange, int2 *trange) {
+    int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= le) return;
+    for (int c = 0; c < 8; c++) child[(long long)b * 8 + c] = -1;
+    if (cnt[b - lb] == 0) return;
+    int j = le + off[b - lb];
+    int4 p = bpos[b];
+    for (int c = 0; c < 8; c++) {
+        int2 s = csr[(b - lb) * 8 + c], t = ctr[(b - lb) * 8 + c];
+        if (s.y <= s.x && t.y <= t.x) continue;
+        bkey[j] = bkey[b] * 8 + c;
+        bpos[j] = make_int4(2 * p.x + (c & 1), 2 * p.y + (c >> 1 & 1), 2 * p.z + (c >> 2 & 1), p.w + 1);
+        parent[j] = b;
+        srange[j] = s;
+        trange[j] = t;
+        child[(long long)b * 8 + c] = j;
+        j++;
+    }
+}
+
+void build_tree(Plan &P, cudaStream_t s) {
+    Tree &t = P.tree;
+    const int D = P.depth_max;
+    size_t cap = 1024;
+    t.key.grow_keep(cap, 0, s);
+    t.bpos.grow_keep(cap, 0, s);
+    t.parent.grow_keep(cap, 0, s);
+    t.child.grow_keep(cap * 8, 0, s);
+    t.srange.grow_keep(cap, 0, s);
+    t.trange.grow_keep(cap, 0, s);
+    k_root<<<1, 1, 0, s>>>(t.key.p, t.bpos.p, t.parent.p, t.srange.p, t.trange.p, (int)P.S, (int)P.T);
+    t.lvl_begin.assign({0, 1});
+    int level = 0;
+    for (;; level++) {
+        int lb = t.lvl_begin[level], le = t.lvl_begin[level + 1], nl = le - lb;
+        P.csr.reserve((size_t)nl * 8);
+        P.ctr.reserve((size_t)nl * 8);
+        P.cnt.reserve(nl + 1);
+        P.off.reserve(nl + 1);
+        k_split<<<blocks(nl, 128), 128, 0, s>>>(lb, le, level, D, P.leaf_max, t.key.p, t.srange.p, t.trange.p,
+                                                 P.keyS.p, P.keyT.p, P.csr.p, P.ctr.p, P.cnt.p);
+        int total = exclusive_scan(P.cnt.p, P.off.p, nl, s);
+        size_t need = (size_t)le + total;
+        t.key.grow_keep(need, le, s);
+        t.bpos.grow_keep(need, le, s);
+        t.parent.grow_keep(need, le, s);
+        t.child.grow_keep(need * 8, (size_t)le * 8, s);
+        t.srange.grow_keep(need, le, s);
+        t.trange.grow_keep(need, le, s);
+        k_emit<<<blocks(nl, 128), 128, 0, s>>>(lb, le, P.cnt.p, P.off.p, P.csr.p, P.ctr.p, t.key.p, t.bpos.p,
+                                                t.parent.p, t.child.p, t.srange.p, t.trange.p);
+        if (total == 0) break;
+        t.lvl_begin.push_back(le + total);
+    }
+    t.depth = level;
+    t.nbox = t.lvl_begin.back();
+    t.lvl_begin_d.reserve(t.lvl_begin.size());
+    PK_CUDA(cudaMemcpyAsync(t.lvl_begin_d.p, t.lvl_begin.data(), sizeof(int) * t.lvl_begin.size(),
+                            cudaMemcpyHostToDevice, s));
+}
+
+// ---------------- lists ----------------
+
+struct TreeView {
+    const unsigned long long *key;
+    const int4 *bpos;
+    const int *child;
+    const int *parent;
+    const int2 *srange, *trange;
+    const int *lvlb;
+    int nlevel;
+    unsigned per;
+};
+
+__device__ inline int lookup(const TreeView &tv, int level, const int w[3]) {
+    if (level >= tv.nlevel) return -1;
+    unsigned long long k = morton3(w[0], w[1], w[2]);
+    int lo = tv.lvlb[level], hi = tv.lvlb[level + 1];
+    int i = lower_bound_key(tv.key, lo, hi, k);
+    return (i < hi && tv.key[i] == k) ? i : -1;
+}
+
+// wrap extended position e at `level`; false if outside along a free axis
+__device__ inline bool wrap_pos(unsigned per, int level, const int e[3], int w[3], int sh[3]) {
+    int n = 1 << level;
+    for (int a = 0; a < 3; a++) {
+        if (per >> a & 1) {
+            sh[a] = floor_div(e[a], n);
+            w[a] = e[a] - sh[a] * n;
+        } else {
+            if (e[a] < 0 || e[a] >= n) return false;
+            sh[a] = 0;
+            w[a] = e[a];
+        }
+    }
+    return true;
+}
+
+__device__ inline bool is_leaf(const TreeView &tv, int b) {
+    const int *c = tv.child + (long long)b * 8;
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+        if (c[i] >= 0) return false;
+    return true;
+}
+
+// closed boxes touch with disjoint interiors; A shifted by sh (unit boxes)
+__device__ inline bool adjacent(int4 A, const int sh[3], int4 B) {
+    int lm = max(A.w, B.w), fa = 1 << (lm - A.w), fb = 1 << (lm - B.w);
+    int pa[3] = {A.x, A.y, A.z}, pb[3] = {B.x, B.y, B.z};
+    bool touch = true, inner = true;
+    for (int a = 0; a < 3; a++) {
+        int alo = (pa[a] + sh[a] * (1 << A.w)) * fa, ahi = alo + fa;
+        int blo = pb[a] * fb, bhi = blo + fb;
+        touch &= (alo <= bhi && blo <= ahi);
+        inner &= (alo < bhi && blo < ahi);
+    }
+    return touch && !inner;
+}
+
+struct ListOut {
+    int *u_box, *w_box, *x_box;
+    unsigned char *u_sh, *w_sh, *x_sh;
+    const int *u_ptr, *w_ptr, *x_ptr;
+    int *u_cnt, *w_cnt, *x_cnt;
+    int *v_slot;
+    const signed char *slot_of;
+    unsigned long long *pairs;
+};
+
+__device__ inline unsigned char code3(const int sh[3]) {
+    return (unsigned char)((sh[0] + 1) * 9 + (sh[1] + 1) * 3 + (sh[2] + 1));
+}
+
+// first existing ancestor (level < l) of extended position e at level l
+__device__ int coarse_ancestor(const TreeView &tv, int l, const int e[3], int sh[3]) {
+    for (int l2 = l - 1; l2 >= 0; l2--) {
+        int e2[3], w2[3];
+        for (int a = 0; a < 3; a++) e2[a] = e[a] >> (l - l2);  // arithmetic shift = floor division
+        if (!wrap_pos(tv.per, l2, e2, w2, sh)) return -1;
+        int a = lookup(tv, l2, w2);
+        if (a >= 0) return is_leaf(tv, a) ? a : -1;
+    }
+    return -1;
+}
+
+__global__ void k_lists(TreeView tv, int nbox, int pass, ListOut o) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int4 B = tv.bpos[b];
+    int l = B.w;
+    int pos[3] = {B.x, B.y, B.z};
+    int nU = 0, nW = 0, nX = 0;
+    int uo = pass ? o.u_ptr[b] : 0, wo = pass ? o.w_ptr[b] : 0, xo = pass ? o.x_ptr[b] : 0;
+    unsigned long long pairs = 0;
+    int2 btr = tv.trange[b];
+    if (is_leaf(tv, b)) {
+        int coarse[27];
+        unsigned char ccode[27];
+        int nc = 0;
+        for (int d = 0; d < 27; d++) {
+            int e[3] = {pos[0] + d / 9 - 1, pos[1] + (d / 3) % 3 - 1, pos[2] + d % 3 - 1};
+            int w[3], sh[3];
+            if (!wrap_pos(tv.per, l, e, w, sh)) continue;
+            int nb = lookup(tv, l, w);
+            if (nb >= 0) {
+                if (is_leaf(tv, nb)) {
+                    if (pass) {
+                        o.u_box[uo + nU] = nb;
+                        o.u_sh[uo + nU] = code3(sh);
+                        int2 s = tv.srange[nb];
+                        pairs += (unsigned long long)(s.y - s.x) * (btr.y - btr.x);
+                    }
+                    nU++;
+                } else {
+                    int stack[8 * kMaxLevel + 8];
+                    int top = 0;
+                    for (int c = 0; c < 8; c++) {
+                        int ch = tv.child[(long long)nb * 8 + c];
+                        if (ch >= 0) stack[top++] = ch;
+                    }
+                    while (top > 0) {
+                        int C = stack[--top];
+                        if (adjacent(tv.bpos[C], sh, B)) {
+                            if (is_leaf(tv, C)) {
+                                if (pass) {
+                                    o.u_box[uo + nU] = C;
+                                    o.u_sh[uo + nU] = code3(sh);
+                                    int2 s = tv.srange[C];
+                                    pairs += (unsigned long long)(s.y - s.x) * (btr.y - btr.x);
+                                }
+                                nU++;
+                            } else {
+                                for (int c = 0; c < 8; c++) {
+                                    int ch = tv.child[(long long)C * 8 + c];
+                                    if (ch >= 0 && top < 8 * kMaxLevel + 8) stack[top++] = ch;
+                                }
+                            }
+                        } else {
+                            if (pass) {
+                                o.w_box[wo + nW] = C;
+                                o.w_sh[wo + nW] = code3(sh);
+                            }
+                            nW++;
+                        }
+                    }
+                }
+            } else {
+                int sh2[3];
+                int a = coarse_ancestor(tv, l, e, sh2);
+                if (a < 0) continue;
+                unsigned char cd = code3(sh2);
+                bool dup = false;
+                for (int i = 0; i < nc; i++) dup |= (coarse[i] == a && ccode[i] == cd);
+                if (dup) continue;
+                coarse[nc] = a;
+                ccode[nc++] = cd;
+                if (pass) {
+                    o.u_box[uo + nU] = a;
+                    o.u_sh[uo + nU] = cd;
+                    int2 s = tv.srange[a];
+                    pairs += (unsigned long long)(s.y - s.x) * (btr.y - btr.x);
+                }
+                nU++;
+            }
+        }
+    }
+    if (l >= 1) {
+        int pp[3] = {pos[0] >> 1, pos[1] >> 1, pos[2] >> 1};
+        int cand[27];
+        unsigned char ccode[27];
+        int nc = 0;
+        int cls = (pos[0] & 1) | (pos[1] & 1) << 1 | (pos[2] & 1) << 2;
+        for (int d = 0; d < 27; d++) {
+            int dd[3] = {d / 9 - 1, (d / 3) % 3 - 1, d % 3 - 1};
+            int e[3] = {pp[0] + dd[0], pp[1] + dd[1], pp[2] + dd[2]};
+            int w[3], sh[3];
+            if (!wrap_pos(tv.per, l - 1, e, w, sh)) continue;
+            int a = lookup(tv, l - 1, w);
+            if (a >= 0 && !is_leaf(tv, a)) {
+                // V list: children of this colleague of the parent
+                if (pass) {
+                    for (int c = 0; c < 8; c++) {
+                        int ch = tv.child[(long long)a * 8 + c];
+                        if (ch < 0) continue;
+                        int off[3] = {2 * e[0] + (c & 1) - pos[0], 2 * e[1] + (c >> 1 & 1) - pos[1],
+                                      2 * e[2] + (c >> 2 & 1) - pos[2]};
+                        if (abs(off[0]) <= 1 && abs(off[1]) <= 1 && abs(off[2]) <= 1) continue;
+                        int oi = ((off[0] + 3) * 7 + (off[1] + 3)) * 7 + (off[2] + 3);
+                        int slot = o.slot_of[cls * 343 + oi];
+                        if (slot >= 0) o.v_slot[(long long)b * kVSlots + slot] = ch;
+                    }
+                }
+                continue;
+            }
+            int sh2[3] = {sh[0], sh[1], sh[2]};
+            if (a < 0) a = coarse_ancestor(tv, l - 1, e, sh2);
+            if (a < 0) continue;  // empty region
+            if (adjacent(tv.bpos[a], sh2, B)) continue;
+            unsigned char cd = code3(sh2);
+            bool dup = false;
+            for (int i = 0; i < nc; i++) dup |= (cand[i] == a && ccode[i] == cd);
+            if (dup) continue;
+            cand[nc] = a;
+            ccode[nc++] = cd;
+            if (pass) {
+                o.x_box[xo + nX] = a;
+                o.x_sh[xo + nX] = cd;
+            }
+            nX++;
+        }
+    }
+    if (!pass) {
+        o.u_cnt[b] = nU;
+        o.w_cnt[b] = nW;
+        o.x_cnt[b] = nX;
+    } else if (pairs) {
+        atomicAdd(o.pairs, pairs);
+    }
+}
+
+__global__ void k_count_v(const int *__restrict__ v_slot, long long n, unsigned long long *cnt) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n && v_slot[i] >= 0) atomicAdd(cnt, 1ULL);
+}
+
+void build_lists(Plan &P, cudaStream_t s) {
+    Tree &t = P.tree;
+    int nb = t.nbox;
+    TreeView tv{t.key.p, t.bpos.p, t.child.p, t.parent.p, t.srange.p, t.trange.p, t.lvl_begin_d.p,
+                (int)t.lvl_begin.size() - 1, P.periodic};
+    t.u_ptr.reserve(nb + 1);
+    t.w_ptr.reserve(nb + 1);
+    t.x_ptr.reserve(nb + 1);
+    DBuf<int> cnt3;
+    cnt3.reserve((size_t)3 * nb);
+    t.v_slot.reserve((size_t)nb * kVSlots);
+    PK_CUDA(cudaMemsetAsync(t.v_slot.p, 0xff, sizeof(int) * (size_t)nb * kVSlots, s));
+    DBuf<unsigned long long> pairs;
+    pairs.reserve(2);
+    PK_CUDA(cudaMemsetAsync(pairs.p, 0, sizeof(unsigned long long) * 2, s));
+    ListOut o{};
+    o.u_cnt = cnt3.p;
+    o.w_cnt = cnt3.p + nb;
+    o.x_cnt = cnt3.p + 2 * nb;
+    o.slot_of = P.slot_of.p;
+    k_lists<<<blocks(nb, 128), 128, 0, s>>>(tv, nb, 0, o);
+    t.nU = exclusive_scan(o.u_cnt, t.u_ptr.p, nb, s);
+    t.nW = exclusive_scan(o.w_cnt, t.w_ptr.p, nb, s);
+    t.nX = exclusive_scan(o.x_cnt, t.x_ptr.p, nb, s);
+    t.u_box.reserve(t.nU + 1);
+    t.u_sh.reserve(t.nU + 1);
+    t.w_box.reserve(t.nW + 1);
+    t.w_sh.reserve(t.nW + 1);
+    t.x_box.reserve(t.nX + 1);
+    t.x_sh.reserve(t.nX + 1);
+    o.u_box = t.u_box.p;
+    o.u_sh = t.u_sh.p;
+    o.u_ptr = t.u_ptr.p;
+    o.w_box = t.w_box.p;
+    o.w_sh = t.w_sh.p;
+    o.w_ptr = t.w_ptr.p;
+    o.x_box = t.x_box.p;
+    o.x_sh = t.x_sh.p;
+    o.x_ptr = t.x_ptr.p;
+    o.v_slot = t.v_slot.p;
+    o.pairs = pairs.p;
+    k_lists<<<blocks(nb, 128), 128, 0, s>>>(tv, nb, 1, o);
+    k_count_v<<<blocks((long long)nb * kVSlots, 256), 256, 0, s>>>(t.v_slot.p, (long long)nb * kVSlots,
+                                                                     pairs.p + 1);
+    unsigned long long h[2];
+    PK_CUDA(cudaMemcpyAsync(h, pairs.p, sizeof h, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaStreamSynchronize(s));
+    t.p2p_pairs = (long long)h[0];
+    t.nV = (long long)h[1];
+    cnt3.release();
+    pairs.release();
+}
+
+// ---------------- entry: keys, sort, gather ----------------
+
+void sort_points(Plan &P, const double *src, const double *dens, const double *trg, cudaStream_t s) {
+    const int D = P.depth_max;
+    long long S = P.S, T = P.T;
+    P.err.reserve(4);
+    PK_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int) * 4, s));
+    P.keyS.reserve(S + 1);
+    P.idxS.reserve(S + 1);
+    P.keyT.reserve(T + 1);
+    P.idxT.reserve(T + 1);
+    P.xs.reserve(3 * S + 3);
+    P.xt.reserve(3 * T + 3);
+    DBuf<double> xn;
+    xn.reserve(3 * std::max(S, T) + 3);
+    if (S) {
+        k_keys<<<blocks(S, 256), 256, 0, s>>>(src, S, P.lo[0], P.lo[1], P.lo[2], P.L, P.periodic, D, xn.p,
+                                              P.keyS.p, P.idxS.p, P.err.p);
+        radix_sort(P.keyS, P.idxS, P.keyS2, P.idxS2, P.hist, (int)S, 3 * D, s);
+        k_gather3<<<blocks(S, 256), 256, 0, s>>>(xn.p, P.idxS.p, S, P.xs.p);
+        int nk = P.nrhs * P.k;
+        P.dens_s.reserve((size_t)S * nk);
+        k_gather_dens<<<blocks(S * nk, 256), 256, 0, s>>>(dens, P.idxS.p, S, P.nrhs, P.k, P.dens_s.p);
+    }
+    if (T) {
+        k_keys<<<blocks(T, 256), 256, 0, s>>>(trg, T, P.lo[0], P.lo[1], P.lo[2], P.L, P.periodic, D, xn.p,
+                                              P.keyT.p, P.idxT.p, P.err.p);
+        radix_sort(P.keyT, P.idxT, P.keyT2, P.idxT2, P.hist, (int)T, 3 * D, s);
+        k_gather3<<<blocks(T, 256), 256, 0, s>>>(xn.p, P.idxT.p, T, P.xt.p);
+    }
+    PK_CUDA(cudaStreamSynchronize(s));
+    xn.release();
+}
+
+}  // namespace pk

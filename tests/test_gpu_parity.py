@@ -1,0 +1,170 @@
+"""CUDA path vs the FP64 oracle (element by element, relative L2 gate).
+
+Tolerances: the FP64 path at p = 10 must reach rel-L2 <= 1e-8 against the
+Ewald oracle; lower p are checked against the KIFMM error they are expected
+to reach (falling with p); invariants (ell independence, translation
+invariance, periodicity) hold to near rounding."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import rel_l2, run
+from paper_1705_02043_gb300 import workloads as w
+import paper_1705_02043_gb300 as pk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cache(tmp_path_factory):
+    return str(tmp_path_factory.mktemp("opcache"))
+
+
+def test_config1_laplace_sp_x(cache):
+    """Laplace, singly periodic along x, N = 2000 uniform, p = 6, leaf <= 50."""
+    x, q = w.laplace_sp_uniform(2000, seed=0)
+    u = run(0, 1, x, q, x, p=6, leaf=50, cache_dir=cache)
+    ref = oracle.laplace_sp(x, q, x, axis=0)
+    e = rel_l2(u, ref)
+    print("config1 p=6 rel_l2", e)
+    assert e < 1e-5
+
+
+def test_madelung_1d_through_gpu(cache):
+    """Sec. 3.2 worked example through the full GPU path: -8 ln 2."""
+    src, q, trg = w.madelung_1d()
+    u = run(0, 4, src, q, trg, p=10, leaf=4, cache_dir=cache)
+    assert np.max(np.abs(u + 8 * math.log(2))) < 1e-9
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_fp64_p10_gate_tp(kernel, cache):
+    """North-star gate: FP64 path, p = 10, rel-L2 <= 1e-8 vs Ewald."""
+    n = 3000
+    if kernel == 0:
+        x, q = w.laplace_uniform(n, seed=3)
+        dens, ref_fn = q[0], oracle.laplace_tp
+    else:
+        x, f = w.stokes_uniform(n, seed=3, neutral=False)
+        dens, ref_fn = f[0], oracle.stokes_tp
+    u = run(kernel, 7, x, dens, x, p=10, leaf=40, cache_dir=cache)
+    ref = ref_fn(x, dens, x)
+    e = rel_l2(u, ref)
+    print("fp64 p=10 kernel", kernel, "rel_l2", e)
+    assert e < 1e-8
+
+
+def test_error_falls_with_p(cache):
+    x, f = w.stokes_uniform(1500, seed=5, neutral=False)
+    ref = oracle.stokes_tp(x, f[0], x)
+    errs = [rel_l2(run(1, 7, x, f[0], x, p=p, leaf=30, cache_dir=cache), ref) for p in (4, 6, 8)]
+    print("stokes TP errors p=4,6,8", errs)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-6
+
+
+def test_ell_independence(cache):
+    """Sec. 3.5: results for ell = 1, 2, 3 agree."""
+    x, f = w.stokes_uniform(1200, seed=6, neutral=False)
+    us = [run(1, 7, x, f[0], x, p=6, leaf=30, ell=ell, cache_dir=cache) for ell in (1, 2, 3)]
+    assert rel_l2(us[1], us[0]) < 1e-11 and rel_l2(us[2], us[0]) < 1e-11
+
+
+def test_translation_invariance_and_box(cache):
+    """Shifting every point (mod L) leaves the potentials unchanged; a box
+    [lo, lo+L) with L != 1 scales them by 1/L."""
+    x, q = w.laplace_uniform(1500, seed=8)
+    q = q[0]
+    a = run(0, 7, x, q, x, p=8, leaf=30, cache_dir=cache)
+    xs = x + np.array([0.31, -0.17, 0.53])
+    b = run(0, 7, xs, q, xs, p=8, leaf=30, cache_dir=cache)
+    assert rel_l2(b, a) < 1e-6
+    lo, L = np.array([-2.0, 1.0, 0.5]), 3.0
+    c = run(0, 7, lo + L * x, q, lo + L * x, p=8, leaf=30, lo=lo, L=L, cache_dir=cache)
+    assert rel_l2(c, a / L) < 1e-12
+
+
+def test_sources_differ_from_targets_and_ragged(cache):
+    """S != T, targets in empty regions, a ragged tail of boxes."""
+    src, f = w.stokes_uniform(1777, seed=9, neutral=False)
+    trg, _ = w.clustered_slab(901, seed=10, nclusters=5, sigma=0.03, zlo=0.0, zhi=1.0, kdim=1)
+    u = run(1, 7, src, f[0], trg, p=8, leaf=25, cache_dir=cache)
+    ref = oracle.stokes_tp(src, f[0], trg)
+    assert rel_l2(u, ref) < 1e-6
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_free_space(kernel, cache):
+    x = w.uniform_points(1600, seed=11)
+    d = np.random.default_rng(0).standard_normal((1600, 1 if kernel == 0 else 3))
+    d = d[:, 0] if kernel == 0 else d
+    u = run(kernel, 0, x, d, x, p=8, leaf=30, cache_dir=cache)
+    ref = oracle.free_space(kernel, x, d, x)
+    assert rel_l2(u, ref) < 1e-6
+
+
+def test_adaptive_clusters_use_w_and_x(cache):
+    """Clustered points: the adaptive tree exercises the W and X lists."""
+    x, q = w.clustered_slab(4000, seed=12, nclusters=6, sigma=0.02, zlo=0.0, zhi=1.0, kdim=1)
+    u, plan = run(0, 7, x, q, x, p=8, leaf=20, depth=10, cache_dir=cache, return_plan=True)
+    st = plan.tree_stats()
+    plan.close()
+    assert st[5] > 0 and st[6] > 0
+    ref = oracle.laplace_tp(x, q, x)
+    assert rel_l2(u, ref) < 1e-6
+
+
+def test_multiple_rhs_match_single(cache):
+    x, f = w.stokes_uniform(1000, seed=13, nrhs=3, neutral=False)
+    u3 = run(1, 7, x, f, x, p=6, leaf=30, cache_dir=cache)
+    for r in range(3):
+        u1 = run(1, 7, x, f[r], x, p=6, leaf=30, cache_dir=cache)
+        assert np.max(np.abs(u3[r] - u1)) < 1e-13 * np.max(np.abs(u1))
+
+
+def test_host_entry_matches_device(cache):
+    x, q = w.laplace_uniform(800, seed=14)
+    dev = run(0, 7, x, q[0], x, p=6, leaf=30, cache_dir=cache)
+    plan = pk.PeriodicKIFMM(0, 7, p=6, leaf_max=30, cache_dir=cache)
+    host = plan.evaluate_host(x, q[None, :, None] if q.ndim == 1 else q[:, :, None], x)
+    plan.close()
+    assert np.array_equal(host[0, :, 0], dev)
+
+
+def test_error_codes(cache):
+    x, q = w.laplace_uniform(300, seed=15)
+    q = q[0].copy()
+    q[0] += 0.5
+    with pytest.raises(pk.PKIFMMError) as e:
+        run(0, 7, x, q, x, p=4, cache_dir=cache)
+    assert e.value.name == "NOT_NEUTRAL"
+    y = x.copy()
+    y[0, 2] = 1.25
+    with pytest.raises(pk.PKIFMMError) as e:
+        run(0, 3, y, q - q.mean(), y, p=4, cache_dir=cache)  # z is free
+    assert e.value.name == "OUT_OF_BOX"
+    y = x.copy()
+    y[3, 1] = np.nan
+    with pytest.raises(pk.PKIFMMError) as e:
+        run(1, 7, y, np.ones((300, 3)), y, p=4, cache_dir=cache)
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(pk.PKIFMMError) as e:
+        pk.PeriodicKIFMM(1, 3, p=6)
+    assert e.value.name == "UNSUPPORTED"
+
+
+def test_empty_inputs(cache):
+    import torch
+    plan = pk.PeriodicKIFMM(1, 7, p=4, cache_dir=cache)
+    dev = torch.device("cuda:0")
+    src = torch.zeros((0, 3), dtype=torch.float64, device=dev)
+    dens = torch.zeros((1, 0, 3), dtype=torch.float64, device=dev)
+    trg = torch.rand((5, 3), dtype=torch.float64, device=dev)
+    out = plan.evaluate(src, dens, trg)
+    assert torch.all(out == 0)
+    out = plan.evaluate(trg, torch.ones((1, 5, 3), dtype=torch.float64, device=dev), src)
+    assert out.shape == (1, 0, 3)
+    plan.close()
