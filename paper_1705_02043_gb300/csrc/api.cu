@@ -42,12 +42,14 @@ int guarded(F &&f) {
 }
 
 __global__ void k_unpermute(const double *__restrict__ pot_s, const int *__restrict__ idx, long long T, int nrhs,
-                            int k, double invL, double *__restrict__ pot) {
+                            int k, double invL, const double *__restrict__ corr, double *__restrict__ pot) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= T * nrhs * k) return;
     long long t = i / (nrhs * k);
     int rem = (int)(i % (nrhs * k)), r = rem / k, a = rem % k;
-    pot[((long long)r * T + idx[t]) * k + a] = pot_s[i] * invL;
+    double v = pot_s[i];
+    if (corr) v += corr[r];
+    pot[((long long)r * T + idx[t]) * k + a] = v * invL;
 }
 
 // sums[2*c] += phi, sums[2*c+1] += |phi| per (rhs, component) c
@@ -74,6 +76,59 @@ __global__ void k_dens_sums(const double *__restrict__ dens, long long S, int nk
         atomicAdd(&sums[2 * c], sh[0]);
         atomicAdd(&sums[2 * c + 1], sh[blockDim.x]);
     }
+}
+
+// Laplace, triply periodic: the far-field kernel K^{P,F} of the Ewald
+// (k = 0 removed) periodic sum is not harmonic in the source position: the
+// neutralising background gives lap_y K^{P,F} = 4 pi / V inside the cell.
+// Two charge sets with the same exterior field (the sources and the root's
+// upward equivalent density) therefore receive far fields that differ by the
+// constant (2 pi / 3V) (sum q |y - c|^2 - sum phi^u |y^u - c|^2).  That
+// constant is restored here so the result is the zero-mean Ewald potential.
+__global__ void k_second_moment_src(const double *__restrict__ xs, const double *__restrict__ dens, long long S,
+                                    int nrhs, double *__restrict__ m2) {
+    int r = blockIdx.y;
+    double acc = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
+        double dx = xs[3 * i] - 0.5, dy = xs[3 * i + 1] - 0.5, dz = xs[3 * i + 2] - 0.5;
+        acc += dens[i * nrhs + r] * (dx * dx + dy * dy + dz * dz);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&m2[r], acc);
+}
+
+template <typename T>
+__global__ void k_second_moment_root(const T *__restrict__ up, const double *__restrict__ g, int n, int nrhs,
+                                     double *__restrict__ m2) {
+    int r = blockIdx.x;
+    double acc = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double g2 = g[3 * j] * g[3 * j] + g[3 * j + 1] * g[3 * j + 1] + g[3 * j + 2] * g[3 * j + 2];
+        acc += (double)up[(long long)r * n + j] * 0.525 * 0.525 * g2;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&m2[nrhs + r], acc);
+}
+
+__global__ void k_moment_finish(const double *m2, int nrhs, double *corr) {
+    int r = threadIdx.x;
+    if (r < nrhs) corr[r] = 2.0 * 3.14159265358979323846 / 3.0 * (m2[r] - m2[nrhs + r]);
+}
+
+const double *laplace_tp_constant(Plan &P, cudaStream_t s) {
+    if (P.kernel != PKIFMM_LAPLACE || P.periodic != 7) return nullptr;
+    int nr = P.nrhs;
+    P.sums.reserve(4 * nr + 4);
+    double *m2 = P.sums.p, *corr = P.sums.p + 2 * nr;
+    PK_CUDA(cudaMemsetAsync(m2, 0, sizeof(double) * 2 * nr, s));
+    dim3 grid((unsigned)std::min<long long>(512, (P.S + 255) / 256), nr);
+    k_second_moment_src<<<grid, 256, 0, s>>>(P.xs.p, P.dens_s.p, P.S, nr, m2);
+    if (P.precision == PKIFMM_FP64)
+        k_second_moment_root<double><<<nr, 256, 0, s>>>(P.up64.p, P.g64.p, P.n, nr, m2);
+    else
+        k_second_moment_root<float><<<nr, 256, 0, s>>>(P.up32.p, P.g64.p, P.n, nr, m2);
+    k_moment_finish<<<1, 64, 0, s>>>(m2, nr, corr);
+    return corr;
 }
 
 bool needs_neutral(const Plan &P) {
@@ -133,7 +188,9 @@ int evaluate_impl(Plan &P, int64_t S, const double *src, const double *dens, int
     record(P, 6, s);
     run_leaves(P, s);
     long long n = T * P.nrhs * P.k;
-    k_unpermute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.pot_s.p, P.idxT.p, T, P.nrhs, P.k, 1.0 / P.L, pot);
+    const double *corr = laplace_tp_constant(P, s);
+    k_unpermute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.pot_s.p, P.idxT.p, T, P.nrhs, P.k, 1.0 / P.L, corr,
+                                                             pot);
     record(P, 7, s);
     PK_CUDA(cudaGetLastError());
     return PKIFMM_OK;
@@ -175,10 +232,10 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, con
         P.L = box_len;
         try {
             PK_CUDA(cudaGetDevice(&P.device));
-            // FP64: singular values <= eps_m * s_max dropped (Appendix B).
-            // MIXED: cut at the binary32 rounding level, since the operators
-            // are applied in binary32.
-            double eps = precision == PKIFMM_FP64 ? std::ldexp(1.0, -52) : std::ldexp(1.0, -24);
+            // Singular values <= eps * dim(A) * s_max are dropped: the numerical
+            // rank threshold of Table 1 (the MATLAB / numpy pinv default), with
+            // eps the unit roundoff of the arithmetic the operators run in.
+            double eps = (precision == PKIFMM_FP64 ? std::ldexp(1.0, -52) : std::ldexp(1.0, -24)) * P.kn;
             if (const char *e = std::getenv("PKIFMM_EPS_MIXED"); e && precision == PKIFMM_MIXED) eps = std::atof(e);
             build_host_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
             upload_operators(P);

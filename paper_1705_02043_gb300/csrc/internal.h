@@ -107,7 +107,7 @@ struct Plan {
     DBuf<double> uc2e_a, uc2e_b, dc2e_a, dc2e_b, m2m, l2l, m2l, root;
     DBuf<float> uc2e_a32, uc2e_b32, dc2e_a32, dc2e_b32, m2m32, l2l32, m2l32;
     DBuf<int> class_slot_op;                    // [8][189] M2L op index per class slot
-    DBuf<signed char> slot_of;                  // [8][343] slot of offset o, -1 if none
+    DBuf<short> slot_of;                        // [8][343] slot of offset o, -1 if none
 
     // evaluation workspace
     int64_t S = 0, T = 0;

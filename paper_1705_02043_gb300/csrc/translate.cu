@@ -79,7 +79,7 @@ void upload_operators(Plan &P) {
                 offs.push_back(y);
                 offs.push_back(z);
             }
-    std::vector<signed char> slot_of(8 * 343, -1);
+    std::vector<short> slot_of(8 * 343, -1);
     std::vector<int> cls_op(8 * kVSlots, -1);
     for (int c = 0; c < 8; c++) {
         int cb[3] = {c & 1, c >> 1 & 1, c >> 2 & 1}, s = 0;
@@ -88,13 +88,13 @@ void upload_operators(Plan &P) {
                 for (int z = -2 - cb[2]; z <= 3 - cb[2]; z++) {
                     if (std::max(std::abs(x), std::max(std::abs(y), std::abs(z))) <= 1) continue;
                     int oi = ((x + 3) * 7 + (y + 3)) * 7 + (z + 3);
-                    slot_of[c * 343 + oi] = (signed char)s;
+                    slot_of[c * 343 + oi] = (short)s;
                     cls_op[c * kVSlots + s] = op_of[oi];
                     s++;
                 }
     }
     P.slot_of.reserve(slot_of.size());
-    PK_CUDA(cudaMemcpy(P.slot_of.p, slot_of.data(), slot_of.size(), cudaMemcpyHostToDevice));
+    PK_CUDA(cudaMemcpy(P.slot_of.p, slot_of.data(), sizeof(short) * slot_of.size(), cudaMemcpyHostToDevice));
     P.class_slot_op.reserve(cls_op.size());
     PK_CUDA(cudaMemcpy(P.class_slot_op.p, cls_op.data(), sizeof(int) * cls_op.size(), cudaMemcpyHostToDevice));
     DBuf<int> doffs;
@@ -685,7 +685,6 @@ static void prepare_points(Plan &P, cudaStream_t s) {
     B::dn(P).reserve(rows);
     B::tmp(P).reserve(rows);
     PK_CUDA(cudaMemsetAsync(B::up(P).p, 0, sizeof(T) * rows, s));
-    PK_CUDA(cudaMemsetAsync(B::chk(P).p, 0, sizeof(T) * (size_t)P.nrhs * P.kn, s));  // root check
 }
 
 template <typename T, int K>
@@ -746,6 +745,8 @@ void run_root(Plan &P, cudaStream_t s) {
     if (P.precision == PKIFMM_FP64) {
         if (P.periodic)
             gemm<double>(P.t_root, nullptr, 1, P.root.p, 0, P.up64.p, P.chk64.p, P.kn, P.nrhs, 0, s);
+        else  // no far field; the row may hold the root leaf's upward check values
+            PK_CUDA(cudaMemsetAsync(P.chk64.p, 0, sizeof(double) * P.nrhs * P.kn, s));
         return;
     }
     root_mixed(P, s);

@@ -400,7 +400,7 @@ struct ListOut {
     const int *u_ptr, *w_ptr, *x_ptr;
     int *u_cnt, *w_cnt, *x_cnt;
     int *v_slot;
-    const signed char *slot_of;
+    const short *slot_of;
     unsigned long long *pairs;
 };
 
