@@ -165,6 +165,11 @@ const char *pkifmm_strerror(int code);
  * string, valid until the next failing call on the thread). */
 const char *pkifmm_last_error_message(void);
 
+/* Total number of CUDA kernels this library has launched in this process
+ * (all plans and threads).  The difference across a region counts the
+ * launches inside it. */
+int64_t pkifmm_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

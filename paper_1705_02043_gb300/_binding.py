@@ -53,6 +53,8 @@ def load_library():
             lib.pkifmm_plan_destroy.restype = None
             lib.pkifmm_strerror.argtypes = [i]
             lib.pkifmm_strerror.restype = ctypes.c_char_p
+            lib.pkifmm_launch_count.argtypes = []
+            lib.pkifmm_launch_count.restype = ctypes.c_int64
             lib.pkifmm_last_error_message.argtypes = []
             lib.pkifmm_last_error_message.restype = ctypes.c_char_p
             _lib = lib
@@ -71,7 +73,7 @@ def _ptr(a):
         return None
     if isinstance(a, np.ndarray):
         return a.ctypes.data_as(ctypes.c_void_p)
-    return ctypes.c_void_p(a.data_ptr())  # torch tensor
+    return ctypes.c_void_p(a.data_ptr())  # torch tensor (device or host)
 
 
 # ---- C-ABI functions, same names ----
@@ -159,6 +161,10 @@ def pkifmm_plan_destroy(plan):
         load_library().pkifmm_plan_destroy(plan)
 
 
+def pkifmm_launch_count():
+    return int(load_library().pkifmm_launch_count())
+
+
 def pkifmm_strerror(code):
     return load_library().pkifmm_strerror(code).decode()
 
@@ -188,12 +194,15 @@ class PeriodicKIFMM:
         pkifmm_evaluate(self.handle, S, src, dens, T, trg, pot, ctypes.c_void_p(stream))
         return pot
 
-    def evaluate_host(self, src, dens, trg, pot=None):
-        """Host (numpy) arrays in and out; copies happen inside the library call."""
-        src, dens, trg = (np.ascontiguousarray(a, dtype=np.float64) for a in (src, dens, trg))
+    def evaluate_host(self, src, dens, trg, pot=None, stream=None):
+        """Host arrays in and out (numpy, or CPU torch tensors, e.g. pinned);
+        the host<->device copies happen inside the library call."""
+        if isinstance(src, np.ndarray):
+            src, dens, trg = (np.ascontiguousarray(a, dtype=np.float64) for a in (src, dens, trg))
         if pot is None:
             pot = np.zeros((self.nrhs, trg.shape[0], self.k))
-        pkifmm_evaluate_host(self.handle, src.shape[0], src, dens, trg.shape[0], trg, pot, None)
+        pkifmm_evaluate_host(self.handle, src.shape[0], src, dens, trg.shape[0], trg, pot,
+                             ctypes.c_void_p(stream) if stream else None)
         return pot
 
     def stage_times(self):

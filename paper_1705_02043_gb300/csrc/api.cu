@@ -122,12 +122,12 @@ const double *laplace_tp_constant(Plan &P, cudaStream_t s) {
     double *m2 = P.sums.p, *corr = P.sums.p + 2 * nr;
     PK_CUDA(cudaMemsetAsync(m2, 0, sizeof(double) * 2 * nr, s));
     dim3 grid((unsigned)std::min<long long>(512, (P.S + 255) / 256), nr);
-    k_second_moment_src<<<grid, 256, 0, s>>>(P.xs.p, P.dens_s.p, P.S, nr, m2);
+    count_launch(), k_second_moment_src<<<grid, 256, 0, s>>>(P.xs.p, P.dens_s.p, P.S, nr, m2);
     if (P.precision == PKIFMM_FP64)
-        k_second_moment_root<double><<<nr, 256, 0, s>>>(P.up64.p, P.g64.p, P.n, nr, m2);
+        count_launch(), k_second_moment_root<double><<<nr, 256, 0, s>>>(P.up64.p, P.g64.p, P.n, nr, m2);
     else
-        k_second_moment_root<float><<<nr, 256, 0, s>>>(P.up32.p, P.g64.p, P.n, nr, m2);
-    k_moment_finish<<<1, 64, 0, s>>>(m2, nr, corr);
+        count_launch(), k_second_moment_root<float><<<nr, 256, 0, s>>>(P.up32.p, P.g64.p, P.n, nr, m2);
+    count_launch(), k_moment_finish<<<1, 64, 0, s>>>(m2, nr, corr);
     return corr;
 }
 
@@ -165,7 +165,7 @@ int evaluate_impl(Plan &P, int64_t S, const double *src, const double *dens, int
         P.sums.reserve(2 * nk);
         PK_CUDA(cudaMemsetAsync(P.sums.p, 0, sizeof(double) * 2 * nk, s));
         dim3 grid((unsigned)std::min<long long>(1024, (S + 255) / 256), nk);
-        k_dens_sums<<<grid, 256, 2 * 256 * sizeof(double), s>>>(P.dens_s.p, S, nk, P.sums.p);
+        count_launch(), k_dens_sums<<<grid, 256, 2 * 256 * sizeof(double), s>>>(P.dens_s.p, S, nk, P.sums.p);
         std::vector<double> h(2 * nk);
         PK_CUDA(cudaMemcpyAsync(h.data(), P.sums.p, sizeof(double) * 2 * nk, cudaMemcpyDeviceToHost, s));
         PK_CUDA(cudaStreamSynchronize(s));
@@ -189,7 +189,7 @@ int evaluate_impl(Plan &P, int64_t S, const double *src, const double *dens, int
     run_leaves(P, s);
     long long n = T * P.nrhs * P.k;
     const double *corr = laplace_tp_constant(P, s);
-    k_unpermute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.pot_s.p, P.idxT.p, T, P.nrhs, P.k, 1.0 / P.L, corr,
+    count_launch(), k_unpermute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.pot_s.p, P.idxT.p, T, P.nrhs, P.k, 1.0 / P.L, corr,
                                                              pot);
     record(P, 7, s);
     PK_CUDA(cudaGetLastError());
@@ -564,5 +564,7 @@ const char *pkifmm_strerror(int code) {
 }
 
 const char *pkifmm_last_error_message(void) { return g_last_error.c_str(); }
+
+int64_t pkifmm_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <stdexcept>
 #include <string>
@@ -24,6 +25,10 @@ struct Error : std::runtime_error {
             throw ::pk::Error(e_ == cudaErrorMemoryAllocation ? PKIFMM_ERR_OOM : PKIFMM_ERR_CUDA, \
                               std::string(#call) + ": " + cudaGetErrorString(e_));            \
     } while (0)
+
+// Kernel launches issued by this library (all threads), for launch accounting.
+inline std::atomic<long long> g_launches{0};
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 constexpr int kMaxLevel = 16;
 constexpr int kVSlots = 189;     // V-list slots per target octant class

@@ -26,9 +26,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <filesystem>
 #include <fstream>
 #include <numeric>
 #include <stdexcept>
+#include <unistd.h>
 
 namespace pk {
 
@@ -371,7 +373,9 @@ bool load_cache(const std::string &path, HostOps &o) {
 }
 
 void save_cache(const std::string &path, HostOps &o) {
-    std::string tmp = path + ".tmp";
+    std::error_code ec;
+    std::filesystem::create_directories(std::filesystem::path(path).parent_path(), ec);
+    std::string tmp = path + ".tmp" + std::to_string((long long)std::hash<std::string>{}(path) ^ (long long)getpid());
     std::ofstream f(tmp, std::ios::binary);
     if (!f) throw std::runtime_error("cache: cannot write " + tmp);
     int hdr[6] = {kVersion, o.kernel, o.p, (int)o.periodic, o.ell, o.kn};

@@ -111,7 +111,7 @@ void upload_operators(Plan &P) {
         upload(P.m2m, H.m2m);
         upload(P.l2l, H.l2l);
         P.m2l.reserve(kM2LOps * kn2);
-        k_m2l_ops<double><<<nblk(tot, 256), 256>>>(P.kernel, P.n, P.g64.p, doffs.p, P.m2l.p);
+        count_launch(), k_m2l_ops<double><<<nblk(tot, 256), 256>>>(P.kernel, P.n, P.g64.p, doffs.p, P.m2l.p);
     } else {
         upload(P.uc2e_a32, H.uc2e_a);
         upload(P.uc2e_b32, H.uc2e_b);
@@ -120,7 +120,7 @@ void upload_operators(Plan &P) {
         upload(P.m2m32, H.m2m);
         upload(P.l2l32, H.l2l);
         P.m2l32.reserve(kM2LOps * kn2);
-        k_m2l_ops<float><<<nblk(tot, 256), 256>>>(P.kernel, P.n, P.g64.p, doffs.p, P.m2l32.p);
+        count_launch(), k_m2l_ops<float><<<nblk(tot, 256), 256>>>(P.kernel, P.n, P.g64.p, doffs.p, P.m2l32.p);
         // the root far field and its solve stay in binary64
         upload(P.dc2e_a, H.dc2e_a);
         upload(P.dc2e_b, H.dc2e_b);
@@ -350,7 +350,7 @@ static void gemm(const Task &t, const int *slot_table, int slot_stride, const T 
                  const T *src, T *dst, int kn, int nrhs, int beta, cudaStream_t s) {
     if (t.ntiles == 0) return;
     dim3 grid(t.ntiles, (kn + GB_N - 1) / GB_N);
-    k_slot_gemm<T><<<grid, 256, 0, s>>>(t.boxes.p, t.tiles.p, slot_table, slot_stride, t.nslots, t.class_ops.p,
+    count_launch(), k_slot_gemm<T><<<grid, 256, 0, s>>>(t.boxes.p, t.tiles.p, slot_table, slot_stride, t.nslots, t.class_ops.p,
                                         ops, op_stride, src, dst, kn, nrhs, beta);
 }
 
@@ -671,13 +671,13 @@ static void prepare_points(Plan &P, cudaStream_t s) {
     auto *yr = reinterpret_cast<V4<T> *>(B::yrel(P).p);
     auto *xr = reinterpret_cast<V4<T> *>(B::xrel(P).p);
     if (P.n_leaves_src)
-        k_relcoords<T><<<P.n_leaves_src, 128, 0, s>>>(P.leaves_src.p, P.tree.bpos.p, P.tree.srange.p, P.xs.p, yr);
+        count_launch(), k_relcoords<T><<<P.n_leaves_src, 128, 0, s>>>(P.leaves_src.p, P.tree.bpos.p, P.tree.srange.p, P.xs.p, yr);
     if (P.n_leaves_trg)
-        k_relcoords<T><<<P.n_leaves_trg, 128, 0, s>>>(P.leaves_trg.p, P.tree.bpos.p, P.tree.trange.p, P.xt.p, xr);
+        count_launch(), k_relcoords<T><<<P.n_leaves_trg, 128, 0, s>>>(P.leaves_trg.p, P.tree.bpos.p, P.tree.trange.p, P.xt.p, xr);
     if (sizeof(T) == 4) {
         long long nd = P.S * P.nrhs * P.k;
         P.dens32.reserve(nd + 1);
-        if (nd) k_cast<float><<<nblk(nd, 256), 256, 0, s>>>(P.dens_s.p, P.dens32.p, nd);
+        if (nd) count_launch(), k_cast<float><<<nblk(nd, 256), 256, 0, s>>>(P.dens_s.p, P.dens32.p, nd);
     }
     size_t rows = (size_t)P.tree.nbox * P.nrhs * P.kn;
     B::up(P).reserve(rows);
@@ -696,7 +696,7 @@ static void upward_t(Plan &P, cudaStream_t s) {
     auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
     if (P.n_leaves_src)
         for (int r = 0; r < nr; r++)
-            k_s2m<T, K><<<P.n_leaves_src, KS_T, 0, s>>>(P.leaves_src.p, P.tree.bpos.p, P.tree.srange.p, yr, B::dens(P), nr,
+            count_launch(), k_s2m<T, K><<<P.n_leaves_src, KS_T, 0, s>>>(P.leaves_src.p, P.tree.bpos.p, P.tree.srange.p, yr, B::dens(P), nr,
                                                          r, B::g(P).p, P.n, B::chk(P).p);
     // UC2E: tmp = U^T q~u ; up = (V S+) tmp
     gemm<T>(P.t_uc2e, nullptr, 1, B::uc2e_b(P), 0, B::chk(P).p, B::tmp(P).p, kn, nr, 0, s);
@@ -734,11 +734,11 @@ void root_mixed(Plan &P, cudaStream_t s) {
         PK_CUDA(cudaMemsetAsync(P.dn32.p, 0, sizeof(float) * rows, s));
         return;
     }
-    k_f2d<float><<<nblk(rows, 256), 256, 0, s>>>(P.up32.p, P.up64.p, rows);
+    count_launch(), k_f2d<float><<<nblk(rows, 256), 256, 0, s>>>(P.up32.p, P.up64.p, rows);
     gemm<double>(P.t_root, nullptr, 1, P.root.p, 0, P.up64.p, P.chk64.p, kn, nr, 0, s);
     gemm<double>(P.t_root, nullptr, 1, P.dc2e_b.p, 0, P.chk64.p, P.tmp64.p, kn, nr, 0, s);
     gemm<double>(P.t_root, nullptr, 1, P.dc2e_a.p, 0, P.tmp64.p, P.dn64.p, kn, nr, 0, s);
-    k_cast<float><<<nblk(rows, 256), 256, 0, s>>>(P.dn64.p, P.dn32.p, rows);
+    count_launch(), k_cast<float><<<nblk(rows, 256), 256, 0, s>>>(P.dn64.p, P.dn32.p, rows);
 }
 
 void run_root(Plan &P, cudaStream_t s) {
@@ -771,7 +771,7 @@ static void downward_t(Plan &P, cudaStream_t s) {
     auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
     if (P.n_xboxes)
         for (int r = 0; r < nr; r++)
-            k_s2l<T, K><<<P.n_xboxes, KS_T, 0, s>>>(P.xboxes.p, P.tree.bpos.p, P.tree.srange.p, P.tree.x_ptr.p,
+            count_launch(), k_s2l<T, K><<<P.n_xboxes, KS_T, 0, s>>>(P.xboxes.p, P.tree.bpos.p, P.tree.srange.p, P.tree.x_ptr.p,
                                                      P.tree.x_box.p, P.tree.x_sh.p, yr, B::dens(P), nr, r, B::g(P).p,
                                                      P.n, B::chk(P).p);
     gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_b(P), 0, B::chk(P).p, B::tmp(P).p, kn, nr, 0, s);
@@ -799,7 +799,7 @@ static void leaves_t(Plan &P, cudaStream_t s) {
     auto *xr = reinterpret_cast<const V4<T> *>(B::xrel(P).p);
     if (P.n_leaves_trg)
         for (int r = 0; r < nr; r++)
-            k_leaf<T, K><<<P.n_leaves_trg, KS_T, 0, s>>>(
+            count_launch(), k_leaf<T, K><<<P.n_leaves_trg, KS_T, 0, s>>>(
                 P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
                 P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
                 B::dn(P).p, nr, r, B::g(P).p, P.n, P.pot_s.p);

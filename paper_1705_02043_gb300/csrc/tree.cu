@@ -82,12 +82,12 @@ int exclusive_scan(const int *in, int *out, int n, cudaStream_t s) {
     int *bsum = nullptr, *boff = nullptr;
     PK_CUDA(cudaMallocAsync(&bsum, sizeof(int) * (nb + 1), s));
     PK_CUDA(cudaMallocAsync(&boff, sizeof(int) * (nb + 1), s));
-    k_scan_block<<<nb, 1024, 0, s>>>(in, out, bsum, n);
+    count_launch(), k_scan_block<<<nb, 1024, 0, s>>>(in, out, bsum, n);
     if (nb > 1) {
         exclusive_scan(bsum, boff, nb, s);
-        k_scan_add<<<nb, 1024, 0, s>>>(out, boff, n, nullptr);
+        count_launch(), k_scan_add<<<nb, 1024, 0, s>>>(out, boff, n, nullptr);
     }
-    k_scan_fix_total<<<1, 1, 0, s>>>(out, in, n);
+    count_launch(), k_scan_fix_total<<<1, 1, 0, s>>>(out, in, n);
     int total = 0;
     PK_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaFreeAsync(bsum, s));
@@ -197,9 +197,9 @@ static void radix_sort(DBuf<unsigned long long> &k, DBuf<int> &v, DBuf<unsigned 
     int *va = v.p, *vb = v2.p;
     int *h = hist.p, *ho = hist.p + 16 * nb + 1;
     for (int sh = 0; sh < bits; sh += 4) {
-        k_rs_count<<<nb, RS_T, 0, s>>>(ka, n, sh, h, nb);
+        count_launch(), k_rs_count<<<nb, RS_T, 0, s>>>(ka, n, sh, h, nb);
         exclusive_scan(h, ho, 16 * nb, s);
-        k_rs_scatter<<<nb, RS_T, 0, s>>>(ka, va, kb, vb, n, sh, ho, nb);
+        count_launch(), k_rs_scatter<<<nb, RS_T, 0, s>>>(ka, va, kb, vb, n, sh, ho, nb);
         std::swap(ka, kb);
         std::swap(va, vb);
     }
@@ -304,7 +304,7 @@ void build_tree(Plan &P, cudaStream_t s) {
     t.child.grow_keep(cap * 8, 0, s);
     t.srange.grow_keep(cap, 0, s);
     t.trange.grow_keep(cap, 0, s);
-    k_root<<<1, 1, 0, s>>>(t.key.p, t.bpos.p, t.parent.p, t.srange.p, t.trange.p, (int)P.S, (int)P.T);
+    count_launch(), k_root<<<1, 1, 0, s>>>(t.key.p, t.bpos.p, t.parent.p, t.srange.p, t.trange.p, (int)P.S, (int)P.T);
     t.lvl_begin.assign({0, 1});
     int level = 0;
     for (;; level++) {
@@ -313,7 +313,7 @@ void build_tree(Plan &P, cudaStream_t s) {
         P.ctr.reserve((size_t)nl * 8);
         P.cnt.reserve(nl + 1);
         P.off.reserve(nl + 1);
-        k_split<<<blocks(nl, 128), 128, 0, s>>>(lb, le, level, D, P.leaf_max, t.key.p, t.srange.p, t.trange.p,
+        count_launch(), k_split<<<blocks(nl, 128), 128, 0, s>>>(lb, le, level, D, P.leaf_max, t.key.p, t.srange.p, t.trange.p,
                                                  P.keyS.p, P.keyT.p, P.csr.p, P.ctr.p, P.cnt.p);
         int total = exclusive_scan(P.cnt.p, P.off.p, nl, s);
         size_t need = (size_t)le + total;
@@ -323,7 +323,7 @@ void build_tree(Plan &P, cudaStream_t s) {
         t.child.grow_keep(need * 8, (size_t)le * 8, s);
         t.srange.grow_keep(need, le, s);
         t.trange.grow_keep(need, le, s);
-        k_emit<<<blocks(nl, 128), 128, 0, s>>>(lb, le, P.cnt.p, P.off.p, P.csr.p, P.ctr.p, t.key.p, t.bpos.p,
+        count_launch(), k_emit<<<blocks(nl, 128), 128, 0, s>>>(lb, le, P.cnt.p, P.off.p, P.csr.p, P.ctr.p, t.key.p, t.bpos.p,
                                                 t.parent.p, t.child.p, t.srange.p, t.trange.p);
         if (total == 0) break;
         t.lvl_begin.push_back(le + total);
@@ -580,7 +580,7 @@ void build_lists(Plan &P, cudaStream_t s) {
     o.w_cnt = cnt3.p + nb;
     o.x_cnt = cnt3.p + 2 * nb;
     o.slot_of = P.slot_of.p;
-    k_lists<<<blocks(nb, 128), 128, 0, s>>>(tv, nb, 0, o);
+    count_launch(), k_lists<<<blocks(nb, 128), 128, 0, s>>>(tv, nb, 0, o);
     t.nU = exclusive_scan(o.u_cnt, t.u_ptr.p, nb, s);
     t.nW = exclusive_scan(o.w_cnt, t.w_ptr.p, nb, s);
     t.nX = exclusive_scan(o.x_cnt, t.x_ptr.p, nb, s);
@@ -601,8 +601,8 @@ void build_lists(Plan &P, cudaStream_t s) {
     o.x_ptr = t.x_ptr.p;
     o.v_slot = t.v_slot.p;
     o.pairs = pairs.p;
-    k_lists<<<blocks(nb, 128), 128, 0, s>>>(tv, nb, 1, o);
-    k_count_v<<<blocks((long long)nb * kVSlots, 256), 256, 0, s>>>(t.v_slot.p, (long long)nb * kVSlots,
+    count_launch(), k_lists<<<blocks(nb, 128), 128, 0, s>>>(tv, nb, 1, o);
+    count_launch(), k_count_v<<<blocks((long long)nb * kVSlots, 256), 256, 0, s>>>(t.v_slot.p, (long long)nb * kVSlots,
                                                                      pairs.p + 1);
     unsigned long long h[2];
     PK_CUDA(cudaMemcpyAsync(h, pairs.p, sizeof h, cudaMemcpyDeviceToHost, s));
@@ -629,19 +629,19 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
     DBuf<double> xn;
     xn.reserve(3 * std::max(S, T) + 3);
     if (S) {
-        k_keys<<<blocks(S, 256), 256, 0, s>>>(src, S, P.lo[0], P.lo[1], P.lo[2], P.L, P.periodic, D, xn.p,
+        count_launch(), k_keys<<<blocks(S, 256), 256, 0, s>>>(src, S, P.lo[0], P.lo[1], P.lo[2], P.L, P.periodic, D, xn.p,
                                               P.keyS.p, P.idxS.p, P.err.p);
         radix_sort(P.keyS, P.idxS, P.keyS2, P.idxS2, P.hist, (int)S, 3 * D, s);
-        k_gather3<<<blocks(S, 256), 256, 0, s>>>(xn.p, P.idxS.p, S, P.xs.p);
+        count_launch(), k_gather3<<<blocks(S, 256), 256, 0, s>>>(xn.p, P.idxS.p, S, P.xs.p);
         int nk = P.nrhs * P.k;
         P.dens_s.reserve((size_t)S * nk);
-        k_gather_dens<<<blocks(S * nk, 256), 256, 0, s>>>(dens, P.idxS.p, S, P.nrhs, P.k, P.dens_s.p);
+        count_launch(), k_gather_dens<<<blocks(S * nk, 256), 256, 0, s>>>(dens, P.idxS.p, S, P.nrhs, P.k, P.dens_s.p);
     }
     if (T) {
-        k_keys<<<blocks(T, 256), 256, 0, s>>>(trg, T, P.lo[0], P.lo[1], P.lo[2], P.L, P.periodic, D, xn.p,
+        count_launch(), k_keys<<<blocks(T, 256), 256, 0, s>>>(trg, T, P.lo[0], P.lo[1], P.lo[2], P.L, P.periodic, D, xn.p,
                                               P.keyT.p, P.idxT.p, P.err.p);
         radix_sort(P.keyT, P.idxT, P.keyT2, P.idxT2, P.hist, (int)T, 3 * D, s);
-        k_gather3<<<blocks(T, 256), 256, 0, s>>>(xn.p, P.idxT.p, T, P.xt.p);
+        count_launch(), k_gather3<<<blocks(T, 256), 256, 0, s>>>(xn.p, P.idxT.p, T, P.xt.p);
     }
     PK_CUDA(cudaStreamSynchronize(s));
     xn.release();
