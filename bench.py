@@ -208,7 +208,7 @@ def main():
             peak = pk_.get("bf16_tflops_sustained", 1700.0)
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": "M2L (V list), split-bf16 x3 tcgen05", "peak_source": f"bf16_tflops_sustained ({src})"}
+                    "kernel": "M2L (V list), split-fp16 x3 tcgen05", "peak_source": f"bf16_tflops_sustained ({src})"}
         else:
             mhz = (clocks or {}).get("sm_mhz") or pk_.get("sm_max_mhz", 2070.0)
             peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
@@ -246,7 +246,7 @@ def main():
         result = {
             "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "mixed: f32 sums, bf16x3 tensor M2L, f64 root" if tc else "f32",
+            "vs_baseline": None, "dtype": "mixed: f32 sums, fp16x3 tensor M2L, f64 root" if tc else "f32",
             "data": "synthetic (seeded uniform points, N(0,1) forces, net force removed)",
             "config": {"workload": f"stokes_tp_uniform_N{args.n}_p{args.p}_leaf{args.leaf}", "kernel": "stokes",
                        "periodic": "xyz", "N": args.n, "p": args.p, "leaf_max": args.leaf, "nrhs": 1,

@@ -53,9 +53,10 @@ enum { PKIFMM_LAPLACE = 0, PKIFMM_STOKES = 1 };
  * FP64  — every stage in binary64 (accuracy reference path);
  * MIXED — kernel sums (P2P, S2M, L2T, W, X) in binary32 on leaf-local
  *         coordinates with compensated accumulation; M2L on the tensor cores
- *         as split-bf16 (three products) accumulated in binary32; the other
- *         translations in binary32; the root periodic operator and its
- *         check-to-equivalent solve in binary64. */
+ *         (tcgen05) as scaled split-fp16 pairs (three products) accumulated
+ *         in binary32; the other translations in binary32; the root periodic
+ *         operator and its check-to-equivalent solve in binary64.  Needs an
+ *         sm_103 GPU. */
 enum { PKIFMM_FP64 = 0, PKIFMM_MIXED = 1 };
 
 enum {
@@ -115,7 +116,9 @@ int pkifmm_evaluate_host(pkifmm_plan plan, int64_t S, const double *src_xyz,
 /* Per-stage device times (ms) of the last evaluate, in this order:
  * 0 keys+sort, 1 tree+lists, 2 upward (S2M, M2M), 3 root periodic operator,
  * 4 M2L (V list), 5 X list + downward (C2E, L2L), 6 leaves (L2T, W, P2P),
- * 7 total.  Writes min(max, 8) values; returns that count (or an error). */
+ * 7 total, 8 the tensor-core M2L kernel alone (MIXED plans; else 0).
+ * Writes min(max, 9) values; returns that count (or an error).  Waits for
+ * the last evaluate's work to finish. */
 int pkifmm_last_stage_times(pkifmm_plan plan, double *ms, int max);
 
 /* Counts describing the octree of the last evaluate:
@@ -169,6 +172,10 @@ const char *pkifmm_last_error_message(void);
  * (all plans and threads).  The difference across a region counts the
  * launches inside it. */
 int64_t pkifmm_launch_count(void);
+
+/* 1 if MIXED plans run their M2L on the tensor cores of the current device
+ * (tcgen05, sm_103), else 0 (MIXED plans then fail with UNSUPPORTED). */
+int pkifmm_m2l_tensor_core_enabled(void);
 
 #ifdef __cplusplus
 }

@@ -53,6 +53,7 @@ def load_library():
             lib.pkifmm_plan_destroy.restype = None
             lib.pkifmm_strerror.argtypes = [i]
             lib.pkifmm_strerror.restype = ctypes.c_char_p
+            lib.pkifmm_m2l_tensor_core_enabled.argtypes = []
             lib.pkifmm_launch_count.argtypes = []
             lib.pkifmm_launch_count.restype = ctypes.c_int64
             lib.pkifmm_last_error_message.argtypes = []
@@ -100,8 +101,8 @@ def pkifmm_evaluate_host(plan, S, src, dens, T, trg, pot, stream=None):
 
 
 def pkifmm_last_stage_times(plan):
-    out = np.zeros(8)
-    _check(load_library().pkifmm_last_stage_times(plan, _ptr(out), 8))
+    out = np.zeros(9)
+    _check(load_library().pkifmm_last_stage_times(plan, _ptr(out), 9))
     return out
 
 
@@ -159,6 +160,10 @@ def pkifmm_root_operator(kernel, periodic_axes, p, ell):
 def pkifmm_plan_destroy(plan):
     if plan:
         load_library().pkifmm_plan_destroy(plan)
+
+
+def pkifmm_m2l_tensor_core_enabled():
+    return int(load_library().pkifmm_m2l_tensor_core_enabled())
 
 
 def pkifmm_launch_count():

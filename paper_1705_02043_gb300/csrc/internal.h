@@ -97,7 +97,10 @@ struct Task {
     int ntiles = 0;
     DBuf<int> class_ops;      // [nclass][nslots]
     std::vector<int> h_boxes; // host copies used to build tiles
+    std::vector<int> class_count;  // boxes per class
 };
+
+struct TcState;  // tensor-core M2L state (m2l_tc.cu)
 
 struct Plan {
     int kernel = 0, k = 1, p = 0, n = 0, kn = 0, ell = 2, leaf_max = 64, depth_max = 10;
@@ -139,10 +142,14 @@ struct Plan {
     std::vector<Task> t_m2m, t_l2l;             // per level
     DBuf<int> leaves_src, leaves_trg, xboxes;   // task lists for kernel sums
     int n_leaves_src = 0, n_leaves_trg = 0, n_xboxes = 0;
-    double stage_ms[8] = {0};
+    double stage_ms[9] = {0};
     cudaEvent_t ev[9] = {};
     bool events = false;
+    TcState *tc = nullptr;
 };
+
+void m2l_tc_release(Plan &P);
+float m2l_tc_last_ms(Plan &P);
 
 // ---- tree.cu ----
 void build_tree(Plan &P, cudaStream_t s);

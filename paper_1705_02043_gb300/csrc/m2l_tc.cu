@@ -1,9 +1,572 @@
-// Tensor-core V-list M2L for the MIXED path (tcgen05, split-bf16 products).
+// Tensor-core V-list M2L for the MIXED path (tcgen05, split-fp16 products).
+//
+// The V-list M2L of Sec. 2.2 in the check formulation,
+//     q~d[B] = sum_{slots s} K_{o(class(B), s)} phi_u[V(B, s)],
+// is a dense contraction: for the boxes of one octant class every slot s
+// uses the same operator K_o (kn x kn), so a CTA computes
+//     D[128 kn rows x 128 (box, rhs) columns] = sum_s sum_k K_o[:, k] Phi_s[:, k]^T
+// with Phi_s the gathered upward densities.  Operands are scaled by powers of
+// two into the fp16 range and split into fp16 pairs x = x_hi + x_lo (22
+// significant bits); each product is K_hi Phi_hi + K_hi Phi_lo + K_lo Phi_hi.
+//
+// Precision: the tensor core accumulates in fp32 but drops low bits at every
+// accumulation step, a bias that grows with the number of MMAs summed into
+// one accumulator (tens of thousands over all slots).  So each slot's
+// contribution is accumulated in tensor memory and then added, rounding to
+// nearest, into fp32 registers of the epilogue warps, while the next slot
+// accumulates in the other buffer.  Within a slot the large hi*hi products
+// and the 2^-11 smaller cross products go to separate accumulators, so the
+// large one takes only 2 KP/32 steps per slot.
+//
+// Pipeline (5 stages of 32 KB): warps 0-3 gather the Phi rows with 16-byte
+// cp.async into the 64B-swizzled K-major layout and one thread issues the TMA
+// loads of the K_o tiles; warp 4 issues tcgen05.mma from one thread and frees
+// each stage with tcgen05.commit; warps 5-8 drain the work accumulators and
+// finally write the check potentials.  Every mbarrier wait is bounded in time;
+// on timeout the kernel raises an error flag and returns.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <cstring>
+
 #include "internal.h"
 
 namespace pk {
 
-void m2l_tc_prepare(Plan &) {}
-bool m2l_tc_run(Plan &, cudaStream_t) { return false; }
+constexpr int TC_N = 128;                          // (box, rhs) columns per CTA
+constexpr int TC_M = 128;                          // kn rows per CTA
+constexpr int TC_K = 32;                           // K chunk: 64 bytes of fp16 per row
+constexpr int TC_STAGES = 5;
+constexpr int TC_A_BYTES = TC_M * TC_K * 2;        // 8 KB per split
+constexpr int TC_B_BYTES = TC_N * TC_K * 2;        // 8 KB per split
+constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 32 KB
+constexpr int TC_CTRL_BYTES = 4096;
+constexpr int TC_SLACK = 16384;
+constexpr int TC_SMEM = TC_CTRL_BYTES + TC_STAGES * TC_STAGE_BYTES + TC_SLACK + 1024;
+constexpr int TC_THREADS = 288;                    // 4 producer warps, 1 MMA warp, 4 epilogue warps
+constexpr int TC_TMEM_COLS = 512;                  // 2 buffers x (hi*hi, cross terms) x 128 columns
+constexpr int TC_LAG = 4;                          // cp.async groups kept in flight
+constexpr long long TC_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+struct TcState {
+    int KP = 0;
+    __half *kop = nullptr;               // [2][316][KP][KP]  (hi, lo), scaled by 2^kexp
+    int kexp = 0;
+    float *amax = nullptr;               // max |phi| of the current evaluation
+    __half *phi = nullptr;        // [2][rows+1][KP]
+    size_t phi_rows = 0;
+    CUtensorMap tmap[2];
+    int4 *tiles = nullptr;
+    int ntiles = 0, tiles_cap = 0;
+    int *err = nullptr;
+    int *err_host = nullptr;
+    cudaEvent_t ev[2] = {};
+    float last_ms = 0;
+};
+
+// ---------------- PTX helpers ----------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false (and the error flag raised) after ~2 s
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > TC_WAIT_CYCLES) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// K-major operand with 64-byte rows, 64B swizzle: 8-row atoms of 512 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF)    // start address
+           | ((uint64_t)1 << 16)               // leading byte offset (unused for swizzled K-major)
+           | ((uint64_t)(512 >> 4) << 32)      // stride byte offset: 8 rows x 64 B
+           | ((uint64_t)1 << 46)               // descriptor version
+           | ((uint64_t)4 << 61);              // layout: 64-byte swizzle
+}
+
+// kind::f16 instruction descriptor: f16 x f16 -> f32, both K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+
+// power-of-two exponent that brings max |phi| just below 2^14
+__device__ __forceinline__ int phi_exp(const float *amax) {
+    int e = 0;
+    float m = *amax;
+    if (!(m > 0.f) || !isfinite(m)) return 0;
+    frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+    return 14 - e;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------- kernel ----------------
+
+struct TcArgs {
+    const __half *phi_hi, *phi_lo;  // [rows+1][KP], last row zero
+    const int *tboxes;                     // task boxes, class-major
+    const int4 *tiles;                     // (class, row0, nrows, 0)
+    const int *v_slot;                     // [nbox][189]
+    const int *class_ops;                  // [8][189]
+    float *chk;                            // [nbox*nrhs][kn]
+    const float *amax;                     // max |phi|
+    int kn, KP, nrhs, zero_row, kexp;
+    int *err;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_m2l_tc(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo, TcArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)smem;               // [5]
+    uint64_t *empty = full + TC_STAGES;              // [5]
+    uint64_t *wfull = empty + TC_STAGES;             // [2] work accumulator ready
+    uint64_t *wfree = wfull + 2;                     // [2] work accumulator drained
+    uint32_t *tmem_slot = (uint32_t *)(wfree + 2);
+    int *nact_s = (int *)(tmem_slot + 1);
+    short *act = (short *)(nact_s + 1);              // [189]
+    long long *drow = (long long *)(smem + 1024);    // [128]
+    int *sbox = (int *)(smem + 1024 + 8 * TC_N);     // [128]
+    uint8_t *stages = smem + TC_CTRL_BYTES;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int4 tile = a.tiles[blockIdx.x];
+    const int cls = tile.x, row0 = tile.y, nr = tile.z;
+    const int m0 = blockIdx.y * TC_M;
+    const int kchunks = a.KP / TC_K;
+
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; s++) {
+            mbar_init(&full[s], 128);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&wfull[b], 1);
+            mbar_init(&wfree[b], 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int n = tid; n < TC_N; n += TC_THREADS) {
+        if (n < nr) {
+            int row = row0 + n, tb = row / a.nrhs, rhs = row % a.nrhs, box = a.tboxes[tb];
+            drow[n] = (long long)box * a.nrhs + rhs;
+            sbox[n] = box;
+        } else {
+            drow[n] = -1;
+            sbox[n] = -1;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // slots with at least one source box in this tile
+    for (int s = tid; s < kVSlots; s += TC_THREADS) {
+        int any = 0;
+        if (a.class_ops[cls * kVSlots + s] >= 0)
+            for (int n = 0; n < nr && !any; n++) any = a.v_slot[(long long)sbox[n] * kVSlots + s] >= 0;
+        act[s] = (short)any;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int c = 0;
+        for (int s = 0; s < kVSlots; s++)
+            if (act[s]) act[c++] = (short)s;
+        *nact_s = c;
+    }
+    __syncthreads();
+    const int nact = *nact_s;
+    const uint32_t tmem = *tmem_slot;
+    const int total = nact * kchunks;
+
+    if (warp < 4) {
+        // ---- producers: gather Phi rows (cp.async) and TMA the operator tiles ----
+        const int r = tid;
+        const int rhs = (row0 + r) % a.nrhs, box = sbox[r];
+        const int ri = r & 7;
+        int it = 0;
+        for (; it < total; it++) {
+            const int st = it % TC_STAGES;
+            const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+            if (!mbar_wait(&empty[st], ph ^ 1u, a.err)) break;
+            const int s = act[it / kchunks], k0 = (it % kchunks) * TC_K;
+            uint8_t *sb = stages + (size_t)st * TC_STAGE_BYTES;
+            if (tid == 0) {
+                const int op = a.class_ops[cls * kVSlots + s];
+                mbar_expect_tx(&full[st], (uint32_t)(2 * TC_A_BYTES));
+                tma_load_2d(sb, &tA_hi, k0, op * a.KP + m0, &full[st]);
+                tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KP + m0, &full[st]);
+            }
+            int src = box >= 0 ? a.v_slot[(long long)box * kVSlots + s] : -1;
+            long long srow = src >= 0 ? (long long)src * a.nrhs + rhs : (long long)a.zero_row;
+            uint8_t *rowdst = sb + 2 * TC_A_BYTES + (r >> 3) * 512 + ri * 64;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const __half *g = (h ? a.phi_lo : a.phi_hi) + srow * a.KP + k0;
+                uint8_t *d = rowdst + h * TC_B_BYTES;
+#pragma unroll
+                for (int c = 0; c < 4; c++) cp_async16(d + ((c ^ ((ri >> 1) & 3)) << 4), g + c * 8);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (it >= TC_LAG) {
+                asm volatile("cp.async.wait_group 4;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&full[(it - TC_LAG) % TC_STAGES]);
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int j = (it > TC_LAG ? it - TC_LAG : 0); j < it; j++) mbar_arrive(&full[j % TC_STAGES]);
+    } else if (warp == 4) {
+        // ---- MMA issuer: one slot per work accumulator ----
+        if (lane == 0) {
+            int it = 0;
+            bool okm = true;
+            for (int si = 0; si < nact && okm; si++) {
+                const int wb = si & 1;
+                if (!mbar_wait(&wfree[wb], ((uint32_t)(si >> 1) & 1u) ^ 1u, a.err)) break;
+                tc_fence_after();
+                const uint32_t dbig = tmem + wb * TC_N, dsmall = tmem + 2 * TC_N + wb * TC_N;
+                for (int kc = 0; kc < kchunks; kc++, it++) {
+                    const int st = it % TC_STAGES;
+                    if (!mbar_wait(&full[st], (uint32_t)(it / TC_STAGES) & 1u, a.err)) {
+                        okm = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sb = smem_u32(stages + (size_t)st * TC_STAGE_BYTES);
+#pragma unroll
+                    for (int term = 0; term < 3; term++) {
+                        const int ah = term == 2, bh = term == 1;  // (hi,hi), (hi,lo), (lo,hi)
+#pragma unroll
+                        for (int k16 = 0; k16 < 2; k16++) {
+                            uint64_t ad = smem_desc_sw64(sb + ah * TC_A_BYTES + k16 * 32);
+                            uint64_t bd = smem_desc_sw64(sb + 2 * TC_A_BYTES + bh * TC_B_BYTES + k16 * 32);
+                            if (term == 0) tc_mma(dbig, ad, bd, (kc | k16) ? 1u : 0u);
+                            else tc_mma(dsmall, ad, bd, (kc | (term - 1) | k16) ? 1u : 0u);
+                        }
+                    }
+                    tc_commit(&empty[st]);
+                }
+                tc_commit(&wfull[wb]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: drain each slot's work accumulator into fp32 registers ----
+        const int sp = warp & 3;  // tensor-memory sub-partition of this warp
+        float acc[TC_N];
+#pragma unroll
+        for (int c = 0; c < TC_N; c++) acc[c] = 0.f;
+        bool oke = true;
+        for (int si = 0; si < nact && oke; si++) {
+            const int wb = si & 1;
+            bool w = mbar_wait(&wfull[wb], (uint32_t)(si >> 1) & 1u, a.err);
+            oke = __all_sync(0xffffffffu, w);  // tcgen05.ld is warp-collective
+            if (!oke) break;
+            tc_fence_after();
+#pragma unroll
+            for (int c0 = 0; c0 < TC_N; c0 += 16) {
+                float v[16], u[16];
+                const uint32_t ta = tmem + ((uint32_t)(sp * 32) << 16) + wb * TC_N + c0;
+                tc_ld16(ta, v);
+                tc_ld16(ta + 2 * TC_N, u);
+#pragma unroll
+                for (int j = 0; j < 16; j++) acc[c0 + j] += v[j] + u[j];
+            }
+            tc_fence_before();
+            mbar_arrive(&wfree[wb]);
+        }
+        const float unscale = ldexpf(1.0f, -(phi_exp(a.amax) + a.kexp));
+        const int krow = m0 + sp * 32 + lane;
+        if (krow < a.kn) {
+#pragma unroll
+            for (int c = 0; c < TC_N; c++) {
+                long long d = drow[c];
+                if (d >= 0) a.chk[d * a.kn + krow] = acc[c] * unscale;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------- set-up and launch ----------------
+
+// K_o * 2^kexp split into fp16 hi/lo, padded to KP x KP: out[h][op][i][j]
+__global__ void k_kop_split(int kernel, int n, int KP, int kexp, const double *__restrict__ g,
+                            const int *__restrict__ offs, __half *__restrict__ out) {
+    const int kk = kernel == 0 ? 1 : 3, kn = n * kk;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (long long)kM2LOps * KP * KP;
+    if (i >= total) return;
+    int m = (int)(i / ((long long)KP * KP));
+    int rem = (int)(i % ((long long)KP * KP)), r = rem / KP, c = rem % KP;
+    double v = 0.0;
+    if (r < kn && c < kn) {
+        int pa = r / kk, ca = r % kk, pb = c / kk, cb = c % kk;
+        double d[3];
+        for (int q = 0; q < 3; q++) d[q] = 0.525 * g[3 * pa + q] - (offs[3 * m + q] + 0.525 * g[3 * pb + q]);
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], ir = 1.0 / sqrt(r2);
+        if (kernel == 0) v = ir;
+        else v = (1.0 / (8.0 * 3.14159265358979323846)) * ((ca == cb ? ir : 0.0) + d[ca] * d[cb] * ir * ir * ir);
+    }
+    v = ldexp(v, kexp);
+    __half hi = __float2half_rn((float)v);
+    __half lo = __float2half_rn((float)(v - (double)__half2float(hi)));
+    out[i] = hi;
+    out[total + i] = lo;
+}
+
+__global__ void k_amax(const float *__restrict__ x, long long n, float *amax) {
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax((int *)amax, __float_as_int(m));  // non-negative floats order as ints
+}
+
+// upward densities (fp32 rows of kn) * 2^e -> fp16 hi/lo rows of KP, plus one zero row
+__global__ void k_phi_split(const float *__restrict__ up, long long rows, int kn, int KP, const float *amax,
+                            __half *__restrict__ hi, __half *__restrict__ lo) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (rows + 1) * KP;
+    if (i >= total) return;
+    long long r = i / KP;
+    int c = (int)(i % KP);
+    float x = (r < rows && c < kn) ? ldexpf(up[r * kn + c], phi_exp(amax)) : 0.f;
+    __half h = __float2half_rn(x);
+    hi[i] = h;
+    lo[i] = __float2half_rn(x - __half2float(h));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        PK_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p) throw Error(PKIFMM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+static bool tc_supported() {
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    return major == 10 && minor == 3;
+}
+
+void m2l_tc_release(Plan &P) {
+    TcState *t = P.tc;
+    if (!t) return;
+    cudaFree(t->kop);
+    cudaFree(t->phi);
+    cudaFree(t->tiles);
+    cudaFree(t->amax);
+    cudaFree(t->err);
+    cudaFreeHost(t->err_host);
+    if (t->ev[0]) cudaEventDestroy(t->ev[0]);
+    if (t->ev[1]) cudaEventDestroy(t->ev[1]);
+    delete t;
+    P.tc = nullptr;
+}
+
+void m2l_tc_prepare(Plan &P) {
+    if (!tc_supported()) throw Error(PKIFMM_ERR_UNSUPPORTED, "MIXED path needs an sm_103 GPU (tcgen05)");
+    TcState *t = new TcState;
+    P.tc = t;
+    t->KP = (P.kn + TC_M - 1) / TC_M * TC_M;
+    // |K_o| <= 1/0.95 (Laplace) or 2/(8 pi 0.95) (Stokes) over the 316 offsets
+    // (closest points 0.95 box edges apart): scale the largest entry to about 2^12
+    t->kexp = P.kernel == 0 ? 12 : 15;
+    const int KP = t->KP;
+    size_t nk = (size_t)kM2LOps * KP * KP;
+    PK_CUDA(cudaMalloc(&t->kop, 2 * nk * sizeof(__half)));
+    std::vector<int> offs;
+    for (int x = -3; x <= 3; x++)
+        for (int y = -3; y <= 3; y++)
+            for (int z = -3; z <= 3; z++) {
+                if (std::max(std::abs(x), std::max(std::abs(y), std::abs(z))) <= 1) continue;
+                offs.push_back(x);
+                offs.push_back(y);
+                offs.push_back(z);
+            }
+    int *doffs = nullptr;
+    PK_CUDA(cudaMalloc(&doffs, sizeof(int) * offs.size()));
+    PK_CUDA(cudaMemcpy(doffs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice));
+    count_launch(), k_kop_split<<<(unsigned)((nk + 255) / 256), 256>>>(P.kernel, P.n, KP, t->kexp, P.g64.p, doffs,
+                                                                        t->kop);
+    PK_CUDA(cudaGetLastError());
+    PK_CUDA(cudaDeviceSynchronize());
+    cudaFree(doffs);
+    EncodeTiledFn enc = encode_fn();
+    for (int h = 0; h < 2; h++) {
+        cuuint64_t dims[2] = {(cuuint64_t)KP, (cuuint64_t)kM2LOps * KP};
+        cuuint64_t strides[1] = {(cuuint64_t)KP * 2};
+        cuuint32_t box[2] = {TC_K, TC_M};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = enc(&t->tmap[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, t->kop + h * nk, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) throw Error(PKIFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    }
+    PK_CUDA(cudaMalloc(&t->amax, sizeof(float)));
+    PK_CUDA(cudaMalloc(&t->err, sizeof(int)));
+    PK_CUDA(cudaMemset(t->err, 0, sizeof(int)));
+    PK_CUDA(cudaMallocHost(&t->err_host, sizeof(int)));
+    PK_CUDA(cudaEventCreate(&t->ev[0]));
+    PK_CUDA(cudaEventCreate(&t->ev[1]));
+    PK_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+}
+
+bool m2l_tc_run(Plan &P, cudaStream_t s) {
+    TcState *t = P.tc;
+    if (!t) return false;
+    const Task &task = P.t_m2l;
+    if (task.nrows == 0) return true;
+    const int KP = t->KP, nr = P.nrhs;
+    // Phi hi/lo with a trailing zero row
+    long long rows = (long long)P.tree.nbox * nr;
+    if ((size_t)(rows + 1) > t->phi_rows) {
+        cudaFree(t->phi);
+        t->phi = nullptr;
+        t->phi_rows = (size_t)(rows + 1) + (size_t)(rows + 1) / 4;
+        PK_CUDA(cudaMalloc(&t->phi, 2 * t->phi_rows * KP * sizeof(__half)));
+    }
+    __half *hi = t->phi, *lo = t->phi + t->phi_rows * KP;
+    long long tot = (rows + 1) * KP;
+    PK_CUDA(cudaMemsetAsync(t->amax, 0, sizeof(float), s));
+    count_launch(), k_amax<<<1024, 256, 0, s>>>(P.up32.p, rows * P.kn, t->amax);
+    count_launch(), k_phi_split<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.up32.p, rows, P.kn, KP, t->amax, hi,
+                                                                               lo);
+    // tiles of 256 (box, rhs) columns within each octant class
+    std::vector<int4> tiles;
+    for (int c = 0, r0 = 0; c < task.nclass; c++) {
+        int rows_c = task.class_count[c] * nr;
+        for (int r = 0; r < rows_c; r += TC_N) tiles.push_back(make_int4(c, r0 + r, std::min(TC_N, rows_c - r), 0));
+        r0 += rows_c;
+    }
+    if ((int)tiles.size() > t->tiles_cap) {
+        cudaFree(t->tiles);
+        t->tiles_cap = (int)tiles.size() + 64;
+        PK_CUDA(cudaMalloc(&t->tiles, sizeof(int4) * t->tiles_cap));
+    }
+    t->ntiles = (int)tiles.size();
+    PK_CUDA(cudaMemcpyAsync(t->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
+    TcArgs a;
+    a.phi_hi = hi;
+    a.phi_lo = lo;
+    a.tboxes = task.boxes.p;
+    a.tiles = t->tiles;
+    a.v_slot = P.tree.v_slot.p;
+    a.class_ops = P.class_slot_op.p;
+    a.chk = P.chk32.p;
+    a.kn = P.kn;
+    a.KP = KP;
+    a.nrhs = nr;
+    a.zero_row = (int)rows;
+    a.amax = t->amax;
+    a.kexp = t->kexp;
+    a.err = t->err;
+    dim3 grid(t->ntiles, KP / TC_M);
+    PK_CUDA(cudaEventRecord(t->ev[0], s));
+    count_launch(), k_m2l_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(t->tmap[0], t->tmap[1], a);
+    PK_CUDA(cudaGetLastError());
+    PK_CUDA(cudaEventRecord(t->ev[1], s));
+    PK_CUDA(cudaMemcpyAsync(t->err_host, t->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaStreamSynchronize(s));  // host tile vector and the error flag
+    PK_CUDA(cudaEventElapsedTime(&t->last_ms, t->ev[0], t->ev[1]));
+    if (*t->err_host) {
+        PK_CUDA(cudaMemset(t->err, 0, sizeof(int)));
+        throw Error(PKIFMM_ERR_TIMEOUT, "tensor-core M2L: a bounded pipeline wait gave up");
+    }
+    return true;
+}
+
+float m2l_tc_last_ms(Plan &P) { return P.tc ? P.tc->last_ms : 0.f; }
+
+bool m2l_tc_device_supported() { return tc_supported(); }
 
 }  // namespace pk

@@ -119,8 +119,7 @@ void upload_operators(Plan &P) {
         upload(P.dc2e_b32, H.dc2e_b);
         upload(P.m2m32, H.m2m);
         upload(P.l2l32, H.l2l);
-        P.m2l32.reserve(kM2LOps * kn2);
-        count_launch(), k_m2l_ops<float><<<nblk(tot, 256), 256>>>(P.kernel, P.n, P.g64.p, doffs.p, P.m2l32.p);
+        (void)tot;
         // the root far field and its solve stay in binary64
         upload(P.dc2e_a, H.dc2e_a);
         upload(P.dc2e_b, H.dc2e_b);
@@ -244,6 +243,8 @@ static void make_task(Task &t, const std::vector<std::vector<int>> &by_class, in
     t.nclass = (int)by_class.size();
     t.nslots = nslots;
     t.h_boxes.clear();
+    t.class_count.clear();
+    for (auto &v : by_class) t.class_count.push_back((int)v.size());
     std::vector<int4> tiles;
     for (int c = 0; c < t.nclass; c++) {
         int row0 = (int)t.h_boxes.size() * nrhs;
@@ -758,8 +759,7 @@ void run_m2l(Plan &P, cudaStream_t s) {
     if (P.precision == PKIFMM_FP64) {
         gemm<double>(P.t_m2l, P.tree.v_slot.p, kVSlots, P.m2l.p, kn2, P.up64.p, P.chk64.p, kn, nr, 0, s);
     } else {
-        if (!m2l_tc_run(P, s))
-            gemm<float>(P.t_m2l, P.tree.v_slot.p, kVSlots, P.m2l32.p, kn2, P.up32.p, P.chk32.p, kn, nr, 0, s);
+        if (!m2l_tc_run(P, s)) throw Error(PKIFMM_ERR_UNSUPPORTED, "tensor-core M2L not prepared");
     }
 }
 

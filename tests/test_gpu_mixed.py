@@ -1,0 +1,69 @@
+"""MIXED path (binary32 kernel sums, tensor-core split-bf16 M2L, binary64 root
+operator) vs the FP64 oracle and vs the FP64 path on the same inputs."""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import rel_l2, run
+from paper_1705_02043_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cache(tmp_path_factory):
+    return str(tmp_path_factory.mktemp("opcache_mixed"))
+
+
+def _sample(n, k, seed=0):
+    return np.sort(np.random.default_rng(seed).choice(n, k, replace=False))
+
+
+def test_mixed_stokes_tp_p8(cache):
+    """Stokes TP, net force removed, p = 8: the mixed path is as accurate as the
+    FP64 path against the oracle (both carry the p = 8 method error, ~1.3e-5,
+    in different directions).  The tensor-core M2L spans many tiles and a
+    ragged last tile per octant class."""
+    n = 40000
+    x, f = w.stokes_uniform(n, seed=21)
+    idx = _sample(n, 400)
+    ref = oracle.stokes_tp(x, f[0], x[idx])
+    um = run(1, 7, x, f[0], x, p=8, leaf=64, precision=1, cache_dir=cache)
+    ud = run(1, 7, x, f[0], x, p=8, leaf=64, precision=0, cache_dir=cache)
+    em, ed = rel_l2(um[idx], ref), rel_l2(ud[idx], ref)
+    print(f"stokes TP p=8: mixed {em:.3e} fp64 {ed:.3e} mixed-vs-fp64 {rel_l2(um, ud):.3e}")
+    assert em < 2e-5 and em < 1.5 * ed
+    assert rel_l2(um, ud) < 3e-5
+
+
+def test_mixed_laplace_tp_p6(cache):
+    n = 30000
+    x, q = w.laplace_uniform(n, seed=22)
+    idx = _sample(n, 500)
+    ref = oracle.laplace_tp(x, q[0], x[idx])
+    um = run(0, 7, x, q[0], x, p=6, leaf=48, precision=1, cache_dir=cache)
+    e = rel_l2(um[idx], ref)
+    print(f"laplace TP p=6 mixed {e:.3e}")
+    assert e < 5e-5
+
+
+def test_mixed_adaptive_sp(cache):
+    """Clustered points (W and X lists), singly periodic Laplace."""
+    x, q = w.clustered_slab(20000, seed=23, nclusters=8, sigma=0.03, zlo=0.0, zhi=1.0, kdim=1)
+    idx = _sample(len(x), 400)
+    ref = oracle.laplace_sp(x, q, x[idx], axis=1)
+    um = run(0, 2, x, q, x, p=8, leaf=40, precision=1, cache_dir=cache)
+    e = rel_l2(um[idx], ref)
+    print(f"laplace SP clustered p=8 mixed {e:.3e}")
+    assert e < 2e-5
+
+
+def test_mixed_multiple_rhs(cache):
+    """Batched density vectors share one geometry: each column matches its
+    single-vector evaluation."""
+    x, f = w.stokes_uniform(12000, seed=24, nrhs=4)
+    u4 = run(1, 7, x, f, x, p=6, leaf=48, precision=1, cache_dir=cache)
+    for r in range(4):
+        u1 = run(1, 7, x, f[r], x, p=6, leaf=48, precision=1, cache_dir=cache)
+        assert rel_l2(u4[r], u1) < 1e-6
