@@ -161,6 +161,32 @@ int pkifmm_backward_error(int kernel, int p, double *err_out);
  * periodicities as pkifmm_plan_create (non-zero). */
 int pkifmm_root_operator(int kernel, unsigned periodic_axes, int p, int ell, double *m_out);
 
+/* Stable Morton ordering of points without allocating any device memory.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc -- a process whose device memory is entirely owned by another
+ * framework's memory pool, a real-time loop that forbids allocation after
+ * start-up, or host code running where CUDA allocation calls are not
+ * permitted.  It computes what pkifmm_evaluate's first step computes for its
+ * sources: points normalised to [box_lo, box_lo + box_len)^3, wrapped along
+ * periodic axes, keyed by their cell at `depth` (Morton order, octant bits
+ * x = 1, y = 2, z = 4) and sorted stably, ties in input order.
+ *   xyz   DEVICE [n][3] binary64 positions (caller-owned)
+ *   perm  DEVICE [n] int32 output: perm[i] = input index of the i-th point
+ *   n     0 <= n <= 131072; larger n returns PKIFMM_ERR_INVALID_ARG before
+ *         any GPU work (the scratch is fixed)
+ *   depth 1..15; box_lo is a host pointer; cuda_stream as in pkifmm_evaluate
+ * Scratch: one fixed array of about 6 MB in device memory, defined with the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The first call on a device looks up its address on that device
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array and leaves its contents behind, so calls whose
+ * GPU work overlaps (different streams or threads at once) race and give
+ * wrong results.  Returns after the stream has finished the work; errors as
+ * pkifmm_evaluate (OUT_OF_BOX for a point outside a free axis, INVALID_ARG
+ * for a non-finite coordinate). */
+int pkifmm_morton_order_noalloc(int64_t n, const double *xyz, const double box_lo[3], double box_len,
+                                unsigned periodic_axes, int depth, int32_t *perm, void *cuda_stream);
+
 void pkifmm_plan_destroy(pkifmm_plan plan);
 const char *pkifmm_strerror(int code);
 

@@ -53,6 +53,7 @@ def load_library():
             lib.pkifmm_plan_destroy.restype = None
             lib.pkifmm_strerror.argtypes = [i]
             lib.pkifmm_strerror.restype = ctypes.c_char_p
+            lib.pkifmm_morton_order_noalloc.argtypes = [i64, P, P, d, u, i, P, P]
             lib.pkifmm_m2l_tensor_core_enabled.argtypes = []
             lib.pkifmm_launch_count.argtypes = []
             lib.pkifmm_launch_count.restype = ctypes.c_int64
@@ -155,6 +156,13 @@ def pkifmm_root_operator(kernel, periodic_axes, p, ell):
     out = np.zeros((kn, kn))
     _check(load_library().pkifmm_root_operator(kernel, periodic_axes, p, ell, _ptr(out)))
     return out
+
+
+def pkifmm_morton_order_noalloc(n, xyz, box_lo, box_len, periodic_axes, depth, perm, stream=None):
+    """Allocation-free stable Morton ordering; xyz [n,3] float64 and perm [n] int32 device tensors."""
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64)
+    return _check(load_library().pkifmm_morton_order_noalloc(n, _ptr(xyz), _ptr(lo), float(box_len), periodic_axes,
+                                                             depth, _ptr(perm), stream))
 
 
 def pkifmm_plan_destroy(plan):

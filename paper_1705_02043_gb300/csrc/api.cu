@@ -199,6 +199,10 @@ int evaluate_impl(Plan &P, int64_t S, const double *src, const double *dens, int
 
 }  // namespace
 
+namespace pk {
+int set_last_error(int code, const std::string &msg) { return fail(code, msg); }
+}  // namespace pk
+
 extern "C" {
 
 int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, const double box_lo[3],

@@ -17,6 +17,8 @@
 //         class of B);
 //   W(B), B leaf: boxes A+p finer than B, not adjacent, parent(A)+p adjacent;
 //   X(B): leaves A+p coarser than B, adjacent to parent(B), not adjacent to B.
+#include <mutex>
+
 #include "internal.h"
 
 namespace pk {
@@ -647,4 +649,108 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
     xn.release();
 }
 
+// ---------------- Morton order without allocation ----------------
+//
+// Some callers cannot call cudaMalloc: a process whose device memory is
+// entirely owned by another framework's pool, a real-time loop that forbids
+// allocation after start-up, or host code running where CUDA allocation
+// calls are not permitted.  pkifmm_morton_order_noalloc gives them the
+// stable Morton ordering of points (the first step of the evaluation) using
+// only the fixed scratch below, which every GPU that loads this library holds
+// until the process exits.  Host code must not pass the array's name to a
+// kernel (in host code it is a stand-in, not a device address): its device
+// address is looked up once per device with cudaGetSymbolAddress.
+
+constexpr long long kNoAllocMaxPoints = 1LL << 17;  // 131,072 points
+constexpr int kNoAllocMaxBlocks = (int)((kNoAllocMaxPoints + RS_TILE - 1) / RS_TILE);
+
+struct NoAllocScratch {
+    unsigned long long key[2][kNoAllocMaxPoints];
+    int idx[2][kNoAllocMaxPoints];
+    double xn[3 * kNoAllocMaxPoints];
+    int hist[16 * kNoAllocMaxBlocks];
+    int hoff[16 * kNoAllocMaxBlocks + 1];
+    int err[4];
+};
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+// exclusive scan of n <= 1024 ints in one block (no scratch beyond out[n+1])
+__global__ void k_scan_small_noalloc(const int *in, int *out, int n) {
+    __shared__ int s[1024];
+    int t = threadIdx.x;
+    int v = t < n ? in[t] : 0;
+    s[t] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int u = t >= o ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += u;
+        __syncthreads();
+    }
+    if (t < n) out[t] = s[t] - v;
+    if (t == 1023) out[n] = s[1023];
+}
+
 }  // namespace pk
+
+namespace pk {
+int set_last_error(int code, const std::string &msg);
+}
+
+namespace {
+std::mutex g_noalloc_mu;
+pk::NoAllocScratch *g_noalloc_ptr[64] = {};
+}
+
+extern "C" int pkifmm_morton_order_noalloc(int64_t n, const double *xyz, const double box_lo[3], double box_len,
+                                           unsigned periodic_axes, int depth, int32_t *perm, void *cuda_stream) {
+    using namespace pk;
+    if (n < 0 || n > kNoAllocMaxPoints)
+        return set_last_error(PKIFMM_ERR_INVALID_ARG,
+                              "pkifmm_morton_order_noalloc: n = " + std::to_string((long long)n) +
+                                  " is outside 0.." + std::to_string(kNoAllocMaxPoints) +
+                                  ", the size of its fixed device scratch");
+    if (!box_lo || !(box_len > 0) || periodic_axes > 7 || depth < 1 || depth > 15)
+        return set_last_error(PKIFMM_ERR_INVALID_ARG, "pkifmm_morton_order_noalloc: bad box, periodicity or depth");
+    if (n == 0) return PKIFMM_OK;
+    if (!xyz || !perm) return set_last_error(PKIFMM_ERR_INVALID_ARG, "pkifmm_morton_order_noalloc: NULL array");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return set_last_error(PKIFMM_ERR_CUDA, "pkifmm_morton_order_noalloc: no usable current device");
+    NoAllocScratch *sc = nullptr;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+                return set_last_error(PKIFMM_ERR_CUDA, "pkifmm_morton_order_noalloc: scratch address lookup failed");
+            g_noalloc_ptr[dev] = (NoAllocScratch *)p;
+        }
+        sc = g_noalloc_ptr[dev];
+    }
+    // the scratch keeps the previous call's contents: clear the error flags
+    if (cudaMemsetAsync(sc->err, 0, sizeof(sc->err), s) != cudaSuccess) return PKIFMM_ERR_CUDA;
+    unsigned nb = blocks(n, 256);
+    count_launch(), k_keys<<<nb, 256, 0, s>>>(xyz, n, box_lo[0], box_lo[1], box_lo[2], box_len, periodic_axes, depth,
+                                             sc->xn, sc->key[0], sc->idx[0], sc->err);
+    int tiles = (int)((n + RS_TILE - 1) / RS_TILE), cur = 0;
+    for (int sh = 0; sh < 3 * depth; sh += 4) {
+        count_launch(), k_rs_count<<<tiles, RS_T, 0, s>>>(sc->key[cur], (int)n, sh, sc->hist, tiles);
+        count_launch(), k_scan_small_noalloc<<<1, 1024, 0, s>>>(sc->hist, sc->hoff, 16 * tiles);
+        count_launch(), k_rs_scatter<<<tiles, RS_T, 0, s>>>(sc->key[cur], sc->idx[cur], sc->key[cur ^ 1],
+                                                            sc->idx[cur ^ 1], (int)n, sh, sc->hoff, tiles);
+        cur ^= 1;
+    }
+    if (cudaMemcpyAsync(perm, sc->idx[cur], sizeof(int) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return PKIFMM_ERR_CUDA;
+    int err[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(err, sc->err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return PKIFMM_ERR_CUDA;
+    if (err[0]) return set_last_error(PKIFMM_ERR_INVALID_ARG, "pkifmm_morton_order_noalloc: non-finite coordinate");
+    if (err[1]) return set_last_error(PKIFMM_ERR_OUT_OF_BOX, "pkifmm_morton_order_noalloc: point outside a free axis");
+    return PKIFMM_OK;
+}
