@@ -18,7 +18,7 @@
 // and the 2^-11 smaller cross products go to separate accumulators, so the
 // large one takes only 2 KP/32 steps per slot.
 //
-// Pipeline (5 stages of 32 KB): warps 0-3 gather the Phi rows with 16-byte
+// Pipeline (6 stages of 32 KB): warps 0-3 gather the Phi rows with 16-byte
 // cp.async into the 64B-swizzled K-major layout and one thread issues the TMA
 // loads of the K_o tiles; warp 4 issues tcgen05.mma from one thread and frees
 // each stage with tcgen05.commit; warps 5-8 drain the work accumulators and
@@ -27,6 +27,7 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "internal.h"
@@ -36,7 +37,7 @@ namespace pk {
 constexpr int TC_N = 128;                          // (box, rhs) columns per CTA
 constexpr int TC_M = 128;                          // kn rows per CTA
 constexpr int TC_K = 32;                           // K chunk: 64 bytes of fp16 per row
-constexpr int TC_STAGES = 5;
+constexpr int TC_STAGES = 6;
 constexpr int TC_A_BYTES = TC_M * TC_K * 2;        // 8 KB per split
 constexpr int TC_B_BYTES = TC_N * TC_K * 2;        // 8 KB per split
 constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 32 KB
@@ -45,7 +46,7 @@ constexpr int TC_SLACK = 16384;
 constexpr int TC_SMEM = TC_CTRL_BYTES + TC_STAGES * TC_STAGE_BYTES + TC_SLACK + 1024;
 constexpr int TC_THREADS = 288;                    // 4 producer warps, 1 MMA warp, 4 epilogue warps
 constexpr int TC_TMEM_COLS = 512;                  // 2 buffers x (hi*hi, cross terms) x 128 columns
-constexpr int TC_LAG = 4;                          // cp.async groups kept in flight
+constexpr int TC_LAG = 5;                          // cp.async groups kept in flight
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 struct TcState {
@@ -62,6 +63,13 @@ struct TcState {
     int *err_host = nullptr;
     cudaEvent_t ev[2] = {};
     float last_ms = 0;
+    int *slot_off = nullptr;             // [8][189][3]
+    __half *grid = nullptr;              // parity sub-grids of the full levels (hi, then lo, per level)
+    size_t grid_cap = 0;
+    int4 *gtiles = nullptr;
+    size_t gtiles_cap = 0;
+    int *gboxes = nullptr;
+    size_t gboxes_cap = 0;
 };
 
 // ---------------- PTX helpers ----------------
@@ -112,6 +120,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned long long morton3_dev(int x, int y, int z) {
+    unsigned long long r = 0;
+    for (int b = 0; b < 21; b++)
+        r |= ((unsigned long long)((x >> b) & 1) << (3 * b)) | ((unsigned long long)((y >> b) & 1) << (3 * b + 1)) |
+             ((unsigned long long)((z >> b) & 1) << (3 * b + 2));
+    return r;
+}
+
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
@@ -153,34 +178,36 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float *v) {
-    uint32_t r[16];
+__device__ __forceinline__ void tc_ld16_nowait(uint32_t taddr, uint32_t *r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---------------- kernel ----------------
 
 struct TcArgs {
-    const __half *phi_hi, *phi_lo;  // [rows+1][KP], last row zero
-    const int *tboxes;                     // task boxes, class-major
-    const int4 *tiles;                     // (class, row0, nrows, 0)
+    const __half *phi_hi, *phi_lo;  // gather mode: [rows+1][KP], last row zero
+    const int *tboxes;                     // gather mode: task boxes, class-major
+    const int4 *tiles;                     // gather: (class, row0, nrows, 0); grid: (class | rblock << 3, i0, j0, k0)
     const int *v_slot;                     // [nbox][189]
     const int *class_ops;                  // [8][189]
+    const int *slot_off;                   // [8][189][3] box offsets of the V slots
     float *chk;                            // [nbox*nrhs][kn]
     const float *amax;                     // max |phi|
     int kn, KP, nrhs, zero_row, kexp;
+    // grid mode (a level where every box exists): Phi as 8 parity sub-grids with a 2-box halo
+    int grid, lvl_begin, zd, bx, by, bz, rb;
     int *err;
 };
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_m2l_tc(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo, TcArgs a) {
+    k_m2l_tc(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+             const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)smem;               // [5]
@@ -195,14 +222,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint8_t *stages = smem + TC_CTRL_BYTES;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int4 tile = a.tiles[blockIdx.x];
-    const int cls = tile.x, row0 = tile.y, nr = tile.z;
-    const int m0 = blockIdx.y * TC_M;
+    // consecutive CTAs: the M tiles of one column tile (they share the
+    // gathered rows), then the next column tile of the same octant class
+    // (same operator stream), so one class fills a wave
+    const int mtiles = a.KP / TC_M;
+    const int4 tile = a.tiles[blockIdx.x / mtiles];
+    const int cls = a.grid ? (tile.x & 7) : tile.x;
+    const int row0 = a.grid ? 0 : tile.y, nr = a.grid ? TC_N : tile.z;
+    const int m0 = (blockIdx.x % mtiles) * TC_M;
     const int kchunks = a.KP / TC_K;
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; s++) {
-            mbar_init(&full[s], 128);
+            mbar_init(&full[s], a.grid ? 1 : 128);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; b++) {
@@ -218,7 +250,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     for (int n = tid; n < TC_N; n += TC_THREADS) {
-        if (n < nr) {
+        if (a.grid) {
+            // column n = rhs + rb (x + bx (y + by z)) of a block of class-cls boxes
+            const int rl = n % a.rb, b = n / a.rb;
+            const int x = b % a.bx, y = (b / a.bx) % a.by, z = b / (a.bx * a.by);
+            const int px = (cls & 1) + 2 * (tile.y + x), py = (cls >> 1 & 1) + 2 * (tile.z + y),
+                      pz = (cls >> 2 & 1) + 2 * (tile.w + z);
+            const int box = a.lvl_begin + (int)morton3_dev(px, py, pz);
+            drow[n] = (long long)box * a.nrhs + (tile.x >> 3) * a.rb + rl;
+            sbox[n] = box;
+        } else if (n < nr) {
             int row = row0 + n, tb = row / a.nrhs, rhs = row % a.nrhs, box = a.tboxes[tb];
             drow[n] = (long long)box * a.nrhs + rhs;
             sbox[n] = box;
@@ -233,8 +274,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // slots with at least one source box in this tile
     for (int s = tid; s < kVSlots; s += TC_THREADS) {
         int any = 0;
-        if (a.class_ops[cls * kVSlots + s] >= 0)
-            for (int n = 0; n < nr && !any; n++) any = a.v_slot[(long long)sbox[n] * kVSlots + s] >= 0;
+        if (a.class_ops[cls * kVSlots + s] >= 0) {
+            if (a.grid) any = 1;  // missing sources are zero halo rows
+            else
+                for (int n = 0; n < nr && !any; n++) any = a.v_slot[(long long)sbox[n] * kVSlots + s] >= 0;
+        }
         act[s] = (short)any;
     }
     __syncthreads();
@@ -249,26 +293,62 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
     const int total = nact * kchunks;
 
-    if (warp < 4) {
+    if (warp < 4 && a.grid) {
+        // ---- producer (grid mode): one thread, TMA for both operands ----
+        if (tid == 0) {
+            int cur_si = -1, op = 0, cx = 0, cy = 0, cz = 0;
+            for (int it = 0; it < total; it++) {
+                const int st = it % TC_STAGES;
+                const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+                if (!mbar_wait(&empty[st], ph ^ 1u, a.err)) break;
+                const int si = it / kchunks, k0 = (it % kchunks) * TC_K;
+                if (si != cur_si) {
+                    cur_si = si;
+                    const int s = act[si];
+                    op = a.class_ops[cls * kVSlots + s];
+                    // sources of the block at offset o: parity sub-grid (c + o) mod 2, origin floor((c + o) / 2)
+                    const int *o = a.slot_off + (cls * kVSlots + s) * 3;
+                    const int qx = (cls & 1) + o[0], qy = (cls >> 1 & 1) + o[1], qz = (cls >> 2 & 1) + o[2];
+                    const int par = (qx & 1) | (qy & 1) << 1 | (qz & 1) << 2;
+                    cx = ((qx - (qx & 1)) >> 1) + tile.y + 2;
+                    cy = ((qy - (qy & 1)) >> 1) + tile.z + 2;
+                    cz = par * a.zd + ((qz - (qz & 1)) >> 1) + tile.w + 2;
+                }
+                uint8_t *sb = stages + (size_t)st * TC_STAGE_BYTES;
+                mbar_expect_tx(&full[st], (uint32_t)(2 * TC_A_BYTES + 2 * TC_B_BYTES));
+                tma_load_2d(sb, &tA_hi, k0, op * a.KP + m0, &full[st]);
+                tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KP + m0, &full[st]);
+                const int r0 = (tile.x >> 3) * a.rb;
+                tma_load_5d(sb + 2 * TC_A_BYTES, &tB_hi, k0, r0, cx, cy, cz, &full[st]);
+                tma_load_5d(sb + 2 * TC_A_BYTES + TC_B_BYTES, &tB_lo, k0, r0, cx, cy, cz, &full[st]);
+                mbar_arrive(&full[st]);
+            }
+        }
+    } else if (warp < 4) {
         // ---- producers: gather Phi rows (cp.async) and TMA the operator tiles ----
         const int r = tid;
         const int rhs = (row0 + r) % a.nrhs, box = sbox[r];
         const int ri = r & 7;
-        int it = 0;
+        int it = 0, cur_si = -1, op = 0;
+        long long srow = 0;
         for (; it < total; it++) {
             const int st = it % TC_STAGES;
             const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
             if (!mbar_wait(&empty[st], ph ^ 1u, a.err)) break;
-            const int s = act[it / kchunks], k0 = (it % kchunks) * TC_K;
+            const int si = it / kchunks, k0 = (it % kchunks) * TC_K;
+            if (si != cur_si) {  // new slot: its operator and this row's source
+                cur_si = si;
+                const int s = act[si];
+                op = a.class_ops[cls * kVSlots + s];
+                int src = box >= 0 ? a.v_slot[(long long)box * kVSlots + s] : -1;
+                srow = src >= 0 ? (long long)src * a.nrhs + rhs : (long long)a.zero_row;
+            }
             uint8_t *sb = stages + (size_t)st * TC_STAGE_BYTES;
             if (tid == 0) {
-                const int op = a.class_ops[cls * kVSlots + s];
                 mbar_expect_tx(&full[st], (uint32_t)(2 * TC_A_BYTES));
                 tma_load_2d(sb, &tA_hi, k0, op * a.KP + m0, &full[st]);
                 tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KP + m0, &full[st]);
             }
-            int src = box >= 0 ? a.v_slot[(long long)box * kVSlots + s] : -1;
-            long long srow = src >= 0 ? (long long)src * a.nrhs + rhs : (long long)a.zero_row;
             uint8_t *rowdst = sb + 2 * TC_A_BYTES + (r >> 3) * 512 + ri * 64;
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -279,7 +359,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
             if (it >= TC_LAG) {
-                asm volatile("cp.async.wait_group 4;" ::: "memory");
+                asm volatile("cp.async.wait_group 5;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(&full[(it - TC_LAG) % TC_STAGES]);
             }
@@ -337,12 +417,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
 #pragma unroll
             for (int c0 = 0; c0 < TC_N; c0 += 16) {
-                float v[16], u[16];
+                uint32_t v[16], u[16];
                 const uint32_t ta = tmem + ((uint32_t)(sp * 32) << 16) + wb * TC_N + c0;
-                tc_ld16(ta, v);
-                tc_ld16(ta + 2 * TC_N, u);
+                tc_ld16_nowait(ta, v);
+                tc_ld16_nowait(ta + 2 * TC_N, u);
+                tc_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; j++) acc[c0 + j] += v[j] + u[j];
+                for (int j = 0; j < 16; j++) acc[c0 + j] += __uint_as_float(v[j]) + __uint_as_float(u[j]);
             }
             tc_fence_before();
             mbar_arrive(&wfree[wb]);
@@ -414,6 +495,41 @@ __global__ void k_phi_split(const float *__restrict__ up, long long rows, int kn
     lo[i] = __float2half_rn(x - __half2float(h));
 }
 
+// Phi of one full level as 8 parity sub-grids with a 2-box halo:
+// row (((par * Zd + z') * Yd + y') * Xd + x') * nrhs + rhs holds the box at
+// position 2 (x' - 2) + (par & 1), ... (wrapped on periodic axes, zero outside
+// on free axes), scaled and split like k_phi_split.
+__global__ void k_phi_grid(const float *__restrict__ up, int lvl_begin, int n, int nrhs, int kn, int KP, unsigned per,
+                           const float *amax, long long rows, __half *__restrict__ hi, __half *__restrict__ lo) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= rows * KP) return;
+    const long long row = i / KP;
+    const int k = (int)(i % KP);
+    const int d = n / 2 + 4;
+    long long rest = row / nrhs;
+    const int rhs = (int)(row % nrhs);
+    const int xq = (int)(rest % d);
+    rest /= d;
+    const int yq = (int)(rest % d);
+    rest /= d;
+    const int zq = (int)(rest % d);
+    const int par = (int)(rest / d);
+    int pos[3] = {2 * (xq - 2) + (par & 1), 2 * (yq - 2) + (par >> 1 & 1), 2 * (zq - 2) + (par >> 2 & 1)};
+    bool inside = true;
+    for (int a = 0; a < 3; a++) {
+        if (per >> a & 1) pos[a] = ((pos[a] % n) + n) % n;
+        else if (pos[a] < 0 || pos[a] >= n) inside = false;
+    }
+    float x = 0.f;
+    if (inside && k < kn) {
+        const int box = lvl_begin + (int)morton3_dev(pos[0], pos[1], pos[2]);
+        x = ldexpf(up[((long long)box * nrhs + rhs) * kn + k], phi_exp(amax));
+    }
+    __half h = __float2half_rn(x);
+    hi[i] = h;
+    lo[i] = __float2half_rn(x - __half2float(h));
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -445,6 +561,10 @@ void m2l_tc_release(Plan &P) {
     cudaFree(t->phi);
     cudaFree(t->tiles);
     cudaFree(t->amax);
+    cudaFree(t->slot_off);
+    cudaFree(t->grid);
+    cudaFree(t->gtiles);
+    cudaFree(t->gboxes);
     cudaFree(t->err);
     cudaFreeHost(t->err_host);
     if (t->ev[0]) cudaEventDestroy(t->ev[0]);
@@ -492,6 +612,23 @@ void m2l_tc_prepare(Plan &P) {
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) throw Error(PKIFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
+    {  // box offset of each V slot, per octant class (the enumeration of the slot tables)
+        std::vector<int> so(8 * kVSlots * 3, 0);
+        for (int c = 0; c < 8; c++) {
+            int cb[3] = {c & 1, c >> 1 & 1, c >> 2 & 1}, sl = 0;
+            for (int x = -2 - cb[0]; x <= 3 - cb[0]; x++)
+                for (int y = -2 - cb[1]; y <= 3 - cb[1]; y++)
+                    for (int z = -2 - cb[2]; z <= 3 - cb[2]; z++) {
+                        if (std::max(std::abs(x), std::max(std::abs(y), std::abs(z))) <= 1) continue;
+                        so[(c * kVSlots + sl) * 3] = x;
+                        so[(c * kVSlots + sl) * 3 + 1] = y;
+                        so[(c * kVSlots + sl) * 3 + 2] = z;
+                        sl++;
+                    }
+        }
+        PK_CUDA(cudaMalloc(&t->slot_off, sizeof(int) * so.size()));
+        PK_CUDA(cudaMemcpy(t->slot_off, so.data(), sizeof(int) * so.size(), cudaMemcpyHostToDevice));
+    }
     PK_CUDA(cudaMalloc(&t->amax, sizeof(float)));
     PK_CUDA(cudaMalloc(&t->err, sizeof(int)));
     PK_CUDA(cudaMemset(t->err, 0, sizeof(int)));
@@ -501,62 +638,175 @@ void m2l_tc_prepare(Plan &P) {
     PK_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
 }
 
+namespace {
+
+struct GridPlan {
+    int level, n, bx, by, bz, rb;
+    long long rows;
+    size_t off;  // element offset of the hi grid in TcState::grid
+};
+
+template <typename T>
+void grow(T *&p, size_t &cap, size_t n) {
+    if (n <= cap) return;
+    cudaFree(p);
+    p = nullptr;
+    cap = n + n / 4 + 16;
+    PK_CUDA(cudaMalloc(&p, cap * sizeof(T)));
+}
+
+}  // namespace
+
 bool m2l_tc_run(Plan &P, cudaStream_t s) {
     TcState *t = P.tc;
     if (!t) return false;
     const Task &task = P.t_m2l;
     if (task.nrows == 0) return true;
-    const int KP = t->KP, nr = P.nrhs;
-    // Phi hi/lo with a trailing zero row
+    const int KP = t->KP, nr = P.nrhs, mtiles = KP / TC_M;
+    const std::vector<int> &lb = P.tree.lvl_begin;
+    const int nlev = (int)lb.size() - 1;
     long long rows = (long long)P.tree.nbox * nr;
-    if ((size_t)(rows + 1) > t->phi_rows) {
-        cudaFree(t->phi);
-        t->phi = nullptr;
-        t->phi_rows = (size_t)(rows + 1) + (size_t)(rows + 1) / 4;
-        PK_CUDA(cudaMalloc(&t->phi, 2 * t->phi_rows * KP * sizeof(__half)));
+
+    // levels where every box exists run with TMA-loaded operands (grid mode)
+    std::vector<GridPlan> gp;
+    std::vector<char> is_grid(nlev, 0);
+    int rb = 0;
+    if (nr <= 128 && (nr & (nr - 1)) == 0) rb = nr;
+    size_t grid_elems = 0;
+    if (rb) {
+        int e = 0;
+        while ((1 << e) < 128 / rb) e++;
+        const int ez = e / 3, ey = (e - ez) / 2, ex = e - ey - ez;
+        for (int l = 1; l < nlev; l++) {
+            long long cnt = lb[l + 1] - lb[l];
+            const int n = 1 << l;
+            if (cnt != (1LL << (3 * l)) || (n / 2) < (1 << ex)) continue;
+            GridPlan g{l, n, 1 << ex, 1 << ey, 1 << ez, rb, 0, 0};
+            const long long d = n / 2 + 4;
+            g.rows = 8 * d * d * d * nr;
+            g.off = grid_elems;
+            grid_elems += 2 * (size_t)g.rows * KP;
+            gp.push_back(g);
+            is_grid[l] = 1;
+        }
     }
-    __half *hi = t->phi, *lo = t->phi + t->phi_rows * KP;
-    long long tot = (rows + 1) * KP;
     PK_CUDA(cudaMemsetAsync(t->amax, 0, sizeof(float), s));
     count_launch(), k_amax<<<1024, 256, 0, s>>>(P.up32.p, rows * P.kn, t->amax);
-    count_launch(), k_phi_split<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.up32.p, rows, P.kn, KP, t->amax, hi,
-                                                                               lo);
-    // tiles of 256 (box, rhs) columns within each octant class
-    std::vector<int4> tiles;
-    for (int c = 0, r0 = 0; c < task.nclass; c++) {
-        int rows_c = task.class_count[c] * nr;
-        for (int r = 0; r < rows_c; r += TC_N) tiles.push_back(make_int4(c, r0 + r, std::min(TC_N, rows_c - r), 0));
-        r0 += rows_c;
+
+    // remaining boxes: gather mode, class-major
+    std::vector<int> gbox;
+    std::vector<int4> gtiles;
+    for (int c = 0, b0 = 0; c < task.nclass; c++) {
+        const int start = (int)gbox.size();
+        for (int i = 0; i < task.class_count[c]; i++) {
+            const int b = task.h_boxes[b0 + i];
+            const int l = (int)(std::upper_bound(lb.begin(), lb.end(), b) - lb.begin()) - 1;
+            if (!is_grid[l]) gbox.push_back(b);
+        }
+        b0 += task.class_count[c];
+        const int rows_c = ((int)gbox.size() - start) * nr;
+        for (int r = 0; r < rows_c; r += TC_N)
+            gtiles.push_back(make_int4(c, start * nr + r, std::min(TC_N, rows_c - r), 0));
     }
-    if ((int)tiles.size() > t->tiles_cap) {
-        cudaFree(t->tiles);
-        t->tiles_cap = (int)tiles.size() + 64;
-        PK_CUDA(cudaMalloc(&t->tiles, sizeof(int4) * t->tiles_cap));
+    // grid tiles: (class | rblock << 3, i0, j0, k0) per level
+    std::vector<int> gt_begin;
+    for (auto &g : gp) {
+        gt_begin.push_back((int)gtiles.size());
+        const int h = g.n / 2;
+        for (int c = 0; c < 8; c++)
+            for (int r = 0; r < nr / g.rb; r++)
+                for (int k0 = 0; k0 < h; k0 += g.bz)
+                    for (int j0 = 0; j0 < h; j0 += g.by)
+                        for (int i0 = 0; i0 < h; i0 += g.bx) gtiles.push_back(make_int4(c | r << 3, i0, j0, k0));
     }
-    t->ntiles = (int)tiles.size();
-    PK_CUDA(cudaMemcpyAsync(t->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
+    gt_begin.push_back((int)gtiles.size());
+    grow(t->gtiles, t->gtiles_cap, gtiles.size() + 1);
+    grow(t->gboxes, t->gboxes_cap, gbox.size() + 1);
+    if (!gtiles.empty())
+        PK_CUDA(cudaMemcpyAsync(t->gtiles, gtiles.data(), sizeof(int4) * gtiles.size(), cudaMemcpyHostToDevice, s));
+    if (!gbox.empty())
+        PK_CUDA(cudaMemcpyAsync(t->gboxes, gbox.data(), sizeof(int) * gbox.size(), cudaMemcpyHostToDevice, s));
+
     TcArgs a;
-    a.phi_hi = hi;
-    a.phi_lo = lo;
-    a.tboxes = task.boxes.p;
-    a.tiles = t->tiles;
+    std::memset(&a, 0, sizeof a);
     a.v_slot = P.tree.v_slot.p;
     a.class_ops = P.class_slot_op.p;
+    a.slot_off = t->slot_off;
     a.chk = P.chk32.p;
+    a.amax = t->amax;
     a.kn = P.kn;
     a.KP = KP;
     a.nrhs = nr;
     a.zero_row = (int)rows;
-    a.amax = t->amax;
     a.kexp = t->kexp;
     a.err = t->err;
-    dim3 grid(t->ntiles, KP / TC_M);
+
+    // densities for gather mode
+    const int ngather_tiles = gt_begin.empty() ? (int)gtiles.size() : gt_begin[0];
+    if (ngather_tiles > 0) {
+        if ((size_t)(rows + 1) > t->phi_rows) {
+            cudaFree(t->phi);
+            t->phi = nullptr;
+            t->phi_rows = (size_t)(rows + 1) + (size_t)(rows + 1) / 4;
+            PK_CUDA(cudaMalloc(&t->phi, 2 * t->phi_rows * KP * sizeof(__half)));
+        }
+        long long tot = (rows + 1) * KP;
+        count_launch(), k_phi_split<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+            P.up32.p, rows, P.kn, KP, t->amax, t->phi, t->phi + t->phi_rows * KP);
+    }
+    // parity grids for grid mode
+    if (!gp.empty()) {
+        grow(t->grid, t->grid_cap, grid_elems);
+        for (auto &g : gp) {
+            __half *hi = t->grid + g.off, *lo = hi + (size_t)g.rows * KP;
+            long long tot = g.rows * KP;
+            count_launch(), k_phi_grid<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+                P.up32.p, lb[g.level], g.n, nr, P.kn, KP, P.periodic, t->amax, g.rows, hi, lo);
+        }
+    }
     PK_CUDA(cudaEventRecord(t->ev[0], s));
-    count_launch(), k_m2l_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(t->tmap[0], t->tmap[1], a);
-    PK_CUDA(cudaGetLastError());
+    if (ngather_tiles > 0) {
+        a.phi_hi = t->phi;
+        a.phi_lo = t->phi + t->phi_rows * KP;
+        a.tboxes = t->gboxes;
+        a.tiles = t->gtiles;
+        a.grid = 0;
+        count_launch(), k_m2l_tc<<<ngather_tiles * mtiles, TC_THREADS, TC_SMEM, s>>>(t->tmap[0], t->tmap[1], t->tmap[0],
+                                                                                     t->tmap[1], a);
+        PK_CUDA(cudaGetLastError());
+    }
+    EncodeTiledFn enc = encode_fn();
+    for (size_t gi = 0; gi < gp.size(); gi++) {
+        const GridPlan &g = gp[gi];
+        const cuuint64_t d = (cuuint64_t)(g.n / 2 + 4);
+        CUtensorMap mb[2];
+        for (int h = 0; h < 2; h++) {
+            __half *base = t->grid + g.off + (size_t)h * g.rows * KP;
+            cuuint64_t dims[5] = {(cuuint64_t)KP, (cuuint64_t)nr, d, d, 8 * d};
+            cuuint64_t row = (cuuint64_t)KP * 2;
+            cuuint64_t strides[4] = {row, row * nr, row * nr * d, row * nr * d * d};
+            cuuint32_t box[5] = {TC_K, (cuuint32_t)g.rb, (cuuint32_t)g.bx, (cuuint32_t)g.by, (cuuint32_t)g.bz};
+            cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+            CUresult r = enc(&mb[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) throw Error(PKIFMM_ERR_CUDA, "cuTensorMapEncodeTiled (level grid) failed");
+        }
+        a.grid = 1;
+        a.tiles = t->gtiles + gt_begin[gi];
+        a.lvl_begin = lb[g.level];
+        a.zd = (int)d;
+        a.bx = g.bx;
+        a.by = g.by;
+        a.bz = g.bz;
+        a.rb = g.rb;
+        const int ntl = gt_begin[gi + 1] - gt_begin[gi];
+        count_launch(), k_m2l_tc<<<ntl * mtiles, TC_THREADS, TC_SMEM, s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
+        PK_CUDA(cudaGetLastError());
+    }
     PK_CUDA(cudaEventRecord(t->ev[1], s));
     PK_CUDA(cudaMemcpyAsync(t->err_host, t->err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PK_CUDA(cudaStreamSynchronize(s));  // host tile vector and the error flag
+    PK_CUDA(cudaStreamSynchronize(s));  // host tile vectors and the error flag
     PK_CUDA(cudaEventElapsedTime(&t->last_ms, t->ev[0], t->ev[1]));
     if (*t->err_host) {
         PK_CUDA(cudaMemset(t->err, 0, sizeof(int)));

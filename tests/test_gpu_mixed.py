@@ -67,3 +67,28 @@ def test_mixed_multiple_rhs(cache):
     for r in range(4):
         u1 = run(1, 7, x, f[r], x, p=6, leaf=48, precision=1, cache_dir=cache)
         assert rel_l2(u4[r], u1) < 1e-6
+
+
+@pytest.mark.parametrize("nrhs", [1, 4])
+def test_mixed_full_levels_tma_grid(nrhs, cache):
+    """2^17 uniform points, leaf 64: every level down to 4 is full, so the
+    level-4 M2L loads its source densities from the parity grids by TMA (and
+    levels 1-3 use the gather path).  At p = 8 the mixed path must be as
+    accurate as the FP64 path against the oracle, and every density vector
+    must match its single-vector evaluation."""
+    n = 1 << 17
+    x, f = w.stokes_uniform(n, seed=25, nrhs=nrhs)
+    um = run(1, 7, x, f if nrhs > 1 else f[0], x, p=8, leaf=64, precision=1, cache_dir=cache)
+    idx = _sample(n, 300)
+    if nrhs == 1:
+        ud = run(1, 7, x, f[0], x, p=8, leaf=64, precision=0, cache_dir=cache)
+        ref = oracle.stokes_tp(x, f[0], x[idx])
+        em, ed = rel_l2(um[idx], ref), rel_l2(ud[idx], ref)
+        print(f"grid-mode p=8: mixed {em:.3e} fp64 {ed:.3e} mixed-vs-fp64 {rel_l2(um, ud):.3e}")
+        assert em < 1.5 * ed + 5e-6
+    else:
+        for r in (0, nrhs - 1):
+            u1 = run(1, 7, x, f[r], x, p=8, leaf=64, precision=1, cache_dir=cache)
+            d = rel_l2(um[r], u1)
+            print(f"grid-mode nrhs={nrhs} column {r} vs single: {d:.3e}")
+            assert d < 1e-6
