@@ -18,6 +18,7 @@
 // every operator load.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 #include "kernels.cuh"
@@ -133,92 +134,152 @@ void upload_operators(Plan &P) {
 
 // ---------------- slot GEMM ----------------
 
-constexpr int GB_M = 64, GB_N = 64, GB_K = 16, G_TM = 4, G_TN = 4;  // 256 threads
+// Tiles: FP64 64 x 64 (4 x 4 per thread), FP32 128 x 128 (8 x 8 per thread);
+// 256 threads.  Rows of a tile belong to one class, so every row of the tile
+// uses the same operator for a given slot.
+// Tile configurations of the slot GEMM.  Every configuration accumulates
+// each output element in the same order (slot by slot, inputs in order), so
+// they give bitwise identical results; the small one only raises parallelism
+// for tasks with few rows (the top octree levels).
+template <typename T, int BM_, int BN_, int BK_, int TM_, int TN_> struct GemmTile {
+    using type = T;
+    static constexpr int BM = BM_, BN = BN_, BK = BK_, TM = TM_, TN = TN_;
+};
+template <typename T> struct GemmCfg;
+template <> struct GemmCfg<double> : GemmTile<double, 64, 64, 16, 4, 4> {};
+template <> struct GemmCfg<float> : GemmTile<float, 128, 128, 16, 8, 8> {};
+template <typename T> using GemmSmall = GemmTile<T, 32, 32, 16, 2, 2>;
+constexpr int GB_M = 64;  // tile rows of FP64 tasks
 
-template <typename T>
+// dst[box][rhs][:] (+)= sum_slots Op[class_ops[cls][s]] src[slot box][rhs][:]
+// for one tile of task rows (blockIdx.x) split into sub-tiles of C::BM rows
+// (blockIdx.z) and C::BN output components (blockIdx.y).  Global loads of the
+// next K step are issued before the current one is multiplied.
+template <typename C>
 __global__ void __launch_bounds__(256) k_slot_gemm(const int *__restrict__ tboxes, const int4 *__restrict__ tiles,
                                                    const int *__restrict__ slot_table, int slot_stride, int nslots,
-                                                   const int *__restrict__ class_ops, const T *__restrict__ ops,
-                                                   long long op_stride, const T *__restrict__ src,
-                                                   T *__restrict__ dst, int kn, int nrhs, int beta) {
-    __shared__ T As[GB_K][GB_M + 1];
-    __shared__ T Bs[GB_K][GB_N + 1];
-    __shared__ long long srow[GB_M], drow[GB_M];
-    __shared__ int sbox[GB_M];
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+                                                   const int *__restrict__ class_ops,
+                                                   const typename C::type *__restrict__ ops, long long op_stride,
+                                                   const typename C::type *__restrict__ src,
+                                                   typename C::type *__restrict__ dst, int kn, int nrhs, int beta) {
+    using T = typename C::type;
+    constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
+    static_assert(BM == BN && (BM / TM) * (BN / TN) == 256, "256 threads cover the tile");
+    constexpr int TX = BN / TN;           // threads along N
+    constexpr int LPT = BM * BK / 256;    // A (and B) elements each thread loads per K step
+    constexpr int RPT = BK / LPT;         // threads per row for loads
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    __shared__ long long srow[BM], drow[BM];
+    __shared__ int sbox[BM];
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int4 tile = tiles[blockIdx.x];
-    const int cls = tile.x, row0 = tile.y, nr = tile.z, n0 = blockIdx.y * GB_N;
-    if (tid < GB_M) {
-        if (tid < nr) {
-            int row = row0 + tid, tb = row / nrhs, rhs = row % nrhs, box = tboxes[tb];
-            drow[tid] = (long long)box * nrhs + rhs;
-            sbox[tid] = box;
+    const int cls = tile.x, row0 = tile.y + blockIdx.z * BM, nr = tile.z - blockIdx.z * BM, n0 = blockIdx.y * BN;
+    if (nr <= 0) return;
+    for (int i = tid; i < BM; i += 256) {
+        if (i < nr) {
+            int row = row0 + i, tb = row / nrhs, rhs = row % nrhs, box = tboxes[tb];
+            drow[i] = (long long)box * nrhs + rhs;
+            sbox[i] = box;
         } else {
-            drow[tid] = -1;
-            sbox[tid] = -1;
+            drow[i] = -1;
+            sbox[i] = -1;
         }
     }
     __syncthreads();
-    T acc[G_TM][G_TN];
+    T acc[TM][TN];
 #pragma unroll
-    for (int i = 0; i < G_TM; i++)
+    for (int i = 0; i < TM; i++)
 #pragma unroll
-        for (int j = 0; j < G_TN; j++) acc[i][j] = (T)0;
-    const int lm = tid / 4, lk = (tid % 4) * 4;
+        for (int j = 0; j < TN; j++) acc[i][j] = (T)0;
+    const int lm = tid / RPT, lk = (tid % RPT) * LPT;
+    const int nn = n0 + lm;
     for (int s = 0; s < nslots; s++) {
         int op = class_ops[cls * nslots + s];
         if (op < 0) continue;
         __syncthreads();
         int any = 0;
-        if (tid < GB_M) {
+        for (int i = tid; i < BM; i += 256) {
             long long sr = -1;
-            if (drow[tid] >= 0) {
-                int b = sbox[tid];
+            if (drow[i] >= 0) {
+                int b = sbox[i];
                 int sb = slot_table ? slot_table[(long long)b * slot_stride + s] : b;
-                if (sb >= 0) sr = (long long)sb * nrhs + (drow[tid] - (long long)b * nrhs);
+                if (sb >= 0) sr = (long long)sb * nrhs + (drow[i] - (long long)b * nrhs);
             }
-            srow[tid] = sr;
-            any = sr >= 0;
+            srow[i] = sr;
+            any |= sr >= 0;
         }
         if (!__syncthreads_or(any)) continue;
         const T *Op = ops + (long long)op * op_stride;
         const long long sr = srow[lm];
-        for (int k0 = 0; k0 < kn; k0 += GB_K) {
+        const T *arow = sr >= 0 ? src + sr * kn : nullptr;
+        const T *brow = nn < kn ? Op + (long long)nn * kn : nullptr;
+        T ra[LPT], rb[LPT];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                int kk = k0 + lk + q;
-                As[lk + q][lm] = (sr >= 0 && kk < kn) ? src[sr * kn + kk] : (T)0;
-                int nn = n0 + lm;
-                Bs[lk + q][lm] = (nn < kn && kk < kn) ? Op[(long long)nn * kn + kk] : (T)0;
+        for (int q = 0; q < LPT; q++) {
+            int kk = lk + q;
+            ra[q] = (arow && kk < kn) ? arow[kk] : (T)0;
+            rb[q] = (brow && kk < kn) ? brow[kk] : (T)0;
+        }
+        for (int k0 = 0; k0 < kn; k0 += BK) {
+#pragma unroll
+            for (int q = 0; q < LPT; q++) {
+                As[lk + q][lm] = ra[q];
+                Bs[lk + q][lm] = rb[q];
             }
             __syncthreads();
+            if (k0 + BK < kn) {
 #pragma unroll
-            for (int kk = 0; kk < GB_K; kk++) {
-                T a[G_TM], b[G_TN];
+                for (int q = 0; q < LPT; q++) {
+                    int kk = k0 + BK + lk + q;
+                    ra[q] = (arow && kk < kn) ? arow[kk] : (T)0;
+                    rb[q] = (brow && kk < kn) ? brow[kk] : (T)0;
+                }
+            }
 #pragma unroll
-                for (int i = 0; i < G_TM; i++) a[i] = As[kk][ty * G_TM + i];
+            for (int kk = 0; kk < BK; kk++) {
+                T a[TM], b[TN];
 #pragma unroll
-                for (int j = 0; j < G_TN; j++) b[j] = Bs[kk][tx * G_TN + j];
+                for (int i = 0; i < TM; i++) a[i] = As[kk][ty * TM + i];
 #pragma unroll
-                for (int i = 0; i < G_TM; i++)
+                for (int j = 0; j < TN; j++) b[j] = Bs[kk][tx * TN + j];
 #pragma unroll
-                    for (int j = 0; j < G_TN; j++) acc[i][j] += a[i] * b[j];
+                for (int i = 0; i < TM; i++)
+#pragma unroll
+                    for (int j = 0; j < TN; j++) acc[i][j] += a[i] * b[j];
             }
             __syncthreads();
         }
     }
 #pragma unroll
-    for (int i = 0; i < G_TM; i++) {
-        long long dr = drow[ty * G_TM + i];
+    for (int i = 0; i < TM; i++) {
+        long long dr = drow[ty * TM + i];
         if (dr < 0) continue;
 #pragma unroll
-        for (int j = 0; j < G_TN; j++) {
-            int nn = n0 + tx * G_TN + j;
-            if (nn >= kn) continue;
-            T *d = dst + dr * kn + nn;
+        for (int j = 0; j < TN; j++) {
+            int nn2 = n0 + tx * TN + j;
+            if (nn2 >= kn) continue;
+            T *d = dst + dr * kn + nn2;
             *d = beta ? *d + acc[i][j] : acc[i][j];
         }
     }
+}
+
+// y[r][i] = sum_j M[i][j] x[r][j] for nrhs vectors (binary64), one warp per row
+__global__ void k_matvec64(const double *__restrict__ M, const double *__restrict__ x, double *__restrict__ y,
+                           int n, int nrhs) {
+    int row = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (row >= n) return;
+    for (int r = 0; r < nrhs; r++) {
+        double acc = 0;
+        for (int j = lane; j < n; j += 32) acc += M[(long long)row * n + j] * x[(long long)r * n + j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[(long long)r * n + row] = acc;
+    }
+}
+
+static void matvec64(const double *M, const double *x, double *y, int n, int nrhs, cudaStream_t s) {
+    count_launch(), k_matvec64<<<(n + 7) / 8, 256, 0, s>>>(M, x, y, n, nrhs);
 }
 
 // ---------------- tasks ----------------
@@ -239,7 +300,7 @@ struct HostTree {
 
 // boxes: per class list of dst boxes
 static void make_task(Task &t, const std::vector<std::vector<int>> &by_class, int nslots,
-                      const std::vector<int> &class_ops, int nrhs, cudaStream_t s) {
+                      const std::vector<int> &class_ops, int nrhs, cudaStream_t s, int bm = GB_M) {
     t.nclass = (int)by_class.size();
     t.nslots = nslots;
     t.h_boxes.clear();
@@ -249,7 +310,7 @@ static void make_task(Task &t, const std::vector<std::vector<int>> &by_class, in
     for (int c = 0; c < t.nclass; c++) {
         int row0 = (int)t.h_boxes.size() * nrhs;
         int nrows = (int)by_class[c].size() * nrhs;
-        for (int r = 0; r < nrows; r += GB_M) tiles.push_back(make_int4(c, row0 + r, std::min(GB_M, nrows - r), 0));
+        for (int r = 0; r < nrows; r += bm) tiles.push_back(make_int4(c, row0 + r, std::min(bm, nrows - r), 0));
         t.h_boxes.insert(t.h_boxes.end(), by_class[c].begin(), by_class[c].end());
     }
     t.nrows = (int)t.h_boxes.size() * nrhs;
@@ -309,8 +370,9 @@ void build_tasks(Plan &P, cudaStream_t s) {
     upload_list(P.xboxes, xb, s);
 
     bool mixed = P.precision == PKIFMM_MIXED;
+    const int bm = mixed ? GemmCfg<float>::BM : GemmCfg<double>::BM;
     // UC2E over leaves with sources
-    make_task(P.t_uc2e, {leaves_src}, 1, {0}, nr, s);
+    make_task(P.t_uc2e, {leaves_src}, 1, {0}, nr, s, bm);
     // M2M per level: non-leaf boxes with sources
     int depth = (int)t.lvl_begin.size() - 1;
     P.t_m2m.resize(depth);
@@ -320,7 +382,7 @@ void build_tasks(Plan &P, cudaStream_t s) {
         std::vector<int> v;
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
             if (!H.leaf(b) && H.has_src(b)) v.push_back(b);
-        make_task(P.t_m2m[l], {v}, 8, ops8, nr, s);
+        make_task(P.t_m2m[l], {v}, 8, ops8, nr, s, bm);
     }
     // root
     make_task(P.t_root, {{0}}, 1, {0}, nr, s);
@@ -330,19 +392,19 @@ void build_tasks(Plan &P, cudaStream_t s) {
         if (H.has_trg(b)) byc[H.octant(b)].push_back(b);
     std::vector<int> cls_op(8 * kVSlots);
     PK_CUDA(cudaMemcpy(cls_op.data(), P.class_slot_op.p, sizeof(int) * cls_op.size(), cudaMemcpyDeviceToHost));
-    make_task(P.t_m2l, byc, kVSlots, cls_op, nr, s);
+    make_task(P.t_m2l, byc, kVSlots, cls_op, nr, s, bm);
     // DC2E over boxes with targets (root separately in binary64 for MIXED)
     std::vector<int> dc;
     for (int b = (mixed ? 1 : 0); b < nb; b++)
         if (H.has_trg(b)) dc.push_back(b);
-    make_task(P.t_dc2e, {dc}, 1, {0}, nr, s);
+    make_task(P.t_dc2e, {dc}, 1, {0}, nr, s, bm);
     // L2L per level >= 1, by octant class
     P.t_l2l.resize(depth);
     for (int l = 1; l < depth; l++) {
         std::vector<std::vector<int>> bc(8);
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
             if (H.has_trg(b)) bc[H.octant(b)].push_back(b);
-        make_task(P.t_l2l[l], bc, 1, ops8, nr, s);
+        make_task(P.t_l2l[l], bc, 1, ops8, nr, s, bm);
     }
 }
 
@@ -350,9 +412,19 @@ template <typename T>
 static void gemm(const Task &t, const int *slot_table, int slot_stride, const T *ops, long long op_stride,
                  const T *src, T *dst, int kn, int nrhs, int beta, cudaStream_t s) {
     if (t.ntiles == 0) return;
-    dim3 grid(t.ntiles, (kn + GB_N - 1) / GB_N);
-    count_launch(), k_slot_gemm<T><<<grid, 256, 0, s>>>(t.boxes.p, t.tiles.p, slot_table, slot_stride, t.nslots, t.class_ops.p,
-                                        ops, op_stride, src, dst, kn, nrhs, beta);
+    using Big = GemmCfg<T>;
+    using Small = GemmSmall<T>;
+    const int bm = std::is_same<T, float>::value ? Big::BM : GB_M;  // rows per task tile (make_task)
+    const long long big_blocks = (long long)t.ntiles * ((kn + Big::BN - 1) / Big::BN) * ((bm + Big::BM - 1) / Big::BM);
+    if (big_blocks < 2 * 152) {
+        dim3 g(t.ntiles, (kn + Small::BN - 1) / Small::BN, (bm + Small::BM - 1) / Small::BM);
+        count_launch(), k_slot_gemm<Small><<<g, 256, 0, s>>>(t.boxes.p, t.tiles.p, slot_table, slot_stride, t.nslots,
+                                                              t.class_ops.p, ops, op_stride, src, dst, kn, nrhs, beta);
+        return;
+    }
+    dim3 grid(t.ntiles, (kn + Big::BN - 1) / Big::BN, (bm + Big::BM - 1) / Big::BM);
+    count_launch(), k_slot_gemm<Big><<<grid, 256, 0, s>>>(t.boxes.p, t.tiles.p, slot_table, slot_stride, t.nslots,
+                                                          t.class_ops.p, ops, op_stride, src, dst, kn, nrhs, beta);
 }
 
 // ---------------- kernel sums ----------------
@@ -504,21 +576,21 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
 // Leaf: L2T + W-list M2T + U-list P2P for the targets of one leaf.
 // Each source tile's partial sum is added to the running total with
 // Kahan compensation.
-template <typename T, int K>
-__global__ void __launch_bounds__(KS_T) k_leaf(
+template <typename T, int K, int NT>
+__global__ void __launch_bounds__(NT) k_leaf(
     const int *__restrict__ leaves, const int4 *__restrict__ bpos, const int2 *__restrict__ srange,
     const int2 *__restrict__ trange, const int *__restrict__ uptr, const int *__restrict__ ubox,
     const unsigned char *__restrict__ ush, const int *__restrict__ wptr, const int *__restrict__ wbox,
     const unsigned char *__restrict__ wsh, const V4<T> *__restrict__ yrel, const V4<T> *__restrict__ xrel,
     const T *__restrict__ dens, const T *__restrict__ up, const T *__restrict__ dn, int nrhs, int rhs,
     const T *__restrict__ g, int n, double *__restrict__ pot) {
-    __shared__ T sy[KS_T][3], sphi[KS_T][K];
+    __shared__ T sy[NT][3], sphi[NT][K];
     const int b = leaves[blockIdx.x];
     const int4 B = bpos[b];
     const T h = (T)exp2i(B.w);
     const int2 tr = trange[b];
     const int kn = n * K;
-    for (int t0 = tr.x; t0 < tr.y; t0 += KS_T) {
+    for (int t0 = tr.x; t0 < tr.y; t0 += NT) {
         int t = t0 + threadIdx.x;
         T x[3] = {0, 0, 0};
         if (t < tr.y) {
@@ -545,7 +617,7 @@ __global__ void __launch_bounds__(KS_T) k_leaf(
         {
             const T sc = (T)1.475 * h;
             const T *phi = dn + ((long long)b * nrhs + rhs) * kn;
-            for (int j0 = 0; j0 < n; j0 += KS_T) {
+            for (int j0 = 0; j0 < n; j0 += NT) {
                 __syncthreads();
                 int j = j0 + threadIdx.x;
                 if (j < n) {
@@ -556,7 +628,7 @@ __global__ void __launch_bounds__(KS_T) k_leaf(
                     for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = phi[j * K + a];
                 }
                 __syncthreads();
-                int m = min(KS_T, n - j0);
+                int m = min(NT, n - j0);
                 for (int jj = 0; jj < m; jj++)
                     Kern<T, K>::add(acc, x[0] - sy[jj][0], x[1] - sy[jj][1], x[2] - sy[jj][2], sphi[jj]);
                 flush();
@@ -572,7 +644,7 @@ __global__ void __launch_bounds__(KS_T) k_leaf(
             const T o0 = (T)off[0], o1 = (T)off[1], o2 = (T)off[2];
             const T sc = (T)(0.525 * exp2i(Ap.w));
             const T *phi = up + ((long long)A * nrhs + rhs) * kn;
-            for (int j0 = 0; j0 < n; j0 += KS_T) {
+            for (int j0 = 0; j0 < n; j0 += NT) {
                 __syncthreads();
                 int j = j0 + threadIdx.x;
                 if (j < n) {
@@ -583,7 +655,7 @@ __global__ void __launch_bounds__(KS_T) k_leaf(
                     for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = phi[j * K + a];
                 }
                 __syncthreads();
-                int m = min(KS_T, n - j0);
+                int m = min(NT, n - j0);
                 for (int jj = 0; jj < m; jj++)
                     Kern<T, K>::add(acc, x[0] - sy[jj][0] + o0, x[1] - sy[jj][1] + o1, x[2] - sy[jj][2] + o2,
                                     sphi[jj]);
@@ -598,7 +670,7 @@ __global__ void __launch_bounds__(KS_T) k_leaf(
             centre_offset(B, bpos[A], sh, off);
             const T o0 = (T)off[0], o1 = (T)off[1], o2 = (T)off[2];
             int2 r = srange[A];
-            for (int s0 = r.x; s0 < r.y; s0 += KS_T) {
+            for (int s0 = r.x; s0 < r.y; s0 += NT) {
                 __syncthreads();
                 int s = s0 + threadIdx.x;
                 if (s < r.y) {
@@ -610,7 +682,7 @@ __global__ void __launch_bounds__(KS_T) k_leaf(
                     for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = dens[(long long)s * nrhs * K + rhs * K + a];
                 }
                 __syncthreads();
-                int m = min(KS_T, r.y - s0);
+                int m = min(NT, r.y - s0);
                 for (int j = 0; j < m; j++)
                     Kern<T, K>::add(acc, x[0] - sy[j][0] + o0, x[1] - sy[j][1] + o1, x[2] - sy[j][2] + o2, sphi[j]);
                 flush();
@@ -736,16 +808,15 @@ void root_mixed(Plan &P, cudaStream_t s) {
         return;
     }
     count_launch(), k_f2d<float><<<nblk(rows, 256), 256, 0, s>>>(P.up32.p, P.up64.p, rows);
-    gemm<double>(P.t_root, nullptr, 1, P.root.p, 0, P.up64.p, P.chk64.p, kn, nr, 0, s);
-    gemm<double>(P.t_root, nullptr, 1, P.dc2e_b.p, 0, P.chk64.p, P.tmp64.p, kn, nr, 0, s);
-    gemm<double>(P.t_root, nullptr, 1, P.dc2e_a.p, 0, P.tmp64.p, P.dn64.p, kn, nr, 0, s);
+    matvec64(P.root.p, P.up64.p, P.chk64.p, kn, nr, s);
+    matvec64(P.dc2e_b.p, P.chk64.p, P.tmp64.p, kn, nr, s);
+    matvec64(P.dc2e_a.p, P.tmp64.p, P.dn64.p, kn, nr, s);
     count_launch(), k_cast<float><<<nblk(rows, 256), 256, 0, s>>>(P.dn64.p, P.dn32.p, rows);
 }
 
 void run_root(Plan &P, cudaStream_t s) {
     if (P.precision == PKIFMM_FP64) {
-        if (P.periodic)
-            gemm<double>(P.t_root, nullptr, 1, P.root.p, 0, P.up64.p, P.chk64.p, P.kn, P.nrhs, 0, s);
+        if (P.periodic) matvec64(P.root.p, P.up64.p, P.chk64.p, P.kn, P.nrhs, s);
         else  // no far field; the row may hold the root leaf's upward check values
             PK_CUDA(cudaMemsetAsync(P.chk64.p, 0, sizeof(double) * P.nrhs * P.kn, s));
         return;
@@ -797,12 +868,21 @@ static void leaves_t(Plan &P, cudaStream_t s) {
     P.pot_s.reserve((size_t)P.T * nr * K + 1);
     auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
     auto *xr = reinterpret_cast<const V4<T> *>(B::xrel(P).p);
-    if (P.n_leaves_trg)
-        for (int r = 0; r < nr; r++)
-            count_launch(), k_leaf<T, K><<<P.n_leaves_trg, KS_T, 0, s>>>(
+    // one block per target leaf; block size near the leaf size (most leaves
+    // hold about s/2 targets)
+    auto launch = [&](auto nt_tag, int r) {
+        constexpr int NT = decltype(nt_tag)::value;
+        count_launch(), k_leaf<T, K, NT><<<P.n_leaves_trg, NT, 0, s>>>(
                 P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
                 P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
                 B::dn(P).p, nr, r, B::g(P).p, P.n, P.pot_s.p);
+    };
+    if (P.n_leaves_trg)
+        for (int r = 0; r < nr; r++) {
+            if (P.leaf_max <= 64) launch(std::integral_constant<int, 32>{}, r);
+            else if (P.leaf_max <= 128) launch(std::integral_constant<int, 64>{}, r);
+            else launch(std::integral_constant<int, 128>{}, r);
+        }
 }
 
 void run_leaves(Plan &P, cudaStream_t s) {
