@@ -20,7 +20,10 @@ are made absolutely convergent with the conventions that fix the result
 * Stokes TP: Hasimoto split, k = 0 removed (zero mean flow; a net force is
   allowed);
 * Laplace SP: direct symmetric image sum with an Euler-Maclaurin tail
-  (requires neutral charges).
+  (requires neutral charges);
+* Laplace / Stokes DP (x, y periodic, z free): 2D Ewald split, in-plane
+  modes by the trapezoid rule in k_z, the k_par = 0 term in closed form
+  (requires neutral charges / zero net in-plane force).
 
 Functions with no closed-form or brute-force pin say so in their docstring
 ("parity unpinned").
@@ -68,6 +71,7 @@ def _load():
             lib.orc_laplace_tp.argtypes = [l, P, P, l, P, d, d, d, i, d, P]
             lib.orc_stokes_tp.argtypes = [l, P, P, l, P, d, d, d, i, d, P]
             lib.orc_laplace_sp.argtypes = [l, P, P, l, P, i, d, l, P]
+            lib.orc_dp.argtypes = [i, l, P, P, l, P, d, d, d, d, d, P]
             _lib = lib
     return _lib
 
@@ -135,6 +139,31 @@ def laplace_sp(src, q, trg, axis: int = 0, L: float = 1.0, M: int = 200) -> np.n
     return out
 
 
+def doubly_periodic(kernel: int, src, dens, trg, L: float = 1.0, xi=None, rc=None) -> np.ndarray:
+    """Periodic in x and y (period L), free in z: 2D Ewald sum.
+
+    The k_z integral of every in-plane Fourier mode is taken by the trapezoid
+    rule with z period H = (z extent of all points)/L + 8, so the aliased
+    images sit at least 8 periods away (weight < exp(-2 pi 8)).
+    """
+    xi, rc, _, kc = ewald_params(xi, rc)
+    y, x = _c(src), _c(trg)
+    phi = _c(dens).reshape(len(y), kdim(kernel))
+    zs = np.concatenate([y[:, 2], x[:, 2]]) if len(y) + len(x) else np.zeros(1)
+    H = (zs.max() - zs.min()) / L + 8.0
+    out = np.zeros((len(x), kdim(kernel)))
+    _load().orc_dp(kernel, len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), L, xi, rc, kc, H, _ptr(out))
+    return out[:, 0] if kernel == LAPLACE else out
+
+
+def laplace_dp(src, q, trg, L: float = 1.0, xi=None, rc=None) -> np.ndarray:
+    return doubly_periodic(LAPLACE, src, q, trg, L, xi, rc)
+
+
+def stokes_dp(src, f, trg, L: float = 1.0, xi=None, rc=None) -> np.ndarray:
+    return doubly_periodic(STOKES, src, f, trg, L, xi, rc)
+
+
 def periodic_sum(kernel: int, periodic_axes: int, src, dens, trg, L: float = 1.0) -> np.ndarray:
     """Dispatch on (kernel, periodicity bitmask: bit0=x, bit1=y, bit2=z).
 
@@ -145,6 +174,8 @@ def periodic_sum(kernel: int, periodic_axes: int, src, dens, trg, L: float = 1.0
         return free_space(kernel, src, dens, trg)
     if periodic_axes == 7:
         return laplace_tp(src, dens, trg, L) if kernel == LAPLACE else stokes_tp(src, dens, trg, L)
+    if periodic_axes == 3:
+        return doubly_periodic(kernel, src, dens, trg, L)
     if kernel == LAPLACE and periodic_axes in (1, 2, 4):
         return laplace_sp(src, dens, trg, axis={1: 0, 2: 1, 4: 2}[periodic_axes], L=L)
     raise NotImplementedError(f"oracle: kernel {kernel} periodicity {periodic_axes}")

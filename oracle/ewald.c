@@ -28,6 +28,14 @@
  *     regularisation -2 H_M and an Euler-Maclaurin tail (Sec. 3.2 notes the
  *     neutral direct sum converges like 1/n^2); the pair-independent constant
  *     cancels by neutrality.
+ *   - Laplace / Stokes DP (periodic in x and y, z free; Sec. 3.3 leaves the
+ *     doubly periodic Ewald sum to the literature): the same real-space
+ *     kernels summed over in-plane images only; the smooth part as the 2D
+ *     lattice sum of its 3D Fourier transform, whose k_z integral is taken by
+ *     the trapezoid rule for every in-plane mode k_par != 0 and in closed
+ *     form for k_par = 0 (a function of z_t - z_s alone); constants dropped
+ *     from the k_par = 0 term cancel for neutral charges / zero net
+ *     in-plane force.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -279,4 +287,140 @@ void orc_laplace_sp(long S, const double *y, const double *phi, long T, const do
         }
         q[t] = acc_get(&a) / L;
     }
+}
+
+/* ---------- doubly periodic (x, y periodic, z free) ---------- */
+
+/* Structure factors F_c(m) = sum_s phi_s,c exp(-i 2 pi sum_a m_a y_s,a / P_a)
+ * for per-axis periods P (unit cell: 1, 1, H) and per-axis |m_a| <= mm[a]. */
+static void structure_factors_box(long S, const double *y, const double *phi, int nc, double L,
+                                  const int mm[3], const double P[3], long nm, const int *m,
+                                  double *re, double *im) {
+    int w[3] = {2 * mm[0] + 1, 2 * mm[1] + 1, 2 * mm[2] + 1}, off[3] = {0, w[0], w[0] + w[1]};
+    int wt = w[0] + w[1] + w[2];
+    memset(re, 0, sizeof(double) * nm * nc);
+    memset(im, 0, sizeof(double) * nm * nc);
+#pragma omp parallel
+    {
+        double *lre = (double *)calloc(nm * nc, sizeof(double));
+        double *lim = (double *)calloc(nm * nc, sizeof(double));
+        double *ec = (double *)malloc(sizeof(double) * wt), *es = (double *)malloc(sizeof(double) * wt);
+#pragma omp for schedule(static)
+        for (long s = 0; s < S; s++) {
+            for (int a = 0; a < 3; a++)
+                for (int j = -mm[a]; j <= mm[a]; j++) {
+                    double th = -2.0 * M_PI * j * (y[3 * s + a] / L) / P[a];
+                    ec[off[a] + j + mm[a]] = cos(th);
+                    es[off[a] + j + mm[a]] = sin(th);
+                }
+            for (long i = 0; i < nm; i++) {
+                int ix = off[0] + m[3 * i] + mm[0], iy = off[1] + m[3 * i + 1] + mm[1], iz = off[2] + m[3 * i + 2] + mm[2];
+                double xr = ec[ix], xi_ = es[ix], yr = ec[iy], yi = es[iy], zr = ec[iz], zi = es[iz];
+                double pr = xr * yr - xi_ * yi, pi_ = xr * yi + xi_ * yr;
+                double er = pr * zr - pi_ * zi, ei = pr * zi + pi_ * zr;
+                for (int c = 0; c < nc; c++) {
+                    double v = phi[(long)nc * s + c];
+                    lre[i * nc + c] += v * er;
+                    lim[i * nc + c] += v * ei;
+                }
+            }
+        }
+#pragma omp critical
+        for (long i = 0; i < nm * nc; i++) { re[i] += lre[i]; im[i] += lim[i]; }
+        free(lre); free(lim); free(ec); free(es);
+    }
+}
+
+/* Doubly periodic Ewald sum, periods L along x and y, z free.
+ * kernel 0: Laplace (phi[S], q[T]);  kernel 1: Stokes (phi[S][3], q[T][3]).
+ * xi, rc: splitting parameter and real-space cutoff (unit cell);
+ * kc: Fourier cutoff; H: z period (unit cells) of the trapezoid rule in k_z,
+ * which must exceed the z extent of sources and targets by enough that
+ * exp(-2 pi (H - extent)) is negligible.
+ * Unit-cell area A = 1.  Per pair (r = x_t - y_s, unit cell):
+ *   real space  sum_{n in Z^2} K_R(r + n), the same kernels as in TP;
+ *   k_par != 0  (1/H) sum_{k = (2pi mx, 2pi my, 2pi mz/H)} K_F^(k) e^{i k.r};
+ *   k_par = 0   Laplace 4 pi [-(z/2) erf(xi z) - e^{-xi^2 z^2}/(2 xi sqrt(pi))],
+ *               Stokes (I - e_z e_z) [-(z/2) erf(xi z) - e^{-xi^2 z^2}/(4 xi sqrt(pi))],
+ *               z = z_t - z_s: the k_z integral of K_F^(0, 0, k_z) (e^{i k_z z} - 1)
+ *               with z-independent constants dropped;
+ *   self        as in TP. */
+void orc_dp(int kernel, long S, const double *y, const double *phi, long T, const double *x,
+            double L, double xi, double rc, double kc, double H, double *q) {
+    const int nc = kernel == 0 ? 1 : 3;
+    int mm[3] = {(int)ceil(kc / (2.0 * M_PI)), (int)ceil(kc / (2.0 * M_PI)), (int)ceil(kc * H / (2.0 * M_PI))};
+    double P[3] = {1.0, 1.0, H};
+    long cap = (long)(2 * mm[0] + 1) * (2 * mm[1] + 1) * (mm[2] + 1), nm = 0;
+    int *m = (int *)malloc(sizeof(int) * 3 * cap);
+    for (int mz = 0; mz <= mm[2]; mz++)
+        for (int my = -mm[1]; my <= mm[1]; my++)
+            for (int mx = -mm[0]; mx <= mm[0]; mx++) {
+                if (mx == 0 && my == 0) continue; /* k_par = 0 handled in closed form */
+                if (mz == 0 && (my < 0 || (my == 0 && mx <= 0))) continue;
+                double kx = 2.0 * M_PI * mx, ky = 2.0 * M_PI * my, kz = 2.0 * M_PI * mz / H;
+                if (kx * kx + ky * ky + kz * kz >= kc * kc) continue;
+                m[3 * nm] = mx; m[3 * nm + 1] = my; m[3 * nm + 2] = mz; nm++;
+            }
+    double *re = (double *)malloc(sizeof(double) * (nm ? nm : 1) * nc);
+    double *im = (double *)malloc(sizeof(double) * (nm ? nm : 1) * nc);
+    structure_factors_box(S, y, phi, nc, L, mm, P, nm, m, re, im);
+    int nr = rc > 0.5 ? (int)ceil(rc - 0.5) : 0;
+    double rc2 = rc * rc, g0 = 2.0 * xi / sqrt(M_PI), c8 = 1.0 / (8.0 * M_PI), sqpi = sqrt(M_PI);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long t = 0; t < T; t++) {
+        acc_t a[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (long s = 0; s < S; s++) {
+            const double *fs = phi + (long)nc * s;
+            double r[3];
+            for (int c = 0; c < 3; c++) r[c] = (x[3 * t + c] - y[3 * s + c]) / L;
+            for (int c = 0; c < 2; c++) r[c] -= floor(r[c] + 0.5);
+            for (int n0 = -nr; n0 <= nr; n0++)
+                for (int n1 = -nr; n1 <= nr; n1++) {
+                    double d[3] = {r[0] + n0, r[1] + n1, r[2]};
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 == 0.0) {
+                        if (kernel == 0) acc_add(&a[0], -g0 * fs[0]);
+                        else
+                            for (int i = 0; i < 3; i++) acc_add(&a[i], -c8 * 2.0 * g0 * fs[i]);
+                        continue;
+                    }
+                    if (r2 >= rc2) continue;
+                    double rr = sqrt(r2);
+                    if (kernel == 0) {
+                        acc_add(&a[0], erfc(xi * rr) / rr * fs[0]);
+                    } else {
+                        double ec = erfc(xi * rr) / rr, ga = g0 * exp(-xi * xi * r2);
+                        double cI = ec - ga, cR = (ec + ga) / r2;
+                        double df = d[0] * fs[0] + d[1] * fs[1] + d[2] * fs[2];
+                        for (int i = 0; i < 3; i++) acc_add(&a[i], c8 * (cI * fs[i] + cR * d[i] * df));
+                    }
+                }
+            /* k_par = 0 term */
+            double z = r[2], ez = exp(-xi * xi * z * z), lin = -0.5 * z * erf(xi * z);
+            if (kernel == 0) {
+                acc_add(&a[0], 4.0 * M_PI * (lin - ez / (2.0 * xi * sqpi)) * fs[0]);
+            } else {
+                double g = lin - ez / (4.0 * xi * sqpi);
+                acc_add(&a[0], g * fs[0]);
+                acc_add(&a[1], g * fs[1]);
+            }
+        }
+        for (long i = 0; i < nm; i++) {
+            double k[3] = {2.0 * M_PI * m[3 * i], 2.0 * M_PI * m[3 * i + 1], 2.0 * M_PI * m[3 * i + 2] / H};
+            double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2], e = k2 / (4.0 * xi * xi);
+            double th = (k[0] * x[3 * t] + k[1] * x[3 * t + 1] + k[2] * x[3 * t + 2]) / L;
+            double ct = cos(th), st = sin(th);
+            if (kernel == 0) {
+                double wk = 2.0 * 4.0 * M_PI / H * exp(-e) / k2;
+                acc_add(&a[0], wk * (re[i] * ct - im[i] * st));
+            } else {
+                double wk = 2.0 / H * (1.0 + e) * exp(-e) / k2, v[3];
+                for (int c = 0; c < 3; c++) v[c] = re[i * 3 + c] * ct - im[i * 3 + c] * st;
+                double kv = (k[0] * v[0] + k[1] * v[1] + k[2] * v[2]) / k2;
+                for (int c = 0; c < 3; c++) acc_add(&a[c], wk * (v[c] - k[c] * kv));
+            }
+        }
+        for (int c = 0; c < nc; c++) q[(long)nc * t + c] = acc_get(&a[c]) / L;
+    }
+    free(m); free(re); free(im);
 }
