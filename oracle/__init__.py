@@ -19,8 +19,8 @@ are made absolutely convergent with the conventions that fix the result
 * Laplace TP: Ewald, k = 0 removed (requires neutral charges);
 * Stokes TP: Hasimoto split, k = 0 removed (zero mean flow; a net force is
   allowed);
-* Laplace SP: direct symmetric image sum with an Euler-Maclaurin tail
-  (requires neutral charges);
+* Laplace / Stokes SP: direct symmetric image sum with an Euler-Maclaurin
+  tail (requires neutral charges / zero net force);
 * Laplace / Stokes DP (x, y periodic, z free): 2D Ewald split, in-plane
   modes by the trapezoid rule in k_z, the k_par = 0 term in closed form
   (requires neutral charges / zero net in-plane force).
@@ -72,6 +72,7 @@ def _load():
             lib.orc_stokes_tp.argtypes = [l, P, P, l, P, d, d, d, i, d, P]
             lib.orc_laplace_sp.argtypes = [l, P, P, l, P, i, d, l, P]
             lib.orc_dp.argtypes = [i, l, P, P, l, P, d, d, d, d, d, P]
+            lib.orc_stokes_sp.argtypes = [l, P, P, l, P, i, d, l, P]
             _lib = lib
     return _lib
 
@@ -139,6 +140,16 @@ def laplace_sp(src, q, trg, axis: int = 0, L: float = 1.0, M: int = 200) -> np.n
     return out
 
 
+def stokes_sp(src, f, trg, axis: int = 0, L: float = 1.0, M: int = 200) -> np.ndarray:
+    """Stokes, singly periodic along ``axis`` (zero net force required): image
+    sum |n|<=M with a pair-independent 1/n regularisation and a closed-form
+    Euler-Maclaurin tail."""
+    y, x, phi = _c(src), _c(trg), _c(f).reshape(-1, 3)
+    out = np.zeros((len(x), 3))
+    _load().orc_stokes_sp(len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), axis, L, M, _ptr(out))
+    return out
+
+
 def doubly_periodic(kernel: int, src, dens, trg, L: float = 1.0, xi=None, rc=None) -> np.ndarray:
     """Periodic in x and y (period L), free in z: 2D Ewald sum.
 
@@ -176,8 +187,9 @@ def periodic_sum(kernel: int, periodic_axes: int, src, dens, trg, L: float = 1.0
         return laplace_tp(src, dens, trg, L) if kernel == LAPLACE else stokes_tp(src, dens, trg, L)
     if periodic_axes == 3:
         return doubly_periodic(kernel, src, dens, trg, L)
-    if kernel == LAPLACE and periodic_axes in (1, 2, 4):
-        return laplace_sp(src, dens, trg, axis={1: 0, 2: 1, 4: 2}[periodic_axes], L=L)
+    if periodic_axes in (1, 2, 4):
+        ax = {1: 0, 2: 1, 4: 2}[periodic_axes]
+        return laplace_sp(src, dens, trg, axis=ax, L=L) if kernel == LAPLACE else stokes_sp(src, dens, trg, ax, L)
     raise NotImplementedError(f"oracle: kernel {kernel} periodicity {periodic_axes}")
 
 

@@ -424,3 +424,112 @@ void orc_dp(int kernel, long S, const double *y, const double *phi, long T, cons
     }
     free(m); free(re); free(im);
 }
+
+/* ---------- singly periodic Stokes ---------- */
+
+/* Regularised 1D lattice sum of the Stokeslet for one pair, axis `ax`
+ * (unit period), r the minimum-image offset:
+ *   G = sum_{|n|<=M} S(r + n e) - (1/8pi)(I + e e^T) 2 H_M
+ *       + sum_{n>M} [S(r + n e) + S(r - n e) - (1/8pi)(I + e e^T) 2/n],
+ * the pair-independent 2 H_M term cancelling for zero net force.  The tail
+ * is summed by Euler-Maclaurin from n0 = M + 1 (integral + g/2 - g'/12);
+ * the integral is closed form: with w1 = a + n0, w2 = n0 - a (a the axial
+ * offset), rho the perpendicular offset, R_i = sqrt(w_i^2 + rho^2),
+ * Lg = -ln((w1 + R1)/2n0) - ln((w2 + R2)/2n0), c = 1/8pi:
+ *   (e,e)    c [2 Lg + w1/R1 + w2/R2 - 2]
+ *   (p,p)    c Lg + c rho_p^2 B,   (p,q) c rho_p rho_q B,
+ *            B = 1/(R1 (R1 + w1)) + 1/(R2 (R2 + w2))
+ *   (e,p)    c rho_p (1/R1 - 1/R2).
+ * The coincident image is excluded. */
+static void stokes_grad(const double d[3], int k, double out[9]) {
+    /* d/dd_k of S(d), times 8 pi */
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r = sqrt(r2), ir3 = 1.0 / (r2 * r), ir5 = ir3 / r2;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            out[3 * i + j] = -(i == j ? d[k] * ir3 : 0.0) + ((i == k ? d[j] : 0.0) + (j == k ? d[i] : 0.0)) * ir3 -
+                             3.0 * d[i] * d[j] * d[k] * ir5;
+}
+
+static void sp_stokes_pair(const double r[3], int ax, long M, double G[9]) {
+    const double c = 1.0 / (8.0 * M_PI);
+    acc_t s[9];
+    memset(s, 0, sizeof s);
+    double blk[9];
+    for (long n = -M; n <= M; n++) {
+        double d[3] = {r[0], r[1], r[2]};
+        d[ax] += (double)n;
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (r2 == 0.0) continue;
+        stokeslet(d, sqrt(r2), blk);
+        for (int i = 0; i < 9; i++) acc_add(&s[i], blk[i]);
+    }
+    double H = 0.0;
+    {
+        acc_t h = {0, 0};
+        for (long n = M; n >= 1; n--) acc_add(&h, 1.0 / (double)n);
+        H = acc_get(&h);
+    }
+    for (int i = 0; i < 3; i++) {
+        acc_add(&s[4 * i], -c * 2.0 * H);
+        if (i == ax) acc_add(&s[4 * i], -c * 2.0 * H);
+    }
+    /* Euler-Maclaurin tail */
+    double n0 = (double)(M + 1), a = r[ax], rho2 = 0.0, rho[3] = {0, 0, 0};
+    for (int i = 0; i < 3; i++)
+        if (i != ax) {
+            rho[i] = r[i];
+            rho2 += r[i] * r[i];
+        }
+    double w1 = a + n0, w2 = n0 - a, R1 = sqrt(w1 * w1 + rho2), R2 = sqrt(w2 * w2 + rho2);
+    double up = (a + (2.0 * n0 * a + a * a + rho2) / (R1 + n0)) / (2.0 * n0);
+    double um = (-a + (-2.0 * n0 * a + a * a + rho2) / (R2 + n0)) / (2.0 * n0);
+    double Lg = -log1p(up) - log1p(um);
+    double B = 1.0 / (R1 * (R1 + w1)) + 1.0 / (R2 * (R2 + w2));
+    double J[9];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double v;
+            if (i == ax && j == ax) v = 2.0 * Lg - rho2 / (R1 * (R1 + w1)) - rho2 / (R2 * (R2 + w2));
+            else if (i == ax) v = rho[j] * (1.0 / R1 - 1.0 / R2);
+            else if (j == ax) v = rho[i] * (1.0 / R1 - 1.0 / R2);
+            else v = (i == j ? Lg : 0.0) + rho[i] * rho[j] * B;
+            J[3 * i + j] = c * v;
+        }
+    /* g(n0) and g'(n0) */
+    double dp[3] = {r[0], r[1], r[2]}, dm[3] = {r[0], r[1], r[2]};
+    dp[ax] += n0;
+    dm[ax] -= n0;
+    double Sp[9], Sm[9], Gp[9], Gm[9];
+    stokeslet(dp, sqrt(dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2]), Sp);
+    stokeslet(dm, sqrt(dm[0] * dm[0] + dm[1] * dm[1] + dm[2] * dm[2]), Sm);
+    stokes_grad(dp, ax, Gp);
+    stokes_grad(dm, ax, Gm);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            int q = 3 * i + j;
+            double reg = (i == j ? 1.0 : 0.0) + (i == ax && j == ax ? 1.0 : 0.0);
+            double g = Sp[q] + Sm[q] - c * reg * 2.0 / n0;
+            double dg = c * (Gp[q] - Gm[q]) + c * reg * 2.0 / (n0 * n0);
+            acc_add(&s[q], J[q]);
+            acc_add(&s[q], 0.5 * g);
+            acc_add(&s[q], -dg / 12.0);
+        }
+    for (int i = 0; i < 9; i++) G[i] = acc_get(&s[i]);
+}
+
+void orc_stokes_sp(long S, const double *y, const double *f, long T, const double *x,
+                   int axis, double L, long M, double *u) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long t = 0; t < T; t++) {
+        acc_t a[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (long s = 0; s < S; s++) {
+            double r[3], G[9];
+            for (int c = 0; c < 3; c++) r[c] = (x[3 * t + c] - y[3 * s + c]) / L;
+            r[axis] -= floor(r[axis] + 0.5);
+            sp_stokes_pair(r, axis, M, G);
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) acc_add(&a[i], G[3 * i + j] * f[3 * s + j]);
+        }
+        for (int c = 0; c < 3; c++) u[3 * t + c] = acc_get(&a[c]) / L;
+    }
+}
