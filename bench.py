@@ -1,12 +1,25 @@
 #!/usr/bin/env python
-"""Benchmark: periodic KIFMM targets/s on the Stokes triply periodic workload.
+"""Benchmark: periodic KIFMM targets/s.
 
-Workload (default): Stokes velocity kernel, triply periodic unit cube,
-N = 1,048,576 uniform points (sources = targets), forces N(0,1) per component
-with the net force removed, p = 8, leaf <= 64, one density vector; the MIXED
-path (binary32 kernel sums, M2L on the tensor cores, binary64 root operator).
-A step is one pkifmm_evaluate: Morton sort, octree, lists, upward pass, root
-periodic operator, M2L, downward pass, leaves.
+Workloads (``--workload``; the default is the first):
+
+* ``stokes_tp``: Stokes velocity kernel, triply periodic unit cube,
+  N = 1,048,576 uniform points (sources = targets), forces N(0,1) per
+  component with the net force removed, p = 8, leaf <= 64, one density
+  vector.
+* ``stokes_dp_slab``: Stokes, periodic in x and y, N = 4,194,304 points in 64
+  Gaussian clusters (sigma 0.02) inside the slab z in [0, 0.2], zero net
+  force, p = 10, adaptive tree to depth 12.
+* ``stokes_tp_batch16``: Stokes TP, N = 2,097,152 uniform points, 16 force
+  vectors on one geometry, p = 8.
+* ``laplace_tp_multi``: 256 independent triply periodic Laplace problems,
+  N log-uniform in [1024, 65536], neutral charges U[-1,1], p = 6, one batched
+  evaluation; the leaf size is picked by the library's autotuner first.
+
+All run the MIXED path (binary32 kernel sums, M2L on the tensor cores,
+binary64 root operator).  A step is one evaluation: Morton sort, octree,
+lists, upward pass, root periodic operator, M2L, downward pass, leaves.
+Targets/s counts targets x density vectors.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 oracle
 (Ewald sum) instead, on a bounded sample of the same workload's targets.
@@ -75,34 +88,84 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def workload(n, seed):
+WORKLOADS = {
+    "stokes_tp": dict(kernel=1, periodic=7, n=1 << 20, p=8, leaf=64, depth=10, nrhs=1, sample=256),
+    "stokes_dp_slab": dict(kernel=1, periodic=3, n=1 << 22, p=10, leaf=64, depth=12, nrhs=1, sample=128),
+    "stokes_tp_batch16": dict(kernel=1, periodic=7, n=1 << 21, p=8, leaf=64, depth=10, nrhs=16, sample=128),
+    "laplace_tp_multi": dict(kernel=0, periodic=7, n=256, p=6, leaf=32, depth=10, nrhs=1, sample=32),
+}
+
+
+def workload(name, n, seed):
+    """(points, densities [nrhs][N][k], problem offsets or None, description)."""
     from paper_1705_02043_gb300 import workloads as w
-    x, f = w.stokes_uniform(n, seed=seed, nrhs=1)
-    return x, f
+    if name == "stokes_tp":
+        x, f = w.stokes_uniform(n, seed=seed, nrhs=1)
+        return x, f, None, "seeded uniform points, N(0,1) forces, net force removed"
+    if name == "stokes_dp_slab":
+        x, f = w.clustered_slab(n, seed=seed, nclusters=64, sigma=0.02, zlo=0.0, zhi=0.2, kdim=3)
+        return x, f[None], None, "64 Gaussian clusters (sigma 0.02) in the slab z in [0, 0.2], N(0,1) forces, zero net"
+    if name == "stokes_tp_batch16":
+        x, f = w.stokes_uniform(n, seed=seed, nrhs=16)
+        return x, f, None, "seeded uniform points, 16 N(0,1) force vectors, each with zero net force"
+    if name == "laplace_tp_multi":
+        x, q, off = w.multi_laplace_tp(n, seed=seed)
+        return x, q[None, :, None], off, f"{n} problems, N log-uniform in [1024, 65536], neutral U[-1,1] charges"
+    raise ValueError(name)
+
+
+def oracle_sum(kernel, periodic, x, d, xt):
+    import oracle
+    out = oracle.periodic_sum(kernel, periodic, x, d, xt)
+    return out if kernel == 1 else out[:, None]
+
+
+def oracle_sample(wl, x, d, off, nsample, rng):
+    """Seeded target sample and the oracle's values there (first density vector)."""
+    kernel, periodic = wl["kernel"], wl["periodic"]
+    if off is None:
+        idx = np.sort(rng.choice(len(x), nsample, replace=False))
+        return idx, oracle_sum(kernel, periodic, x, d[0], x[idx])
+    # independent problems: 8 seeded problems, nsample targets each
+    probs = np.sort(rng.choice(len(off) - 1, min(8, len(off) - 1), replace=False))
+    idx, ref = [], []
+    for j in probs:
+        a, b = off[j], off[j + 1]
+        t = np.sort(rng.choice(b - a, min(nsample, b - a), replace=False)) + a
+        idx.append(t)
+        ref.append(oracle_sum(kernel, periodic, x[a:b], d[0, a:b], x[t]))
+    return np.concatenate(idx), np.concatenate(ref)
+
+
+def workload_name(name, wl, n, p, leaf):
+    if name == "laplace_tp_multi":
+        return f"laplace_tp_multi_{n}problems_p{p}"
+    return f"{name}_N{n}_p{p}_leaf{leaf}" + (f"_nrhs{wl['nrhs']}" if wl["nrhs"] > 1 else "")
 
 
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on a bounded target sample per step."""
     if rank != 0:
         return
-    import oracle
-    x, f = workload(args.n, 0)
+    wl = WORKLOADS[args.workload]
+    x, d, off, desc = workload(args.workload, args.n, 0)
     rng = np.random.default_rng(123)
-    per_step = args.ref_sample
-    times = []
+    times, ntg = [], 0
     for s in range(args.warmup + args.steps):
-        idx = rng.choice(args.n, per_step, replace=False)
         t = time.perf_counter()
-        oracle.stokes_tp(x, f[0], x[idx])
+        idx, _ = oracle_sample(wl, x, d, off, args.ref_sample, rng)
         if s >= args.warmup:
             times.append(time.perf_counter() - t)
-    v = per_step / float(np.mean(times))
-    sample = f"{per_step} of {args.n} targets per step (seeded), all {args.n} sources"
+            ntg = len(idx)
+    v = ntg / float(np.mean(times))
+    sample = (f"{ntg} targets per step (seeded) of the workload, all sources of their problem; "
+              f"first density vector")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "targets/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"stokes_tp_uniform_N{args.n}_p8_leaf64", "oracle": "Hasimoto Ewald, FP64, CPU"},
+        "config": {"workload": workload_name(args.workload, wl, args.n, args.p, args.leaf),
+                   "oracle": "Ewald sums (Hasimoto for Stokes), FP64, CPU"},
         "cpu_baseline": {"value": v, "unit": "targets/s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -114,13 +177,20 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=1 << 20)
-    ap.add_argument("--p", type=int, default=8)
-    ap.add_argument("--leaf", type=int, default=64)
-    ap.add_argument("--sample", type=int, default=256, help="oracle targets for accuracy / cpu_baseline")
+    ap.add_argument("--workload", default="stokes_tp", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=None, help="points (problems for laplace_tp_multi)")
+    ap.add_argument("--p", type=int, default=None)
+    ap.add_argument("--leaf", type=int, default=None)
+    ap.add_argument("--sample", type=int, default=None, help="oracle targets for accuracy / cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=64, help="oracle targets per reference step")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison step")
     args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    args.n = args.n or wl["n"]
+    args.p = args.p or wl["p"]
+    args.leaf = args.leaf or wl["leaf"]
+    args.sample = args.sample or wl["sample"]
+    kernel, periodic, nrhs, k = wl["kernel"], wl["periodic"], wl["nrhs"], (1 if wl["kernel"] == 0 else 3)
 
     rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
@@ -129,6 +199,7 @@ def main():
 
     import torch
     import paper_1705_02043_gb300 as pk
+    from paper_1705_02043_gb300 import multi
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -142,128 +213,150 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    x, f = workload(args.n, rank)
+    x, d, off, desc = workload(args.workload, args.n, rank)
+    ntrg = len(x)
     cache = os.path.join(ROOT, "_build_cache")
-    plan = pk.PeriodicKIFMM(pk.STOKES, 7, p=args.p, leaf_max=args.leaf, depth_max=10, precision=pk.MIXED,
-                            nrhs=1, cache_dir=cache)
-    tx, tf = torch.tensor(x, device=dev), torch.tensor(f, device=dev)
-    out = torch.empty((1, args.n, 3), dtype=torch.float64, device=dev)
+    plan = pk.PeriodicKIFMM(kernel, periodic, p=args.p, leaf_max=args.leaf, depth_max=wl["depth"],
+                            precision=pk.MIXED, nrhs=nrhs, cache_dir=cache)
+    tx, td = torch.tensor(x, device=dev), torch.tensor(np.ascontiguousarray(d), device=dev)
+    out = torch.empty((nrhs, ntrg, k), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
+    tuned = None
+    if off is not None:
+        best, ms = plan.autotune_leaf(off, off, tx, td, tx, candidates=(16, 24, 32, 48, 64, 96), reps=1)
+        tuned = {"candidates": [16, 24, 32, 48, 64, 96], "ms": [round(float(v), 3) for v in ms], "best": best}
+        args.leaf = best
+
+    def evaluate(o):
+        if off is None:
+            plan.evaluate(tx, td, tx, o)
+        else:
+            plan.evaluate_batched(off, off, tx, td, tx, o)
+
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > L2
     for _ in range(args.warmup):
-        plan.evaluate(tx, tf, tx, out)
+        evaluate(out)
     barrier()
     clk = ClockSampler(local)
     l0 = pk.pkifmm_launch_count()
     step_ms, m2l_ms = [], []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
+    for i in range(args.steps):
         flush.add_(1.0)  # write a buffer larger than L2 between timed steps
-        ev[k][0].record(stream)
-        plan.evaluate(tx, tf, tx, out)
-        ev[k][1].record(stream)
+        ev[i][0].record(stream)
+        evaluate(out)
+        ev[i][1].record(stream)
         torch.cuda.synchronize()
-        step_ms.append(ev[k][0].elapsed_time(ev[k][1]))
-        m2l_ms.append(float(plan.stage_times()[4]))
+        step_ms.append(ev[i][0].elapsed_time(ev[i][1]))
+        m2l_ms.append(float(plan.stage_times()[8]))
     barrier()
     launches = pk.pkifmm_launch_count() - l0
     clocks = clk.stop()
     stages = plan.stage_times().tolist()
     stats = plan.tree_stats().tolist()
-    t_step = float(np.mean(step_ms))
-    if dist is not None:
-        t = torch.tensor([t_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = world * args.n / (t_step / 1e3)
+    t_step = multi.max_over_ranks(float(np.mean(step_ms)), dist, dev)
+    value = world * ntrg * nrhs / (t_step / 1e3)
 
-    # end to end through the host-buffer entry point (pinned host memory)
+    # end to end through the public API with host buffers (pinned host memory):
+    # host->device copies of points and densities, the evaluation, device->host result
     hx = torch.tensor(x).pin_memory()
-    hf = torch.tensor(f).pin_memory()
-    hp = torch.empty((1, args.n, 3), dtype=torch.float64).pin_memory()
-    plan.evaluate_host(hx, hf, hx, hp)
+    hd = torch.tensor(np.ascontiguousarray(d)).pin_memory()
+    hp = torch.empty((nrhs, ntrg, k), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        if off is None:
+            plan.evaluate_host(hx, hd, hx, hp)
+        else:
+            gx, gd = hx.to(dev, non_blocking=True), hd.to(dev, non_blocking=True)
+            go = plan.evaluate_batched(off, off, gx, gd, gx)
+            hp.copy_(go, non_blocking=True)
+            torch.cuda.synchronize()
+
+    e2e_step()
     barrier()
     e2e_t = []
     for _ in range(max(3, min(args.steps, 5))):
         flush.add_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        plan.evaluate_host(hx, hf, hx, hp)
+        e2e_step()
         e2e_t.append(time.perf_counter() - t0)
-    e2e_v = world * args.n / float(np.mean(e2e_t))
-    h2d = 3 * 8 * args.n * 3  # sources, forces, targets
-    d2h = 3 * 8 * args.n
+    e2e_v = world * ntrg * nrhs / multi.max_over_ranks(float(np.mean(e2e_t)), dist, dev)
+    h2d = 8 * (3 * ntrg + nrhs * ntrg * k) if off is not None else 8 * (3 * ntrg + nrhs * ntrg * k + 3 * ntrg)
+    d2h = 8 * nrhs * ntrg * k
 
     result = None
     if rank == 0:
-        u = out.cpu().numpy()[0]
+        u = out.cpu().numpy()
         pk_, src = peaks()
         nV = stats[4]
-        kn = 3 * (6 * (args.p - 1) ** 2 + 2)
-        flops = 2.0 * kn * kn * nV  # per M2L launch, nrhs = 1
+        kn = k * (6 * (args.p - 1) ** 2 + 2)
+        flops = 2.0 * kn * kn * nV * nrhs  # per M2L (all launches of one evaluation)
         m2l_avg = float(np.mean(m2l_ms))
         achieved = flops / (m2l_avg / 1e3) / 1e12
-        tc = plan_uses_tensor_cores()
-        if tc:
-            peak = pk_.get("bf16_tflops_sustained", 1700.0)
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": "M2L (V list), split-fp16 x3 tcgen05", "peak_source": f"bf16_tflops_sustained ({src})"}
-        else:
-            mhz = (clocks or {}).get("sm_mhz") or pk_.get("sm_max_mhz", 2070.0)
-            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "M2L (V list), FP32 FMA",
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
-        roof["algorithmic_flops_per_launch"] = flops
-        roof["avg_launch_ms"] = m2l_avg
+        peak = pk_.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_m2l_tc: M2L (V list), split-fp16 x3 tcgen05",
+                "peak_source": f"bf16_tflops_sustained ({src}), same rate as fp16",
+                "algorithmic_flops_per_launch": flops, "avg_launch_ms": m2l_avg,
+                "issued_tensor_frac": achieved * 3 / peak}
         # accuracy and the CPU baseline: the FP64 oracle on a seeded target sample
-        import oracle
         rng = np.random.default_rng(123)
-        idx = np.sort(rng.choice(args.n, args.sample, replace=False))
         t0 = time.perf_counter()
-        ref = oracle.stokes_tp(x, f[0], x[idx])
+        idx, ref = oracle_sample(wl, x, d, off, args.sample, rng)
         t_cpu = time.perf_counter() - t0
-        err = oracle.error_metrics(u[idx], ref)
+        err = __import__("oracle").error_metrics(u[0][idx], ref)
         fp64 = None
         if not args.no_fp64:
-            p64 = pk.PeriodicKIFMM(pk.STOKES, 7, p=args.p, leaf_max=args.leaf, depth_max=10, precision=pk.FP64,
-                                   nrhs=1, cache_dir=cache)
+            p64 = pk.PeriodicKIFMM(kernel, periodic, p=args.p, leaf_max=args.leaf, depth_max=wl["depth"],
+                                   precision=pk.FP64, nrhs=nrhs, cache_dir=cache)
             o64 = torch.empty_like(out)
-            p64.evaluate(tx, tf, tx, o64)
+
+            def ev64():
+                if off is None:
+                    p64.evaluate(tx, td, tx, o64)
+                else:
+                    p64.evaluate_batched(off, off, tx, td, tx, o64)
+            ev64()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.add_(1.0)
             e0.record(stream)
-            p64.evaluate(tx, tf, tx, o64)
+            ev64()
             e1.record(stream)
             torch.cuda.synchronize()
             t64 = e0.elapsed_time(e1)
-            fp64 = {"value": args.n / (t64 / 1e3), "unit": "targets/s", "ms_per_step": t64,
-                    "rel_l2": oracle.error_metrics(o64.cpu().numpy()[0][idx], ref)["rel_l2"],
+            fp64 = {"value": ntrg * nrhs / (t64 / 1e3), "unit": "targets/s", "ms_per_step": t64,
+                    "rel_l2": __import__("oracle").error_metrics(o64.cpu().numpy()[0][idx], ref)["rel_l2"],
                     "stage_ms": p64.stage_times().tolist()}
             p64.close()
         result = {
             "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "mixed: f32 sums, fp16x3 tensor M2L, f64 root" if tc else "f32",
-            "data": "synthetic (seeded uniform points, N(0,1) forces, net force removed)",
-            "config": {"workload": f"stokes_tp_uniform_N{args.n}_p{args.p}_leaf{args.leaf}", "kernel": "stokes",
-                       "periodic": "xyz", "N": args.n, "p": args.p, "leaf_max": args.leaf, "nrhs": 1,
+            "vs_baseline": None, "dtype": "mixed: f32 sums, fp16x3 tensor M2L, f64 root",
+            "data": f"synthetic ({desc})",
+            "config": {"workload": workload_name(args.workload, wl, args.n, args.p, args.leaf),
+                       "kernel": "stokes" if kernel == 1 else "laplace",
+                       "periodic": {7: "xyz", 3: "xy", 0: "none"}.get(periodic, str(periodic)),
+                       "N": ntrg, "p": args.p, "leaf_max": args.leaf, "depth_max": wl["depth"], "nrhs": nrhs,
+                       "problems": 1 if off is None else len(off) - 1,
                        "precision": "mixed", "parallelism": f"{world} independent problems",
                        "l2": "256 MiB buffer written between timed steps"},
             "e2e": {"value": e2e_v, "unit": "targets/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * float(np.mean(e2e_t))},
             "gpu_launches": launches,
             "roofline": roof,
-            "cpu_baseline": {"value": args.sample / t_cpu, "unit": "targets/s", "cores": os.cpu_count(),
+            "cpu_baseline": {"value": len(idx) / t_cpu, "unit": "targets/s", "cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": f"{args.sample} of {args.n} targets (seeded), all {args.n} sources"},
-            "accuracy": {"vs": "FP64 Ewald oracle", "targets": args.sample, **err},
+                             "sample": f"{len(idx)} seeded targets of the workload, all sources of their problem, "
+                                       f"first density vector"},
+            "accuracy": {"vs": "FP64 Ewald oracle", "targets": int(len(idx)), "density_vector": 0, **err},
             "fp64_path": fp64,
             "stage_ms": dict(zip(["sort", "tree_lists", "upward", "root", "m2l", "downward", "leaves", "total"],
                                  stages)),
             "tree": dict(zip(["boxes", "leaves", "depth", "U", "V", "W", "X", "p2p_pairs"], stats)),
+            "autotune": tuned,
             "clocks": clocks,
         }
     plan.close()

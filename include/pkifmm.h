@@ -21,6 +21,8 @@
  * (compatcondition), Sec. 3.3, Sec. 3.4):
  *   Laplace, any periodicity: charges must be neutral;
  *   Stokes SP/DP: net force must be zero;
+ *   DP (x, y periodic, z free; Sec. 3.3): the k_par = 0 (sheet) part of K^P
+ *     is fixed up to a z-independent constant, which cancels by the above;
  *   Stokes TP: a net force is allowed, zero mean flow (Hasimoto, k = 0 removed).
  *   Laplace TP: k = 0 removed (zero mean potential).
  *
@@ -68,14 +70,15 @@ enum {
     PKIFMM_ERR_OOM = -5,          /* device or host allocation failed */
     PKIFMM_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
     PKIFMM_ERR_CACHE = -7,        /* operator cache unreadable / unwritable */
-    PKIFMM_ERR_UNSUPPORTED = -8   /* combination not built (e.g. DP kernel) */
+    PKIFMM_ERR_UNSUPPORTED = -8   /* combination not built (DP in x-z or y-z; MIXED without tcgen05) */
 };
 
 /* Build a plan: Algorithm 2, Stage 1 (precompute), Sec. 2.2-2.3.
  *   kernel         PKIFMM_LAPLACE or PKIFMM_STOKES
  *   periodic_axes  bit 0 = x, bit 1 = y, bit 2 = z; 0 = free space.
- *                  Built: 0 (any kernel), 7 (TP, both kernels),
- *                  one axis (SP, Laplace).  Others return UNSUPPORTED.
+ *                  Built for both kernels: 0 (free space), one axis
+ *                  (SP: 1, 2 or 4), 3 (DP in x and y), 7 (TP).  The
+ *                  other doubly periodic pairs (5, 6) return UNSUPPORTED.
  *   box_lo, box_len  B0 = [box_lo, box_lo + box_len)^3 (host pointer, 3 doubles)
  *   p              points per edge of the equivalent/check surfaces (Sec. 2.2,
  *                  n = 6(p-1)^2 + 2), 4 <= p <= 16
@@ -112,6 +115,44 @@ int pkifmm_evaluate(pkifmm_plan plan, int64_t S, const double *src_xyz,
 int pkifmm_evaluate_host(pkifmm_plan plan, int64_t S, const double *src_xyz,
                          const double *dens, int64_t T, const double *trg_xyz,
                          double *pot, void *cuda_stream);
+
+/* Many independent problems in one evaluation (a batch), e.g. a set of
+ * unit cells of different sizes sharing kernel, periodicity, box and p
+ * (each problem is the problem of Sec. 2.2 on its own).  Problem j owns
+ * sources src_off[j] .. src_off[j+1]-1 and targets trg_off[j] ..
+ * trg_off[j+1]-1 of the concatenated arrays:
+ *   src_off, trg_off  HOST arrays of nprob + 1 non-decreasing int64,
+ *                     src_off[0] = trg_off[0] = 0; S = src_off[nprob],
+ *                     T = trg_off[nprob]
+ *   src_xyz, dens, trg_xyz, pot  DEVICE arrays laid out as in
+ *                     pkifmm_evaluate for S sources and T targets
+ *                     (dens [nrhs][S][k], pot [nrhs][T][k]).
+ * All problems are evaluated together: one forest with one root per
+ * problem (problem index above the Morton key), every stage one pass over
+ * all problems' boxes; no interaction crosses problems.  The compatibility
+ * condition is checked per problem (NOT_NEUTRAL if any problem violates
+ * it).  nprob >= 1 with nprob <= 2^(63 - 3 depth_max); otherwise
+ * INVALID_ARG.  Results equal nprob separate pkifmm_evaluate calls up to
+ * rounding. */
+int pkifmm_evaluate_batched(pkifmm_plan plan, int nprob, const int64_t *src_off,
+                            const int64_t *trg_off, const double *src_xyz,
+                            const double *dens, const double *trg_xyz, double *pot,
+                            void *cuda_stream);
+
+/* Leaf-size autotuner (the paper fixes s by hand, Sec. 3.6; no counterpart).
+ * For each candidate leaf size s (candidates[0..ncand-1], each >= 1) the
+ * plan evaluates the given batch (arguments as pkifmm_evaluate_batched) once
+ * to warm up and then `reps` times, timing each call on the host clock
+ * around the call plus a stream synchronisation; the fastest candidate
+ * becomes the plan's leaf size and is written to *best_out, the per
+ * candidate minimum times (ms) to ms_out[0..ncand-1] (nullable).  pot holds
+ * the last evaluation's result.  Operators do not depend on s, so nothing
+ * is recomputed.  On error the plan keeps its previous leaf size. */
+int pkifmm_autotune_leaf(pkifmm_plan plan, int nprob, const int64_t *src_off,
+                         const int64_t *trg_off, const double *src_xyz,
+                         const double *dens, const double *trg_xyz, double *pot,
+                         const int *candidates, int ncand, int reps, int *best_out,
+                         double *ms_out, void *cuda_stream);
 
 /* Per-stage device times (ms) of the last evaluate, in this order:
  * 0 keys+sort, 1 tree+lists, 2 upward (S2M, M2M), 3 root periodic operator,

@@ -42,6 +42,8 @@ def load_library():
             lib.pkifmm_plan_create.argtypes = [ctypes.POINTER(P), i, u, P, d, i, i, i, i, i, i, ctypes.c_char_p]
             lib.pkifmm_evaluate.argtypes = [P, i64, P, P, i64, P, P, P]
             lib.pkifmm_evaluate_host.argtypes = [P, i64, P, P, i64, P, P, P]
+            lib.pkifmm_evaluate_batched.argtypes = [P, i, P, P, P, P, P, P, P]
+            lib.pkifmm_autotune_leaf.argtypes = [P, i, P, P, P, P, P, P, P, i, i, P, P, P]
             lib.pkifmm_last_stage_times.argtypes = [P, P, i]
             lib.pkifmm_tree_stats.argtypes = [P, P, i]
             lib.pkifmm_tree_export.argtypes = [P, P, P, P, P, P, P, P]
@@ -99,6 +101,27 @@ def pkifmm_evaluate(plan, S, src, dens, T, trg, pot, stream=None):
 def pkifmm_evaluate_host(plan, S, src, dens, T, trg, pot, stream=None):
     return _check(load_library().pkifmm_evaluate_host(plan, S, _ptr(src), _ptr(dens), T, _ptr(trg), _ptr(pot),
                                                       stream))
+
+
+def pkifmm_evaluate_batched(plan, nprob, src_off, trg_off, src, dens, trg, pot, stream=None):
+    so = np.ascontiguousarray(src_off, dtype=np.int64)
+    to = np.ascontiguousarray(trg_off, dtype=np.int64)
+    if so.shape != (nprob + 1,) or to.shape != (nprob + 1,):
+        raise ValueError("offsets must have nprob + 1 entries")
+    return _check(load_library().pkifmm_evaluate_batched(plan, nprob, _ptr(so), _ptr(to), _ptr(src), _ptr(dens),
+                                                         _ptr(trg), _ptr(pot), stream))
+
+
+def pkifmm_autotune_leaf(plan, nprob, src_off, trg_off, src, dens, trg, pot, candidates, reps=2, stream=None):
+    so = np.ascontiguousarray(src_off, dtype=np.int64)
+    to = np.ascontiguousarray(trg_off, dtype=np.int64)
+    cand = np.ascontiguousarray(candidates, dtype=np.int32)
+    best = np.zeros(1, dtype=np.int32)
+    ms = np.zeros(len(cand))
+    _check(load_library().pkifmm_autotune_leaf(plan, nprob, _ptr(so), _ptr(to), _ptr(src), _ptr(dens), _ptr(trg),
+                                               _ptr(pot), _ptr(cand), len(cand), reps, _ptr(best), _ptr(ms),
+                                               stream))
+    return int(best[0]), ms
 
 
 def pkifmm_last_stage_times(plan):
@@ -206,6 +229,35 @@ class PeriodicKIFMM:
             stream = torch.cuda.current_stream(src.device).cuda_stream
         pkifmm_evaluate(self.handle, S, src, dens, T, trg, pot, ctypes.c_void_p(stream))
         return pot
+
+    def evaluate_batched(self, src_off, trg_off, src, dens, trg, pot=None, stream=None):
+        """Independent problems in one call: problem j owns rows
+        src_off[j]:src_off[j+1] of src/dens and trg_off[j]:trg_off[j+1] of trg
+        (CUDA tensors as in evaluate; offsets on the host)."""
+        import torch
+        for t in (src, dens, trg):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("inputs must be contiguous float64 CUDA tensors")
+        nprob = len(src_off) - 1
+        if pot is None:
+            pot = torch.empty((self.nrhs, trg.shape[0], self.k), dtype=torch.float64, device=src.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(src.device).cuda_stream
+        pkifmm_evaluate_batched(self.handle, nprob, src_off, trg_off, src, dens, trg, pot, ctypes.c_void_p(stream))
+        return pot
+
+    def autotune_leaf(self, src_off, trg_off, src, dens, trg, candidates=(16, 24, 32, 48, 64, 96, 128), reps=2,
+                      stream=None):
+        """Time the batch for each candidate leaf size and keep the fastest;
+        returns (best leaf size, per-candidate ms)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(src.device).cuda_stream
+        pot = torch.empty((self.nrhs, trg.shape[0], self.k), dtype=torch.float64, device=src.device)
+        best, ms = pkifmm_autotune_leaf(self.handle, len(src_off) - 1, src_off, trg_off, src, dens, trg, pot,
+                                        candidates, reps, ctypes.c_void_p(stream))
+        self.leaf_max = best
+        return best, ms
 
     def evaluate_host(self, src, dens, trg, pot=None, stream=None):
         """Host arrays in and out (numpy, or CPU torch tensors, e.g. pinned);

@@ -2,6 +2,7 @@
 // include/pkifmm.h).  Orchestrates Algorithm 2: Stage 1 in
 // pkifmm_plan_create, Stage 2 in pkifmm_evaluate.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -42,23 +43,29 @@ int guarded(F &&f) {
     }
 }
 
+// corr [nprob][nrhs] (nullable); the problem of sorted target t is the prefix of its key
 __global__ void k_unpermute(const double *__restrict__ pot_s, const int *__restrict__ idx, long long T, int nrhs,
-                            int k, double invL, const double *__restrict__ corr, double *__restrict__ pot) {
+                            int k, double invL, const double *__restrict__ corr,
+                            const unsigned long long *__restrict__ keyT, int key_shift, double *__restrict__ pot) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= T * nrhs * k) return;
     long long t = i / (nrhs * k);
     int rem = (int)(i % (nrhs * k)), r = rem / k, a = rem % k;
     double v = pot_s[i];
-    if (corr) v += corr[r];
+    if (corr) v += corr[(long long)(keyT[t] >> key_shift) * nrhs + r];
     pot[((long long)r * T + idx[t]) * k + a] = v * invL;
 }
 
-// sums[2*c] += phi, sums[2*c+1] += |phi| per (rhs, component) c
-__global__ void k_dens_sums(const double *__restrict__ dens, long long S, int nk, double *sums) {
+// sums[2*(j*nk+c)] += phi, sums[2*(j*nk+c)+1] += |phi| per problem j (blockIdx.z,
+// sorted sources soff[j]..soff[j+1]) and (rhs, component) c
+__global__ void k_dens_sums(const double *__restrict__ dens, const long long *__restrict__ soff, int nk,
+                            double *sums) {
     extern __shared__ double sh[];
-    int c = blockIdx.y;
+    int c = blockIdx.y, j = blockIdx.z;
     double a = 0, b = 0;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < S; s += (long long)gridDim.x * blockDim.x) {
+    const long long s0 = soff[j], s1 = soff[j + 1];
+    for (long long s = s0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; s < s1;
+         s += (long long)gridDim.x * blockDim.x) {
         double v = dens[s * nk + c];
         a += v;
         b += fabs(v);
@@ -74,8 +81,8 @@ __global__ void k_dens_sums(const double *__restrict__ dens, long long S, int nk
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        atomicAdd(&sums[2 * c], sh[0]);
-        atomicAdd(&sums[2 * c + 1], sh[blockDim.x]);
+        atomicAdd(&sums[2 * ((long long)j * nk + c)], sh[0]);
+        atomicAdd(&sums[2 * ((long long)j * nk + c) + 1], sh[blockDim.x]);
     }
 }
 
@@ -86,20 +93,23 @@ __global__ void k_dens_sums(const double *__restrict__ dens, long long S, int nk
 // upward equivalent density) therefore receive far fields that differ by the
 // constant (2 pi / 3V) (sum q |y - c|^2 - sum phi^u |y^u - c|^2).  That
 // constant is restored here so the result is the zero-mean Ewald potential.
-__global__ void k_second_moment_src(const double *__restrict__ xs, const double *__restrict__ dens, long long S,
-                                    int nrhs, double *__restrict__ m2) {
-    int r = blockIdx.y;
+// m2[j*nrhs + r]: problem j (blockIdx.z), sorted sources soff[j]..soff[j+1]
+__global__ void k_second_moment_src(const double *__restrict__ xs, const double *__restrict__ dens,
+                                    const long long *__restrict__ soff, int nrhs, double *__restrict__ m2) {
+    int r = blockIdx.y, j = blockIdx.z;
     double acc = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = soff[j] + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < soff[j + 1];
+         i += (long long)gridDim.x * blockDim.x) {
         double dx = xs[3 * i] - 0.5, dy = xs[3 * i + 1] - 0.5, dz = xs[3 * i + 2] - 0.5;
         acc += dens[i * nrhs + r] * (dx * dx + dy * dy + dz * dz);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&m2[r], acc);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&m2[(long long)j * nrhs + r], acc);
 }
 
+// roots are boxes 0..nprob-1: block r = j * nrhs + rhs reads row r; writes m2[rows + r]
 template <typename T>
-__global__ void k_second_moment_root(const T *__restrict__ up, const double *__restrict__ g, int n, int nrhs,
+__global__ void k_second_moment_root(const T *__restrict__ up, const double *__restrict__ g, int n, int rows,
                                      double *__restrict__ m2) {
     int r = blockIdx.x;
     double acc = 0;
@@ -108,27 +118,27 @@ __global__ void k_second_moment_root(const T *__restrict__ up, const double *__r
         acc += (double)up[(long long)r * n + j] * 0.525 * 0.525 * g2;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&m2[nrhs + r], acc);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&m2[rows + r], acc);
 }
 
-__global__ void k_moment_finish(const double *m2, int nrhs, double *corr) {
-    int r = threadIdx.x;
-    if (r < nrhs) corr[r] = 2.0 * 3.14159265358979323846 / 3.0 * (m2[r] - m2[nrhs + r]);
+__global__ void k_moment_finish(const double *m2, int rows, double *corr) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < rows) corr[r] = 2.0 * 3.14159265358979323846 / 3.0 * (m2[r] - m2[rows + r]);
 }
 
 const double *laplace_tp_constant(Plan &P, cudaStream_t s) {
     if (P.kernel != PKIFMM_LAPLACE || P.periodic != 7) return nullptr;
-    int nr = P.nrhs;
-    P.sums.reserve(4 * nr + 4);
-    double *m2 = P.sums.p, *corr = P.sums.p + 2 * nr;
-    PK_CUDA(cudaMemsetAsync(m2, 0, sizeof(double) * 2 * nr, s));
-    dim3 grid((unsigned)std::min<long long>(512, (P.S + 255) / 256), nr);
-    count_launch(), k_second_moment_src<<<grid, 256, 0, s>>>(P.xs.p, P.dens_s.p, P.S, nr, m2);
+    const int nr = P.nrhs, rows = P.nprob * nr;
+    P.sums.reserve(3 * (size_t)rows + 4);
+    double *m2 = P.sums.p, *corr = P.sums.p + 2 * rows;
+    PK_CUDA(cudaMemsetAsync(m2, 0, sizeof(double) * 2 * rows, s));
+    dim3 grid((unsigned)std::min<long long>(64, (P.S / P.nprob + 255) / 256 + 1), nr, P.nprob);
+    count_launch(), k_second_moment_src<<<grid, 256, 0, s>>>(P.xs.p, P.dens_s.p, P.soff.p, nr, m2);
     if (P.precision == PKIFMM_FP64)
-        count_launch(), k_second_moment_root<double><<<nr, 256, 0, s>>>(P.up64.p, P.g64.p, P.n, nr, m2);
+        count_launch(), k_second_moment_root<double><<<rows, 256, 0, s>>>(P.up64.p, P.g64.p, P.n, rows, m2);
     else
-        count_launch(), k_second_moment_root<float><<<nr, 256, 0, s>>>(P.up32.p, P.g64.p, P.n, nr, m2);
-    count_launch(), k_moment_finish<<<1, 64, 0, s>>>(m2, nr, corr);
+        count_launch(), k_second_moment_root<float><<<rows, 256, 0, s>>>(P.up32.p, P.g64.p, P.n, rows, m2);
+    count_launch(), k_moment_finish<<<(rows + 255) / 256, 256, 0, s>>>(m2, rows, corr);
     return corr;
 }
 
@@ -142,13 +152,25 @@ void record(Plan &P, int i, cudaStream_t s) {
     if (P.events) PK_CUDA(cudaEventRecord(P.ev[i], s));
 }
 
-int evaluate_impl(Plan &P, int64_t S, const double *src, const double *dens, int64_t T, const double *trg,
-                  double *pot, cudaStream_t s) {
-    if (S < 0 || T < 0 || S > (1LL << 30) || T > (1LL << 30)) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
+// nprob independent problems: problem j owns sources soff[j]..soff[j+1] and
+// targets toff[j]..toff[j+1] (host CSR arrays of nprob+1 entries).
+int evaluate_impl(Plan &P, int nprob, const int64_t *soff, const int64_t *toff, const double *src,
+                  const double *dens, const double *trg, double *pot, cudaStream_t s) {
+    if (nprob < 1 || !soff || !toff) return fail(PKIFMM_ERR_INVALID_ARG, "nprob < 1 or NULL offsets");
+    int pbits = 0;
+    while ((1LL << pbits) < nprob) pbits++;
+    if (3 * P.depth_max + pbits > 63) return fail(PKIFMM_ERR_INVALID_ARG, "too many problems for depth_max");
+    if (soff[0] != 0 || toff[0] != 0) return fail(PKIFMM_ERR_INVALID_ARG, "offsets must start at 0");
+    for (int j = 0; j < nprob; j++)
+        if (soff[j + 1] < soff[j] || toff[j + 1] < toff[j])
+            return fail(PKIFMM_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    const int64_t S = soff[nprob], T = toff[nprob];
+    if (S > (1LL << 30) || T > (1LL << 30)) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
     if ((S && (!src || !dens)) || (T && (!trg || !pot))) return fail(PKIFMM_ERR_INVALID_ARG, "NULL array");
     PK_CUDA(cudaSetDevice(P.device));
     P.S = S;
     P.T = T;
+    P.nprob = nprob;
     std::fill(P.stage_ms, P.stage_ms + 9, 0.0);
     if (T == 0) return PKIFMM_OK;
     if (S == 0) {
@@ -156,21 +178,37 @@ int evaluate_impl(Plan &P, int64_t S, const double *src, const double *dens, int
         return PKIFMM_OK;
     }
     record(P, 0, s);
+    {
+        std::vector<long long> h(2 * (size_t)(nprob + 1));
+        P.same_offsets = true;
+        for (int j = 0; j <= nprob; j++) {
+            h[j] = soff[j];
+            h[nprob + 1 + j] = toff[j];
+            P.same_offsets &= soff[j] == toff[j];
+        }
+        P.soff.reserve(nprob + 1);
+        P.toff.reserve(nprob + 1);
+        PK_CUDA(cudaMemcpyAsync(P.soff.p, h.data(), sizeof(long long) * (nprob + 1), cudaMemcpyHostToDevice, s));
+        PK_CUDA(cudaMemcpyAsync(P.toff.p, h.data() + nprob + 1, sizeof(long long) * (nprob + 1),
+                                cudaMemcpyHostToDevice, s));
+        PK_CUDA(cudaStreamSynchronize(s));  // h goes out of scope
+    }
     sort_points(P, src, dens, trg, s);
     int err[4] = {0, 0, 0, 0};
     PK_CUDA(cudaMemcpy(err, P.err.p, sizeof err, cudaMemcpyDeviceToHost));
     if (err[0]) return fail(PKIFMM_ERR_INVALID_ARG, "non-finite coordinate");
     if (err[1]) return fail(PKIFMM_ERR_OUT_OF_BOX, "point outside the box along a free axis");
     if (needs_neutral(P)) {
-        int nk = P.nrhs * P.k;
-        P.sums.reserve(2 * nk);
-        PK_CUDA(cudaMemsetAsync(P.sums.p, 0, sizeof(double) * 2 * nk, s));
-        dim3 grid((unsigned)std::min<long long>(1024, (S + 255) / 256), nk);
-        count_launch(), k_dens_sums<<<grid, 256, 2 * 256 * sizeof(double), s>>>(P.dens_s.p, S, nk, P.sums.p);
-        std::vector<double> h(2 * nk);
-        PK_CUDA(cudaMemcpyAsync(h.data(), P.sums.p, sizeof(double) * 2 * nk, cudaMemcpyDeviceToHost, s));
+        const int nk = P.nrhs * P.k;
+        const size_t nsum = 2 * (size_t)nk * nprob;
+        P.sums.reserve(nsum);
+        PK_CUDA(cudaMemsetAsync(P.sums.p, 0, sizeof(double) * nsum, s));
+        dim3 grid((unsigned)std::min<long long>(nprob > 1 ? 64 : 1024, (S / nprob + 255) / 256 + 1), nk, nprob);
+        count_launch(), k_dens_sums<<<grid, 256, 2 * 256 * sizeof(double), s>>>(P.dens_s.p, P.soff.p, nk, P.sums.p);
+        std::vector<double> h(nsum);
+        PK_CUDA(cudaMemcpyAsync(h.data(), P.sums.p, sizeof(double) * nsum, cudaMemcpyDeviceToHost, s));
         PK_CUDA(cudaStreamSynchronize(s));
-        for (int c = 0; c < nk; c++)
+        for (size_t c = 0; c < nsum / 2; c++)
             if (std::fabs(h[2 * c]) > 1e-12 * h[2 * c + 1])
                 return fail(PKIFMM_ERR_NOT_NEUTRAL, "densities violate the compatibility condition (net charge / force)");
     }
@@ -191,7 +229,7 @@ int evaluate_impl(Plan &P, int64_t S, const double *src, const double *dens, int
     long long n = T * P.nrhs * P.k;
     const double *corr = laplace_tp_constant(P, s);
     count_launch(), k_unpermute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.pot_s.p, P.idxT.p, T, P.nrhs, P.k, 1.0 / P.L, corr,
-                                                             pot);
+                                                             P.keyT.p, 3 * P.depth_max, pot);
     record(P, 7, s);
     PK_CUDA(cudaGetLastError());
     return PKIFMM_OK;
@@ -217,8 +255,8 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, con
         nrhs < 1 || nrhs > 64 || (precision != PKIFMM_FP64 && precision != PKIFMM_MIXED))
         return fail(PKIFMM_ERR_INVALID_ARG, "p / ell / leaf_max / depth_max / nrhs / precision out of range");
     bool sp = periodic_axes == 1 || periodic_axes == 2 || periodic_axes == 4;
-    if (!(periodic_axes == 0 || periodic_axes == 7 || (sp && kernel == PKIFMM_LAPLACE)))
-        return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built for this kernel");
+    if (!(periodic_axes == 0 || periodic_axes == 7 || periodic_axes == 3 || sp))
+        return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built (doubly periodic: x and y only)");
     return guarded([&]() {
         auto *h = new pkifmm_plan_s;
         Plan &P = h->P;
@@ -260,7 +298,19 @@ int pkifmm_evaluate(pkifmm_plan plan, int64_t S, const double *src_xyz, const do
                     const double *trg_xyz, double *pot, void *cuda_stream) {
     if (!plan) return fail(PKIFMM_ERR_INVALID_ARG, "plan is NULL");
     return guarded([&]() {
-        return evaluate_impl(plan->P, S, src_xyz, dens, T, trg_xyz, pot, (cudaStream_t)cuda_stream);
+        if (S < 0 || T < 0) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
+        int64_t so[2] = {0, S}, to[2] = {0, T};
+        return evaluate_impl(plan->P, 1, so, to, src_xyz, dens, trg_xyz, pot, (cudaStream_t)cuda_stream);
+    });
+}
+
+int pkifmm_evaluate_batched(pkifmm_plan plan, int nprob, const int64_t *src_off, const int64_t *trg_off,
+                            const double *src_xyz, const double *dens, const double *trg_xyz, double *pot,
+                            void *cuda_stream) {
+    if (!plan) return fail(PKIFMM_ERR_INVALID_ARG, "plan is NULL");
+    return guarded([&]() {
+        return evaluate_impl(plan->P, nprob, src_off, trg_off, src_xyz, dens, trg_xyz, pot,
+                             (cudaStream_t)cuda_stream);
     });
 }
 
@@ -270,6 +320,7 @@ int pkifmm_evaluate_host(pkifmm_plan plan, int64_t S, const double *src_xyz, con
     return guarded([&]() {
         Plan &P = plan->P;
         cudaStream_t s = (cudaStream_t)cuda_stream;
+        if (S < 0 || T < 0 || S > (1LL << 30) || T > (1LL << 30)) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
         PK_CUDA(cudaSetDevice(P.device));
         size_t bs = sizeof(double) * 3 * S, bd = sizeof(double) * S * P.nrhs * P.k;
         size_t bt = sizeof(double) * 3 * T, bp = sizeof(double) * T * P.nrhs * P.k;
@@ -282,7 +333,9 @@ int pkifmm_evaluate_host(pkifmm_plan plan, int64_t S, const double *src_xyz, con
             PK_CUDA(cudaMemcpyAsync(dd, dens, bd, cudaMemcpyHostToDevice, s));
         }
         if (T) PK_CUDA(cudaMemcpyAsync(dt, trg_xyz, bt, cudaMemcpyHostToDevice, s));
-        int rc = evaluate_impl(P, S, ds, dd, T, dt, dp, s);
+        if (S < 0 || T < 0) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
+        int64_t so[2] = {0, S}, to[2] = {0, T};
+        int rc = evaluate_impl(P, 1, so, to, ds, dd, dt, dp, s);
         if (rc == PKIFMM_OK && T) PK_CUDA(cudaMemcpyAsync(pot, dp, bp, cudaMemcpyDeviceToHost, s));
         PK_CUDA(cudaStreamSynchronize(s));
         buf.release();
@@ -309,6 +362,52 @@ int pkifmm_last_stage_times(pkifmm_plan plan, double *ms, int max) {
         int m = std::min(max, 9);
         for (int i = 0; i < m; i++) ms[i] = P.stage_ms[i];
         return m;
+    });
+}
+
+int pkifmm_autotune_leaf(pkifmm_plan plan, int nprob, const int64_t *src_off, const int64_t *trg_off,
+                         const double *src_xyz, const double *dens, const double *trg_xyz, double *pot,
+                         const int *candidates, int ncand, int reps, int *best_out, double *ms_out,
+                         void *cuda_stream) {
+    if (!plan || !candidates || ncand < 1 || reps < 1 || !best_out)
+        return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
+    for (int c = 0; c < ncand; c++)
+        if (candidates[c] < 1) return fail(PKIFMM_ERR_INVALID_ARG, "leaf size < 1");
+    return guarded([&]() {
+        Plan &P = plan->P;
+        cudaStream_t s = (cudaStream_t)cuda_stream;
+        const int keep = P.leaf_max;
+        int best = keep;
+        double best_ms = 1e300;
+        for (int c = 0; c < ncand; c++) {
+            P.leaf_max = candidates[c];
+            int rc = evaluate_impl(P, nprob, src_off, trg_off, src_xyz, dens, trg_xyz, pot, s);  // warm-up
+            if (rc != PKIFMM_OK) {
+                P.leaf_max = keep;
+                return rc;
+            }
+            PK_CUDA(cudaStreamSynchronize(s));
+            double t_min = 1e300;
+            for (int r = 0; r < reps; r++) {
+                auto t0 = std::chrono::steady_clock::now();
+                rc = evaluate_impl(P, nprob, src_off, trg_off, src_xyz, dens, trg_xyz, pot, s);
+                PK_CUDA(cudaStreamSynchronize(s));
+                auto t1 = std::chrono::steady_clock::now();
+                if (rc != PKIFMM_OK) {
+                    P.leaf_max = keep;
+                    return rc;
+                }
+                t_min = std::min(t_min, std::chrono::duration<double, std::milli>(t1 - t0).count());
+            }
+            if (ms_out) ms_out[c] = t_min;
+            if (t_min < best_ms) {
+                best_ms = t_min;
+                best = candidates[c];
+            }
+        }
+        P.leaf_max = best;
+        *best_out = best;
+        return (int)PKIFMM_OK;
     });
 }
 
@@ -499,7 +598,7 @@ int pkifmm_root_operator(int kernel, unsigned periodic_axes, int p, int ell, dou
     bool sp = periodic_axes == 1 || periodic_axes == 2 || periodic_axes == 4;
     if ((kernel != 0 && kernel != 1) || p < 2 || p > 16 || ell < 1 || ell > 8 || !m_out)
         return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
-    if (!(periodic_axes == 7 || (sp && kernel == 0))) return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built");
+    if (!(periodic_axes == 7 || periodic_axes == 3 || sp)) return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built");
     return guarded([&]() {
         auto M = root_operator(kernel, p, periodic_axes, ell, surface_grid(p));
         std::copy(M.begin(), M.end(), m_out);

@@ -119,6 +119,9 @@ struct Plan {
 
     // evaluation workspace
     int64_t S = 0, T = 0;
+    int nprob = 1;                              // independent problems in this evaluation
+    DBuf<long long> soff, toff;                 // [nprob+1] CSR offsets of their points
+    bool same_offsets = true;                   // soff == toff element by element
     DBuf<unsigned long long> keyS, keyT, keyS2, keyT2;
     DBuf<int> idxS, idxT, idxS2, idxT2;
     DBuf<int> hist;

@@ -270,13 +270,173 @@ void far_sp_laplace(int axis, int ell, const double *r, double *out) {
     out[0] = s.get();
 }
 
+// Doubly periodic (x, y periodic, z free), unit cell, 2D Ewald split with
+// the Hasimoto smooth part K_F (Laplace: erf(xi r)/r).  Per in-plane Fourier
+// mode k = (k_x, k_y) != 0 the z transform of K_F^ is taken in closed form:
+//   J(z) = int dk_z/2pi e^{-K^2/4xi^2}/K^2 e^{i k_z z}
+//        = [e^{kz} erfc(k/2xi + xi z) + e^{-kz} erfc(k/2xi - xi z)] / 4k,
+//   H(z) = int dk_z/2pi (1 + K^2/4xi^2) e^{-K^2/4xi^2}/K^4 e^{i k_z z}
+//        = -dJ/d(k^2),   H'(z) = -z P / 8k,
+// with K^2 = k^2 + k_z^2, P the bracket of J and D the same with a minus sign.
+// The Stokes block is (K^2 I - kk^T) H with k_z -> -i d/dz:
+//   in-plane (J + E/(4 xi sqrt(pi))) delta_ij - k_i k_j H,  (i,z): i k_i H',
+//   (z,z) k^2 H,  E = e^{-k^2/4xi^2 - xi^2 z^2}.
+// The k = 0 mode is the sheet field with z-independent constants dropped
+// (they cancel for neutral densities):
+//   Laplace 4 pi [-(z/2) erf(xi z) - e^{-xi^2 z^2}/(2 xi sqrt(pi))],
+//   Stokes  (I - e_z e_z) [-(z/2) erf(xi z) - e^{-xi^2 z^2}/(4 xi sqrt(pi))].
+// Near images |n|_inf <= ell (in-plane) contribute K_R - K = -K_F; farther
+// real-space images are negligible for |r_a| <= 1.1 and xi = 7.5.
+void far_dp(int kernel, int ell, const double *r, double *out) {
+    const double xi = 7.5, kc = 2.0 * 6.6 * xi, sqpi = std::sqrt(kPi);
+    const int mmax = (int)std::ceil(kc / (2 * kPi));
+    const double g0 = 2.0 * xi / sqpi;
+    int k = kernel == 0 ? 1 : 3;
+    Neumaier acc[9];
+    for (int n0 = -ell; n0 <= ell; n0++)
+        for (int n1 = -ell; n1 <= ell; n1++) {
+            double d[3] = {r[0] + n0, r[1] + n1, r[2]};
+            double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double dd = std::sqrt(d2);
+            if (kernel == 0) {
+                acc[0].add(d2 > 0 ? -std::erf(xi * dd) / dd : -g0);
+            } else {
+                double cI, cR;
+                if (d2 > 0) {
+                    double e = g0 * std::exp(-xi * xi * d2), f = std::erf(xi * dd) / dd;
+                    cI = e + f;
+                    cR = -(e - f) / d2;
+                } else {
+                    cI = 2.0 * g0;
+                    cR = 0.0;
+                }
+                for (int a = 0; a < 3; a++)
+                    for (int b = 0; b < 3; b++)
+                        acc[3 * a + b].add(-((a == b ? cI : 0.0) + cR * d[a] * d[b]) / (8.0 * kPi));
+            }
+        }
+    const double z = r[2];
+    for (int my = 0; my <= mmax; my++)
+        for (int mx = -mmax; mx <= mmax; mx++) {
+            if (my == 0 && mx <= 0) continue;  // half plane of in-plane modes, k = 0 below
+            double kx = 2 * kPi * mx, ky = 2 * kPi * my, kk = std::sqrt(kx * kx + ky * ky);
+            if (kk >= kc) continue;
+            double th = kx * r[0] + ky * r[1], cs = std::cos(th), sn = std::sin(th);
+            double ap = kk / (2 * xi) + xi * z, am = kk / (2 * xi) - xi * z;
+            double tp = std::exp(kk * z) * std::erfc(ap), tm = std::exp(-kk * z) * std::erfc(am);
+            double P = tp + tm, D = tp - tm;
+            double E = std::exp(-kk * kk / (4 * xi * xi) - xi * xi * z * z);
+            double J = P / (4 * kk);
+            if (kernel == 0) {
+                acc[0].add(2.0 * 4.0 * kPi * J * cs);
+                continue;
+            }
+            double H = P / (8 * kk * kk * kk) - z * D / (8 * kk * kk) + E / (4 * kk * kk * xi * sqpi);
+            double Hp = -z * P / (8 * kk);
+            double kv[2] = {kx, ky};
+            for (int i = 0; i < 2; i++)
+                for (int j = 0; j < 2; j++)
+                    acc[3 * i + j].add(2.0 * cs * ((i == j ? J + E / (4 * xi * sqpi) : 0.0) - kv[i] * kv[j] * H));
+            for (int i = 0; i < 2; i++) {
+                double v = -2.0 * kv[i] * Hp * sn;  // (k, -k) pair of i k_i H' e^{i k.r}
+                acc[3 * i + 2].add(v);
+                acc[3 * 2 + i].add(v);
+            }
+            acc[8].add(2.0 * cs * kk * kk * H);
+        }
+    double lin = -0.5 * z * std::erf(xi * z), ez = std::exp(-xi * xi * z * z);
+    if (kernel == 0) {
+        acc[0].add(4.0 * kPi * (lin - ez / (2 * xi * sqpi)));
+    } else {
+        double g = lin - ez / (4 * xi * sqpi);
+        acc[0].add(g);
+        acc[4].add(g);
+    }
+    for (int i = 0; i < k * k; i++) out[i] = acc[i].get();
+}
+
+// Singly periodic Stokes along `axis`, unit period, zero net force:
+// K^{P,F}_ell(r) = sum_{n > ell} [S(r + n e) + S(r - n e) - (2/n) C] - sum_{2<=n<=ell} (2/n) C,
+// C = (I + e e^T)/8pi (the monopole far field of one image), which cancels
+// for zero net force; n <= M explicitly, then Euler-Maclaurin from n0 = M+1
+// with the closed-form integral of the summand.  In the frame (e, p, q):
+// w1 = x + n0, w2 = n0 - x, R_i = |(w_i, rho)|, lg = -ln((w1+R1)/2n0) - ln((w2+R2)/2n0),
+// beta = 1/(R1(R1+w1)) + 1/(R2(R2+w2)):
+//   int (e,e) = (2 lg - rho^2 beta)/8pi,  int (e,p) = rho_p (1/R1 - 1/R2)/8pi,
+//   int (p,q) = (lg delta_pq + rho_p rho_q beta)/8pi.
+void far_sp_stokes(int axis, int ell, const double *r, double *out) {
+    const long M = 512;
+    const double c8 = 1.0 / (8.0 * kPi);
+    double C[9];
+    for (int i = 0; i < 9; i++) C[i] = 0.0;
+    for (int i = 0; i < 3; i++) C[4 * i] = c8;
+    C[4 * axis] += c8;
+    auto stokeslet = [&](const double d[3], double o[9]) {
+        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], id = 1.0 / std::sqrt(d2), id3 = id * id * id;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) o[3 * i + j] = c8 * ((i == j ? id : 0.0) + d[i] * d[j] * id3);
+    };
+    Neumaier acc[9];
+    for (long n = ell; n >= 2; n--)
+        for (int i = 0; i < 9; i++) acc[i].add(-2.0 / n * C[i]);
+    double sp[9], sm[9];
+    for (long n = M; n > ell; n--) {
+        double dp[3] = {r[0], r[1], r[2]}, dm[3] = {r[0], r[1], r[2]};
+        dp[axis] += n;
+        dm[axis] -= n;
+        stokeslet(dp, sp);
+        stokeslet(dm, sm);
+        for (int i = 0; i < 9; i++) acc[i].add(sp[i] + sm[i] - 2.0 / n * C[i]);
+    }
+    const double n0 = M + 1.0, x = r[axis];
+    double rho[3] = {r[0], r[1], r[2]};
+    rho[axis] = 0.0;
+    const double rho2 = rho[0] * rho[0] + rho[1] * rho[1] + rho[2] * rho[2];
+    const double w1 = x + n0, w2 = n0 - x, R1 = std::sqrt(w1 * w1 + rho2), R2 = std::sqrt(w2 * w2 + rho2);
+    const double u1 = (x + (2 * n0 * x + x * x + rho2) / (R1 + n0)) / (2 * n0);
+    const double u2 = (-x + (-2 * n0 * x + x * x + rho2) / (R2 + n0)) / (2 * n0);
+    const double lg = -std::log1p(u1) - std::log1p(u2);
+    const double beta = 1.0 / (R1 * (R1 + w1)) + 1.0 / (R2 * (R2 + w2));
+    // g(n0) and its derivative in n: d/dn S(r +- n e) = +-(e.grad) S
+    double dp[3] = {r[0], r[1], r[2]}, dm[3] = {r[0], r[1], r[2]};
+    dp[axis] += n0;
+    dm[axis] -= n0;
+    stokeslet(dp, sp);
+    stokeslet(dm, sm);
+    auto dS = [&](const double d[3], int i, int j) {  // d S_ij / d d_axis
+        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], dd = std::sqrt(d2), i3 = 1.0 / (d2 * dd), i5 = i3 / d2;
+        double v = -(i == j ? d[axis] * i3 : 0.0) + ((i == axis ? d[j] : 0.0) + (j == axis ? d[i] : 0.0)) * i3 -
+                   3.0 * d[i] * d[j] * d[axis] * i5;
+        return c8 * v;
+    };
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double in;
+            if (i == axis && j == axis) in = 2 * lg - rho2 * beta;
+            else if (i == axis) in = rho[j] * (1.0 / R1 - 1.0 / R2);
+            else if (j == axis) in = rho[i] * (1.0 / R1 - 1.0 / R2);
+            else in = (i == j ? lg : 0.0) + rho[i] * rho[j] * beta;
+            const int q = 3 * i + j;
+            double g = sp[q] + sm[q] - 2.0 / n0 * C[q];
+            double dg = dS(dp, i, j) - dS(dm, i, j) + 2.0 / (n0 * n0) * C[q];
+            acc[q].add(c8 * in);
+            acc[q].add(0.5 * g);
+            acc[q].add(-dg / 12.0);
+        }
+    for (int i = 0; i < 9; i++) out[i] = acc[i].get();
+}
+
 }  // namespace
 
 void far_kernel_block(int kernel, unsigned periodic, int ell, const double *r, double *out) {
     if (periodic == 7) {
         far_tp(kernel, ell, r, out);
-    } else if (kernel == 0 && (periodic == 1 || periodic == 2 || periodic == 4)) {
-        far_sp_laplace(periodic == 1 ? 0 : periodic == 2 ? 1 : 2, ell, r, out);
+    } else if (periodic == 3) {
+        far_dp(kernel, ell, r, out);
+    } else if (periodic == 1 || periodic == 2 || periodic == 4) {
+        const int axis = periodic == 1 ? 0 : periodic == 2 ? 1 : 2;
+        if (kernel == 0) far_sp_laplace(axis, ell, r, out);
+        else far_sp_stokes(axis, ell, r, out);
     } else {
         throw std::runtime_error("far kernel: periodicity not supported");
     }

@@ -114,6 +114,10 @@ void upload_operators(Plan &P) {
         P.m2l.reserve(kM2LOps * kn2);
         count_launch(), k_m2l_ops<double><<<nblk(tot, 256), 256>>>(P.kernel, P.n, P.g64.p, doffs.p, P.m2l.p);
     } else {
+        // the check-to-equivalent maps stay two factors, (V S+) and U^T: their
+        // product has entries of order 1/s_min and would cancel
+        // catastrophically in binary32 (the M2M / L2L products include the
+        // smoothing kernel matrix and do not)
         upload(P.uc2e_a32, H.uc2e_a);
         upload(P.uc2e_b32, H.uc2e_b);
         upload(P.dc2e_a32, H.dc2e_a);
@@ -266,11 +270,12 @@ __global__ void __launch_bounds__(256) k_slot_gemm(const int *__restrict__ tboxe
 }
 
 // y[r][i] = sum_j M[i][j] x[r][j] for nrhs vectors (binary64), one warp per row
+// (blockIdx.y covers vectors 16 y .. 16 y + 15, e.g. the roots of a batch)
 __global__ void k_matvec64(const double *__restrict__ M, const double *__restrict__ x, double *__restrict__ y,
                            int n, int nrhs) {
     int row = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x & 31;
     if (row >= n) return;
-    for (int r = 0; r < nrhs; r++) {
+    for (int r = blockIdx.y * 16; r < min(nrhs, (int)blockIdx.y * 16 + 16); r++) {
         double acc = 0;
         for (int j = lane; j < n; j += 32) acc += M[(long long)row * n + j] * x[(long long)r * n + j];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -279,7 +284,8 @@ __global__ void k_matvec64(const double *__restrict__ M, const double *__restric
 }
 
 static void matvec64(const double *M, const double *x, double *y, int n, int nrhs, cudaStream_t s) {
-    count_launch(), k_matvec64<<<(n + 7) / 8, 256, 0, s>>>(M, x, y, n, nrhs);
+    if (nrhs <= 0) return;
+    count_launch(), k_matvec64<<<dim3((n + 7) / 8, (nrhs + 15) / 16), 256, 0, s>>>(M, x, y, n, nrhs);
 }
 
 // ---------------- tasks ----------------
@@ -388,14 +394,14 @@ void build_tasks(Plan &P, cudaStream_t s) {
     make_task(P.t_root, {{0}}, 1, {0}, nr, s);
     // M2L: boxes of level >= 1 with targets, by octant class
     std::vector<std::vector<int>> byc(8);
-    for (int b = 1; b < nb; b++)
+    for (int b = P.nprob; b < nb; b++)  // boxes 0..nprob-1 are the problems' roots
         if (H.has_trg(b)) byc[H.octant(b)].push_back(b);
     std::vector<int> cls_op(8 * kVSlots);
     PK_CUDA(cudaMemcpy(cls_op.data(), P.class_slot_op.p, sizeof(int) * cls_op.size(), cudaMemcpyDeviceToHost));
     make_task(P.t_m2l, byc, kVSlots, cls_op, nr, s, bm);
     // DC2E over boxes with targets (root separately in binary64 for MIXED)
     std::vector<int> dc;
-    for (int b = (mixed ? 1 : 0); b < nb; b++)
+    for (int b = (mixed ? P.nprob : 0); b < nb; b++)
         if (H.has_trg(b)) dc.push_back(b);
     make_task(P.t_dc2e, {dc}, 1, {0}, nr, s, bm);
     // L2L per level >= 1, by octant class
@@ -405,6 +411,148 @@ void build_tasks(Plan &P, cudaStream_t s) {
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
             if (H.has_trg(b)) bc[H.octant(b)].push_back(b);
         make_task(P.t_l2l[l], bc, 1, ops8, nr, s, bm);
+    }
+}
+
+// Large binary32 slot GEMM: a 128 x 128 output tile per CTA, 16 K per step,
+// shared memory double-buffered, next step's global loads in registers while
+// the current one is multiplied, 16-byte loads where rows allow.  Each thread
+// owns rows {4 ty + i, 64 + 4 ty + i} and columns {4 tx + j, 64 + 4 tx + j}
+// (i, j < 4), read as float4 from shared memory without bank conflicts.  The
+// slots with a source in the tile are listed first and walked as one K
+// sequence; every output element is accumulated slot by slot, inputs in
+// order, exactly as in k_slot_gemm.
+constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 16;
+constexpr int SG_MAX_SLOTS = 256;
+
+__global__ void __launch_bounds__(256) k_slot_gemm_f32(const int *__restrict__ tboxes, const int4 *__restrict__ tiles,
+                                                       const int *__restrict__ slot_table, int slot_stride, int nslots,
+                                                       const int *__restrict__ class_ops, const float *__restrict__ ops,
+                                                       long long op_stride, const float *__restrict__ src,
+                                                       float *__restrict__ dst, int kn, int nrhs, int beta) {
+    __shared__ __align__(16) float As[2][SG_BK][SG_BM];
+    __shared__ __align__(16) float Bs[2][SG_BK][SG_BN];
+    __shared__ long long drow[SG_BM];
+    __shared__ int sbox[SG_BM];
+    __shared__ short act[SG_MAX_SLOTS];
+    __shared__ int nact_s;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int4 tile = tiles[blockIdx.x];
+    const int cls = tile.x, row0 = tile.y, nr = tile.z, n0 = blockIdx.y * SG_BN;
+    for (int i = tid; i < SG_BM; i += 256) {
+        if (i < nr) {
+            int row = row0 + i, tb = row / nrhs, rhs = row % nrhs, box = tboxes[tb];
+            drow[i] = (long long)box * nrhs + rhs;
+            sbox[i] = box;
+        } else {
+            drow[i] = -1;
+            sbox[i] = -1;
+        }
+    }
+    __syncthreads();
+    for (int sl = tid; sl < nslots; sl += 256) {
+        int any = 0;
+        if (class_ops[cls * nslots + sl] >= 0)
+            for (int i = 0; i < nr && !any; i++)
+                any = !slot_table || slot_table[(long long)sbox[i] * slot_stride + sl] >= 0;
+        act[sl] = (short)any;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int c = 0;
+        for (int sl = 0; sl < nslots; sl++)
+            if (act[sl]) act[c++] = (short)sl;
+        nact_s = c;
+    }
+    __syncthreads();
+    const int nk = (kn + SG_BK - 1) / SG_BK, total = nact_s * nk;
+    const bool vec = (kn & 3) == 0;
+    // loader: row lm of A (and of B), 8 consecutive k from lk
+    const int lm = tid >> 1, lk = (tid & 1) * 8;
+    const int my_box = sbox[lm];
+    const long long my_rhs = drow[lm] >= 0 ? drow[lm] - (long long)my_box * nrhs : 0;
+    const int nn = n0 + lm;
+    float ra[8], rb[8];
+    auto load = [&](int it) {
+        const int sl = act[it / nk], k0 = (it % nk) * SG_BK + lk;
+        const int op = class_ops[cls * nslots + sl];
+        const float *arow = nullptr;
+        if (my_box >= 0) {
+            const int sb = slot_table ? slot_table[(long long)my_box * slot_stride + sl] : my_box;
+            if (sb >= 0) arow = src + ((long long)sb * nrhs + my_rhs) * kn;
+        }
+        const float *brow = nn < kn ? ops + (long long)op * op_stride + (long long)nn * kn : nullptr;
+        if (vec && k0 + 8 <= kn) {
+            if (arow) {
+                float4 u = *reinterpret_cast<const float4 *>(arow + k0), v = *reinterpret_cast<const float4 *>(arow + k0 + 4);
+                ra[0] = u.x; ra[1] = u.y; ra[2] = u.z; ra[3] = u.w; ra[4] = v.x; ra[5] = v.y; ra[6] = v.z; ra[7] = v.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; q++) ra[q] = 0.f;
+            }
+            if (brow) {
+                float4 u = *reinterpret_cast<const float4 *>(brow + k0), v = *reinterpret_cast<const float4 *>(brow + k0 + 4);
+                rb[0] = u.x; rb[1] = u.y; rb[2] = u.z; rb[3] = u.w; rb[4] = v.x; rb[5] = v.y; rb[6] = v.z; rb[7] = v.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; q++) rb[q] = 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                ra[q] = (arow && k0 + q < kn) ? arow[k0 + q] : 0.f;
+                rb[q] = (brow && k0 + q < kn) ? brow[k0 + q] : 0.f;
+            }
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            As[buf][lk + q][lm] = ra[q];
+            Bs[buf][lk + q][lm] = rb[q];
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[i][j] = 0.f;
+    if (total > 0) {
+        load(0);
+        store(0);
+        __syncthreads();
+        for (int it = 0; it < total; it++) {
+            const int buf = it & 1;
+            if (it + 1 < total) load(it + 1);
+#pragma unroll
+            for (int kk = 0; kk < SG_BK; kk++) {
+                float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][4 * ty]);
+                float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + 4 * ty]);
+                float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][4 * tx]);
+                float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + 4 * tx]);
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int i = 0; i < 8; i++)
+#pragma unroll
+                    for (int j = 0; j < 8; j++) acc[i][j] += a[i] * b[j];
+            }
+            if (it + 1 < total) store(buf ^ 1);
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int m = (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
+        const long long dr = drow[m];
+        if (dr < 0) continue;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int c = n0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
+            if (c >= kn) continue;
+            float *d = dst + dr * kn + c;
+            *d = beta ? *d + acc[i][j] : acc[i][j];
+        }
     }
 }
 
@@ -423,6 +571,14 @@ static void gemm(const Task &t, const int *slot_table, int slot_stride, const T 
         return;
     }
     dim3 grid(t.ntiles, (kn + Big::BN - 1) / Big::BN, (bm + Big::BM - 1) / Big::BM);
+    if constexpr (std::is_same<T, float>::value) {
+        static_assert(Big::BM == SG_BM && Big::BN == SG_BN, "binary32 tiles");
+        if (t.nslots <= SG_MAX_SLOTS) {
+            count_launch(), k_slot_gemm_f32<<<grid, 256, 0, s>>>(t.boxes.p, t.tiles.p, slot_table, slot_stride, t.nslots,
+                                                                  t.class_ops.p, ops, op_stride, src, dst, kn, nrhs, beta);
+            return;
+        }
+    }
     count_launch(), k_slot_gemm<Big><<<grid, 256, 0, s>>>(t.boxes.p, t.tiles.p, slot_table, slot_stride, t.nslots,
                                                           t.class_ops.p, ops, op_stride, src, dst, kn, nrhs, beta);
 }
@@ -430,7 +586,7 @@ static void gemm(const Task &t, const int *slot_table, int slot_stride, const T 
 // ---------------- kernel sums ----------------
 
 template <typename T>
-struct V4 { T x, y, z, w; };
+struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };  // one 16-byte (binary32) access
 
 __device__ __forceinline__ double exp2i(int l) { return ldexp(1.0, -l); }
 
@@ -460,47 +616,94 @@ __global__ void k_cast(const double *__restrict__ a, T *__restrict__ b, long lon
 
 constexpr int KS_T = 128;  // threads of the kernel-sum blocks
 
+template <typename T, int K, int R>
+struct LeafAcc {
+    T acc[R][K], tot[R][K], cmp[R][K];
+    __device__ void init() {
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int a = 0; a < K; a++) acc[r][a] = tot[r][a] = cmp[r][a] = 0;
+    }
+    __device__ void flush() {
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int a = 0; a < K; a++) {
+                T y = acc[r][a] - cmp[r][a], s = tot[r][a] + y;
+                cmp[r][a] = (s - tot[r][a]) - y;
+                tot[r][a] = s;
+                acc[r][a] = 0;
+            }
+    }
+    // one source at offset d = x - y with densities f[r][a]
+    __device__ __forceinline__ void add(T dx, T dy, T dz, const T (*f)[K]) {
+        const T ir = inv_sqrt(dx * dx + dy * dy + dz * dz);
+        if constexpr (K == 1) {
+#pragma unroll
+            for (int r = 0; r < R; r++) acc[r][0] += ir * f[r][0];
+        } else {
+            const T cir = (T)0.039788735772973836 * ir;  // 1/(8 pi r)
+            const T c3 = cir * ir * ir;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const T fr = (f[r][0] * dx + f[r][1] * dy + f[r][2] * dz) * c3;
+                acc[r][0] += f[r][0] * cir + dx * fr;
+                acc[r][1] += f[r][1] * cir + dy * fr;
+                acc[r][2] += f[r][2] * cir + dz * fr;
+            }
+        }
+    }
+};
+
 // S2M: q~u[B][rhs][i] = h sum_{s in B} K(1.475 h g_i - yrel_s) phi_s
-template <typename T, int K>
+template <typename T, int K, int R>
 __global__ void __launch_bounds__(KS_T) k_s2m(const int *__restrict__ leaves, const int4 *__restrict__ bpos,
                                               const int2 *__restrict__ srange, const V4<T> *__restrict__ yrel,
-                                              const T *__restrict__ dens, int nrhs, int rhs,
+                                              const T *__restrict__ dens, int nrhs, int rhs0,
                                               const T *__restrict__ g, int n, T *__restrict__ chk) {
-    __shared__ T sy[KS_T][3], sphi[KS_T][K];
+    __shared__ V4<T> sy[KS_T];
+    __shared__ T sphi[KS_T][R][K];
     const int b = leaves[blockIdx.x];
     const int4 p = bpos[b];
     const T h = (T)exp2i(p.w), sc = (T)1.475 * h;
     const int2 r = srange[b];
-    const int kn = n * K;
+    const int kn = n * K, nv = min(R, nrhs - rhs0);
     for (int i0 = 0; i0 < n; i0 += KS_T) {
         int i = i0 + threadIdx.x;
-        T x[3] = {0, 0, 0};
+        T x0 = 0, x1 = 0, x2 = 0;
         if (i < n) {
-            x[0] = sc * g[3 * i];
-            x[1] = sc * g[3 * i + 1];
-            x[2] = sc * g[3 * i + 2];
+            x0 = sc * g[3 * i];
+            x1 = sc * g[3 * i + 1];
+            x2 = sc * g[3 * i + 2];
         }
-        T acc[K];
-#pragma unroll
-        for (int a = 0; a < K; a++) acc[a] = 0;
+        LeafAcc<T, K, R> L;
+        L.init();
         for (int s0 = r.x; s0 < r.y; s0 += KS_T) {
             __syncthreads();
-            int s = s0 + threadIdx.x;
-            if (s < r.y) {
-                V4<T> v = yrel[s];
-                sy[threadIdx.x][0] = v.x;
-                sy[threadIdx.x][1] = v.y;
-                sy[threadIdx.x][2] = v.z;
+            int sidx = s0 + threadIdx.x;
+            if (sidx < r.y) {
+                sy[threadIdx.x] = yrel[sidx];
 #pragma unroll
-                for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = dens[(long long)s * nrhs * K + rhs * K + a];
+                for (int q = 0; q < R; q++)
+#pragma unroll
+                    for (int a = 0; a < K; a++)
+                        sphi[threadIdx.x][q][a] = q < nv ? dens[(long long)sidx * nrhs * K + (rhs0 + q) * K + a] : (T)0;
             }
             __syncthreads();
             int m = min(KS_T, r.y - s0);
-            for (int j = 0; j < m; j++) Kern<T, K>::add(acc, x[0] - sy[j][0], x[1] - sy[j][1], x[2] - sy[j][2], sphi[j]);
+            for (int j = 0; j < m; j++) {
+                const V4<T> y = sy[j];
+                L.add(x0 - y.x, x1 - y.y, x2 - y.z, sphi[j]);
+            }
         }
         if (i < n) {
 #pragma unroll
-            for (int a = 0; a < K; a++) chk[((long long)b * nrhs + rhs) * kn + i * K + a] = h * acc[a];
+            for (int q = 0; q < R; q++)
+                if (q < nv)
+#pragma unroll
+                    for (int a = 0; a < K; a++)
+                        chk[((long long)b * nrhs + rhs0 + q) * kn + i * K + a] = h * L.acc[q][a];
         }
     }
 }
@@ -520,118 +723,124 @@ __device__ __forceinline__ void centre_offset(int4 B, int4 A, const int sh[3], d
 }
 
 // X list: q~d[B][rhs][i] += h_B sum_{(A,p) in X(B)} sum_{s in A} K(0.525 h_B g_i - yrel_s + off) phi_s
-template <typename T, int K>
+template <typename T, int K, int R>
 __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, const int4 *__restrict__ bpos,
                                               const int2 *__restrict__ srange, const int *__restrict__ xptr,
                                               const int *__restrict__ xbox, const unsigned char *__restrict__ xsh,
                                               const V4<T> *__restrict__ yrel, const T *__restrict__ dens, int nrhs,
-                                              int rhs, const T *__restrict__ g, int n, T *__restrict__ chk) {
-    __shared__ T sy[KS_T][3], sphi[KS_T][K];
+                                              int rhs0, const T *__restrict__ g, int n, T *__restrict__ chk) {
+    __shared__ V4<T> sy[KS_T];
+    __shared__ T sphi[KS_T][R][K];
     const int b = boxes[blockIdx.x];
     const int4 B = bpos[b];
     const T h = (T)exp2i(B.w), sc = (T)0.525 * h;
-    const int kn = n * K;
+    const int kn = n * K, nv = min(R, nrhs - rhs0);
     for (int i0 = 0; i0 < n; i0 += KS_T) {
         int i = i0 + threadIdx.x;
-        T x[3] = {0, 0, 0};
+        T x0 = 0, x1 = 0, x2 = 0;
         if (i < n) {
-            x[0] = sc * g[3 * i];
-            x[1] = sc * g[3 * i + 1];
-            x[2] = sc * g[3 * i + 2];
+            x0 = sc * g[3 * i];
+            x1 = sc * g[3 * i + 1];
+            x2 = sc * g[3 * i + 2];
         }
-        T acc[K];
-#pragma unroll
-        for (int a = 0; a < K; a++) acc[a] = 0;
+        LeafAcc<T, K, R> L;
+        L.init();
         for (int e = xptr[b]; e < xptr[b + 1]; e++) {
             int A = xbox[e], sh[3];
             decode_shift(xsh[e], sh);
             double off[3];
             centre_offset(B, bpos[A], sh, off);
-            T o0 = (T)off[0], o1 = (T)off[1], o2 = (T)off[2];
+            const T xo0 = x0 + (T)off[0], xo1 = x1 + (T)off[1], xo2 = x2 + (T)off[2];
             int2 r = srange[A];
             for (int s0 = r.x; s0 < r.y; s0 += KS_T) {
                 __syncthreads();
-                int s = s0 + threadIdx.x;
-                if (s < r.y) {
-                    V4<T> v = yrel[s];
-                    sy[threadIdx.x][0] = v.x;
-                    sy[threadIdx.x][1] = v.y;
-                    sy[threadIdx.x][2] = v.z;
+                int sidx = s0 + threadIdx.x;
+                if (sidx < r.y) {
+                    sy[threadIdx.x] = yrel[sidx];
 #pragma unroll
-                    for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = dens[(long long)s * nrhs * K + rhs * K + a];
+                    for (int q = 0; q < R; q++)
+#pragma unroll
+                        for (int a = 0; a < K; a++)
+                            sphi[threadIdx.x][q][a] =
+                                q < nv ? dens[(long long)sidx * nrhs * K + (rhs0 + q) * K + a] : (T)0;
                 }
                 __syncthreads();
                 int m = min(KS_T, r.y - s0);
-                for (int j = 0; j < m; j++)
-                    Kern<T, K>::add(acc, x[0] - sy[j][0] + o0, x[1] - sy[j][1] + o1, x[2] - sy[j][2] + o2, sphi[j]);
+                for (int j = 0; j < m; j++) {
+                    const V4<T> y = sy[j];
+                    L.add(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
+                }
             }
         }
         if (i < n) {
 #pragma unroll
-            for (int a = 0; a < K; a++) chk[((long long)b * nrhs + rhs) * kn + i * K + a] += h * acc[a];
+            for (int q = 0; q < R; q++)
+                if (q < nv)
+#pragma unroll
+                    for (int a = 0; a < K; a++)
+                        chk[((long long)b * nrhs + rhs0 + q) * kn + i * K + a] += h * L.acc[q][a];
         }
     }
 }
 
-// Leaf: L2T + W-list M2T + U-list P2P for the targets of one leaf.
-// Each source tile's partial sum is added to the running total with
-// Kahan compensation.
-template <typename T, int K, int NT>
+// Kernel sums at a target leaf for up to R density vectors at once (the
+// geometry and 1/r are shared): L2T from the downward equivalent surface,
+// W-list M2T from upward equivalent surfaces, U-list P2P with periodic images.
+// One thread per target; sources staged in shared memory NT at a time as
+// (x, y, z) and R x K densities; the image offset of a source box is added to
+// the target once.  Each staged tile is summed in registers and added to the
+// running total with Kahan compensation.
+template <typename T, int K, int NT, int R>
 __global__ void __launch_bounds__(NT) k_leaf(
     const int *__restrict__ leaves, const int4 *__restrict__ bpos, const int2 *__restrict__ srange,
     const int2 *__restrict__ trange, const int *__restrict__ uptr, const int *__restrict__ ubox,
     const unsigned char *__restrict__ ush, const int *__restrict__ wptr, const int *__restrict__ wbox,
     const unsigned char *__restrict__ wsh, const V4<T> *__restrict__ yrel, const V4<T> *__restrict__ xrel,
-    const T *__restrict__ dens, const T *__restrict__ up, const T *__restrict__ dn, int nrhs, int rhs,
+    const T *__restrict__ dens, const T *__restrict__ up, const T *__restrict__ dn, int nrhs, int rhs0,
     const T *__restrict__ g, int n, double *__restrict__ pot) {
-    __shared__ T sy[NT][3], sphi[NT][K];
+    __shared__ V4<T> sy[NT];
+    __shared__ T sphi[NT][R][K];
     const int b = leaves[blockIdx.x];
     const int4 B = bpos[b];
     const T h = (T)exp2i(B.w);
     const int2 tr = trange[b];
-    const int kn = n * K;
+    const int kn = n * K, nv = min(R, nrhs - rhs0);
+    // stage surface points of a box of half-width sc around the origin, densities from phi rows
+    auto stage_surface = [&](int j0, T sc, const T *phi) {
+        int j = j0 + threadIdx.x;
+        if (j < n) {
+            sy[threadIdx.x] = V4<T>{sc * g[3 * j], sc * g[3 * j + 1], sc * g[3 * j + 2], (T)0};
+#pragma unroll
+            for (int r = 0; r < R; r++)
+#pragma unroll
+                for (int a = 0; a < K; a++)
+                    sphi[threadIdx.x][r][a] = r < nv ? phi[(long long)r * kn + j * K + a] : (T)0;
+        }
+    };
     for (int t0 = tr.x; t0 < tr.y; t0 += NT) {
-        int t = t0 + threadIdx.x;
-        T x[3] = {0, 0, 0};
+        const int t = t0 + threadIdx.x;
+        T x0 = 0, x1 = 0, x2 = 0;
         if (t < tr.y) {
             V4<T> v = xrel[t];
-            x[0] = v.x;
-            x[1] = v.y;
-            x[2] = v.z;
+            x0 = v.x;
+            x1 = v.y;
+            x2 = v.z;
         }
-        T tot[K], cmp[K], acc[K];
-#pragma unroll
-        for (int a = 0; a < K; a++) tot[a] = cmp[a] = 0;
-        auto flush = [&]() {
-#pragma unroll
-            for (int a = 0; a < K; a++) {
-                T y = acc[a] - cmp[a], s = tot[a] + y;
-                cmp[a] = (s - tot[a]) - y;
-                tot[a] = s;
-                acc[a] = 0;
-            }
-        };
-#pragma unroll
-        for (int a = 0; a < K; a++) acc[a] = 0;
+        LeafAcc<T, K, R> L;
+        L.init();
         // L2T from the downward equivalent surface (edge 2.95 h)
         {
-            const T sc = (T)1.475 * h;
-            const T *phi = dn + ((long long)b * nrhs + rhs) * kn;
+            const T *phi = dn + ((long long)b * nrhs + rhs0) * kn;
             for (int j0 = 0; j0 < n; j0 += NT) {
                 __syncthreads();
-                int j = j0 + threadIdx.x;
-                if (j < n) {
-                    sy[threadIdx.x][0] = sc * g[3 * j];
-                    sy[threadIdx.x][1] = sc * g[3 * j + 1];
-                    sy[threadIdx.x][2] = sc * g[3 * j + 2];
-#pragma unroll
-                    for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = phi[j * K + a];
-                }
+                stage_surface(j0, (T)1.475 * h, phi);
                 __syncthreads();
-                int m = min(NT, n - j0);
-                for (int jj = 0; jj < m; jj++)
-                    Kern<T, K>::add(acc, x[0] - sy[jj][0], x[1] - sy[jj][1], x[2] - sy[jj][2], sphi[jj]);
-                flush();
+                const int m = min(NT, n - j0);
+                for (int jj = 0; jj < m; jj++) {
+                    const V4<T> y = sy[jj];
+                    L.add(x0 - y.x, x1 - y.y, x2 - y.z, sphi[jj]);
+                }
+                L.flush();
             }
         }
         // W list: upward equivalent surfaces (edge 1.05 h_A) of finer boxes
@@ -641,25 +850,18 @@ __global__ void __launch_bounds__(NT) k_leaf(
             int4 Ap = bpos[A];
             double off[3];
             centre_offset(B, Ap, sh, off);
-            const T o0 = (T)off[0], o1 = (T)off[1], o2 = (T)off[2];
-            const T sc = (T)(0.525 * exp2i(Ap.w));
-            const T *phi = up + ((long long)A * nrhs + rhs) * kn;
+            const T xo0 = x0 + (T)off[0], xo1 = x1 + (T)off[1], xo2 = x2 + (T)off[2];
+            const T *phi = up + ((long long)A * nrhs + rhs0) * kn;
             for (int j0 = 0; j0 < n; j0 += NT) {
                 __syncthreads();
-                int j = j0 + threadIdx.x;
-                if (j < n) {
-                    sy[threadIdx.x][0] = sc * g[3 * j];
-                    sy[threadIdx.x][1] = sc * g[3 * j + 1];
-                    sy[threadIdx.x][2] = sc * g[3 * j + 2];
-#pragma unroll
-                    for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = phi[j * K + a];
-                }
+                stage_surface(j0, (T)(0.525 * exp2i(Ap.w)), phi);
                 __syncthreads();
-                int m = min(NT, n - j0);
-                for (int jj = 0; jj < m; jj++)
-                    Kern<T, K>::add(acc, x[0] - sy[jj][0] + o0, x[1] - sy[jj][1] + o1, x[2] - sy[jj][2] + o2,
-                                    sphi[jj]);
-                flush();
+                const int m = min(NT, n - j0);
+                for (int jj = 0; jj < m; jj++) {
+                    const V4<T> y = sy[jj];
+                    L.add(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[jj]);
+                }
+                L.flush();
             }
         }
         // U list: direct sums, periodic images through the shift
@@ -668,29 +870,36 @@ __global__ void __launch_bounds__(NT) k_leaf(
             decode_shift(ush[e], sh);
             double off[3];
             centre_offset(B, bpos[A], sh, off);
-            const T o0 = (T)off[0], o1 = (T)off[1], o2 = (T)off[2];
-            int2 r = srange[A];
-            for (int s0 = r.x; s0 < r.y; s0 += NT) {
+            const T xo0 = x0 + (T)off[0], xo1 = x1 + (T)off[1], xo2 = x2 + (T)off[2];
+            const int2 rg = srange[A];
+            for (int s0 = rg.x; s0 < rg.y; s0 += NT) {
                 __syncthreads();
-                int s = s0 + threadIdx.x;
-                if (s < r.y) {
-                    V4<T> v = yrel[s];
-                    sy[threadIdx.x][0] = v.x;
-                    sy[threadIdx.x][1] = v.y;
-                    sy[threadIdx.x][2] = v.z;
+                const int sidx = s0 + threadIdx.x;
+                if (sidx < rg.y) {
+                    sy[threadIdx.x] = yrel[sidx];
 #pragma unroll
-                    for (int a = 0; a < K; a++) sphi[threadIdx.x][a] = dens[(long long)s * nrhs * K + rhs * K + a];
+                    for (int r = 0; r < R; r++)
+#pragma unroll
+                        for (int a = 0; a < K; a++)
+                            sphi[threadIdx.x][r][a] =
+                                r < nv ? dens[(long long)sidx * nrhs * K + (rhs0 + r) * K + a] : (T)0;
                 }
                 __syncthreads();
-                int m = min(NT, r.y - s0);
-                for (int j = 0; j < m; j++)
-                    Kern<T, K>::add(acc, x[0] - sy[j][0] + o0, x[1] - sy[j][1] + o1, x[2] - sy[j][2] + o2, sphi[j]);
-                flush();
+                const int m = min(NT, rg.y - s0);
+                for (int j = 0; j < m; j++) {
+                    const V4<T> y = sy[j];
+                    L.add(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
+                }
+                L.flush();
             }
         }
         if (t < tr.y) {
 #pragma unroll
-            for (int a = 0; a < K; a++) pot[(long long)t * nrhs * K + rhs * K + a] = (double)tot[a] - (double)cmp[a];
+            for (int r = 0; r < R; r++)
+                if (r < nv)
+#pragma unroll
+                    for (int a = 0; a < K; a++)
+                        pot[(long long)t * nrhs * K + (rhs0 + r) * K + a] = (double)L.tot[r][a] - (double)L.cmp[r][a];
         }
     }
 }
@@ -768,9 +977,17 @@ static void upward_t(Plan &P, cudaStream_t s) {
     const long long kn2 = (long long)kn * kn;
     auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
     if (P.n_leaves_src)
-        for (int r = 0; r < nr; r++)
-            count_launch(), k_s2m<T, K><<<P.n_leaves_src, KS_T, 0, s>>>(P.leaves_src.p, P.tree.bpos.p, P.tree.srange.p, yr, B::dens(P), nr,
-                                                         r, B::g(P).p, P.n, B::chk(P).p);
+        for (int r = 0; r < nr; r += 4) {  // up to 4 density vectors per pass
+            auto go = [&](auto rt) {
+                constexpr int R = decltype(rt)::value;
+                count_launch(), k_s2m<T, K, R><<<P.n_leaves_src, KS_T, 0, s>>>(
+                    P.leaves_src.p, P.tree.bpos.p, P.tree.srange.p, yr, B::dens(P), nr, r, B::g(P).p, P.n,
+                    B::chk(P).p);
+            };
+            if (nr - r == 1) go(std::integral_constant<int, 1>{});
+            else if (nr - r == 2) go(std::integral_constant<int, 2>{});
+            else go(std::integral_constant<int, 4>{});
+        }
     // UC2E: tmp = U^T q~u ; up = (V S+) tmp
     gemm<T>(P.t_uc2e, nullptr, 1, B::uc2e_b(P), 0, B::chk(P).p, B::tmp(P).p, kn, nr, 0, s);
     gemm<T>(P.t_uc2e, nullptr, 1, B::uc2e_a(P), 0, B::tmp(P).p, B::up(P).p, kn, nr, 0, s);
@@ -797,7 +1014,7 @@ __global__ void k_f2d(const T *__restrict__ a, double *__restrict__ b, long long
 // MIXED: the root far field (Algorithm 2 step c) and its check-to-equivalent
 // solve run in binary64 on a binary64 copy of the root's upward density.
 void root_mixed(Plan &P, cudaStream_t s) {
-    const int kn = P.kn, nr = P.nrhs;
+    const int kn = P.kn, nr = P.nrhs * P.nprob;  // the roots are boxes 0..nprob-1
     long long rows = (long long)nr * kn;
     P.chk64.reserve(rows);
     P.tmp64.reserve(rows);
@@ -816,9 +1033,10 @@ void root_mixed(Plan &P, cudaStream_t s) {
 
 void run_root(Plan &P, cudaStream_t s) {
     if (P.precision == PKIFMM_FP64) {
-        if (P.periodic) matvec64(P.root.p, P.up64.p, P.chk64.p, P.kn, P.nrhs, s);
-        else  // no far field; the row may hold the root leaf's upward check values
-            PK_CUDA(cudaMemsetAsync(P.chk64.p, 0, sizeof(double) * P.nrhs * P.kn, s));
+        const int nr = P.nrhs * P.nprob;  // the roots are boxes 0..nprob-1
+        if (P.periodic) matvec64(P.root.p, P.up64.p, P.chk64.p, P.kn, nr, s);
+        else  // no far field; the rows may hold root leaves' upward check values
+            PK_CUDA(cudaMemsetAsync(P.chk64.p, 0, sizeof(double) * nr * P.kn, s));
         return;
     }
     root_mixed(P, s);
@@ -841,10 +1059,17 @@ static void downward_t(Plan &P, cudaStream_t s) {
     const long long kn2 = (long long)kn * kn;
     auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
     if (P.n_xboxes)
-        for (int r = 0; r < nr; r++)
-            count_launch(), k_s2l<T, K><<<P.n_xboxes, KS_T, 0, s>>>(P.xboxes.p, P.tree.bpos.p, P.tree.srange.p, P.tree.x_ptr.p,
-                                                     P.tree.x_box.p, P.tree.x_sh.p, yr, B::dens(P), nr, r, B::g(P).p,
-                                                     P.n, B::chk(P).p);
+        for (int r = 0; r < nr; r += 4) {
+            auto go = [&](auto rt) {
+                constexpr int R = decltype(rt)::value;
+                count_launch(), k_s2l<T, K, R><<<P.n_xboxes, KS_T, 0, s>>>(
+                    P.xboxes.p, P.tree.bpos.p, P.tree.srange.p, P.tree.x_ptr.p, P.tree.x_box.p, P.tree.x_sh.p, yr,
+                    B::dens(P), nr, r, B::g(P).p, P.n, B::chk(P).p);
+            };
+            if (nr - r == 1) go(std::integral_constant<int, 1>{});
+            else if (nr - r == 2) go(std::integral_constant<int, 2>{});
+            else go(std::integral_constant<int, 4>{});
+        }
     gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_b(P), 0, B::chk(P).p, B::tmp(P).p, kn, nr, 0, s);
     gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_a(P), 0, B::tmp(P).p, B::dn(P).p, kn, nr, 0, s);
     for (size_t l = 1; l < P.t_l2l.size(); l++)
@@ -869,19 +1094,24 @@ static void leaves_t(Plan &P, cudaStream_t s) {
     auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
     auto *xr = reinterpret_cast<const V4<T> *>(B::xrel(P).p);
     // one block per target leaf; block size near the leaf size (most leaves
-    // hold about s/2 targets)
-    auto launch = [&](auto nt_tag, int r) {
-        constexpr int NT = decltype(nt_tag)::value;
-        count_launch(), k_leaf<T, K, NT><<<P.n_leaves_trg, NT, 0, s>>>(
+    // hold about s/2 targets); up to 4 density vectors per pass
+    auto launch = [&](auto nt_tag, auto r_tag, int r0) {
+        constexpr int NT = decltype(nt_tag)::value, R = decltype(r_tag)::value;
+        count_launch(), k_leaf<T, K, NT, R><<<P.n_leaves_trg, NT, 0, s>>>(
                 P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
                 P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
-                B::dn(P).p, nr, r, B::g(P).p, P.n, P.pot_s.p);
+                B::dn(P).p, nr, r0, B::g(P).p, P.n, P.pot_s.p);
+    };
+    auto launch_r = [&](auto nt_tag, int r0) {
+        if (nr - r0 == 1) launch(nt_tag, std::integral_constant<int, 1>{}, r0);
+        else if (nr - r0 == 2) launch(nt_tag, std::integral_constant<int, 2>{}, r0);
+        else launch(nt_tag, std::integral_constant<int, 4>{}, r0);
     };
     if (P.n_leaves_trg)
-        for (int r = 0; r < nr; r++) {
-            if (P.leaf_max <= 64) launch(std::integral_constant<int, 32>{}, r);
-            else if (P.leaf_max <= 128) launch(std::integral_constant<int, 64>{}, r);
-            else launch(std::integral_constant<int, 128>{}, r);
+        for (int r0 = 0; r0 < nr; r0 += 4) {
+            if (P.leaf_max <= 64) launch_r(std::integral_constant<int, 32>{}, r0);
+            else if (P.leaf_max <= 128) launch_r(std::integral_constant<int, 64>{}, r0);
+            else launch_r(std::integral_constant<int, 128>{}, r0);
         }
 }
 

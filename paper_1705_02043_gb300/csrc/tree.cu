@@ -10,6 +10,11 @@
 // B0 and its periodic images ("copy-and-paste", Sec. 2.2): list entries are
 // (box, shift) pairs, the shift in {-1,0,1}^3 naming the image.
 //
+// Several independent problems (a batch) share one forest: every point's key
+// carries its problem index above the 3*depth_max Morton bits, the problems'
+// roots are boxes 0..nprob-1 at level 0, and a box's key at level l is
+// prob * 8^l + (its Morton prefix), so lists never cross problems.
+//
 // Lists (standard KIFMM definitions; the paper defers to them):
 //   U(B), B leaf: leaves A with A+p adjacent to B, and B itself;
 //   V(B): children of colleagues of parent(B) not adjacent to B, stored as a
@@ -101,11 +106,23 @@ int exclusive_scan(const int *in, int *out, int n, cudaStream_t s) {
 // ---------------- keys ----------------
 
 // err[0]: NaN/inf coordinate, err[1]: point outside [0,1) along a free axis.
+// off[0..nprob] (nullable: one problem): CSR offsets of the problems' points.
 __global__ void k_keys(const double *__restrict__ xyz, long long n, double lo0, double lo1, double lo2,
                        double L, unsigned per, int D, double *__restrict__ xn,
-                       unsigned long long *__restrict__ key, int *__restrict__ idx, int *err) {
+                       unsigned long long *__restrict__ key, int *__restrict__ idx, int *err,
+                       const long long *__restrict__ off = nullptr, int nprob = 1) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    unsigned long long prob = 0;
+    if (off) {  // largest j with off[j] <= i
+        int lo = 0, hi = nprob - 1;
+        while (lo < hi) {
+            int m = (lo + hi + 1) >> 1;
+            if (off[m] <= i) lo = m;
+            else hi = m - 1;
+        }
+        prob = (unsigned long long)lo;
+    }
     double lo[3] = {lo0, lo1, lo2};
     int c[3];
     double sc = (double)(1 << D);
@@ -126,7 +143,7 @@ __global__ void k_keys(const double *__restrict__ xyz, long long n, double lo0, 
         int v = (int)floor(__dmul_rn(x, sc));
         c[a] = min(max(v, 0), (1 << D) - 1);
     }
-    key[i] = morton3(c[0], c[1], c[2]);
+    key[i] = prob << (3 * D) | morton3(c[0], c[1], c[2]);
     idx[i] = (int)i;
 }
 
@@ -242,12 +259,17 @@ __device__ inline int lower_bound_key(const unsigned long long *key, int lo, int
     return lo;
 }
 
-__global__ void k_root(unsigned long long *key, int4 *bpos, int *parent, int2 *sr, int2 *tr, int S, int T) {
-    key[0] = 0;
-    bpos[0] = make_int4(0, 0, 0, 0);
-    parent[0] = -1;
-    sr[0] = make_int2(0, S);
-    tr[0] = make_int2(0, T);
+// one root per problem; its points are the problem's CSR range (the sort
+// keeps problems contiguous and in order)
+__global__ void k_roots(int nprob, const long long *__restrict__ soff, const long long *__restrict__ toff,
+                        unsigned long long *key, int4 *bpos, int *parent, int2 *sr, int2 *tr) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nprob) return;
+    key[j] = (unsigned long long)j;
+    bpos[j] = make_int4(0, 0, 0, 0);
+    parent[j] = -1;
+    sr[j] = make_int2((int)soff[j], (int)soff[j + 1]);
+    tr[j] = make_int2((int)toff[j], (int)toff[j + 1]);
 }
 
 __global__ void k_split(int lb, int le, int level, int D, int smax, const unsigned long long *__restrict__ bkey,
@@ -299,15 +321,17 @@ __global__ void k_emit(int lb, int le, const int *__restrict__ cnt, const int *_
 void build_tree(Plan &P, cudaStream_t s) {
     Tree &t = P.tree;
     const int D = P.depth_max;
-    size_t cap = 1024;
+    const int np = P.nprob;
+    size_t cap = std::max<size_t>(1024, (size_t)np);
     t.key.grow_keep(cap, 0, s);
     t.bpos.grow_keep(cap, 0, s);
     t.parent.grow_keep(cap, 0, s);
     t.child.grow_keep(cap * 8, 0, s);
     t.srange.grow_keep(cap, 0, s);
     t.trange.grow_keep(cap, 0, s);
-    count_launch(), k_root<<<1, 1, 0, s>>>(t.key.p, t.bpos.p, t.parent.p, t.srange.p, t.trange.p, (int)P.S, (int)P.T);
-    t.lvl_begin.assign({0, 1});
+    count_launch(), k_roots<<<blocks(np, 128), 128, 0, s>>>(np, P.soff.p, P.toff.p, t.key.p, t.bpos.p, t.parent.p,
+                                                             t.srange.p, t.trange.p);
+    t.lvl_begin.assign({0, np});
     int level = 0;
     for (;; level++) {
         int lb = t.lvl_begin[level], le = t.lvl_begin[level + 1], nl = le - lb;
@@ -350,9 +374,9 @@ struct TreeView {
     unsigned per;
 };
 
-__device__ inline int lookup(const TreeView &tv, int level, const int w[3]) {
+__device__ inline int lookup(const TreeView &tv, int level, const int w[3], unsigned long long prob) {
     if (level >= tv.nlevel) return -1;
-    unsigned long long k = morton3(w[0], w[1], w[2]);
+    unsigned long long k = prob << (3 * level) | morton3(w[0], w[1], w[2]);
     int lo = tv.lvlb[level], hi = tv.lvlb[level + 1];
     int i = lower_bound_key(tv.key, lo, hi, k);
     return (i < hi && tv.key[i] == k) ? i : -1;
@@ -411,12 +435,12 @@ __device__ inline unsigned char code3(const int sh[3]) {
 }
 
 // first existing ancestor (level < l) of extended position e at level l
-__device__ int coarse_ancestor(const TreeView &tv, int l, const int e[3], int sh[3]) {
+__device__ int coarse_ancestor(const TreeView &tv, int l, const int e[3], int sh[3], unsigned long long prob) {
     for (int l2 = l - 1; l2 >= 0; l2--) {
         int e2[3], w2[3];
         for (int a = 0; a < 3; a++) e2[a] = e[a] >> (l - l2);  // arithmetic shift = floor division
         if (!wrap_pos(tv.per, l2, e2, w2, sh)) return -1;
-        int a = lookup(tv, l2, w2);
+        int a = lookup(tv, l2, w2, prob);
         if (a >= 0) return is_leaf(tv, a) ? a : -1;
     }
     return -1;
@@ -428,6 +452,7 @@ __global__ void k_lists(TreeView tv, int nbox, int pass, ListOut o) {
     int4 B = tv.bpos[b];
     int l = B.w;
     int pos[3] = {B.x, B.y, B.z};
+    const unsigned long long prob = tv.key[b] >> (3 * l);
     int nU = 0, nW = 0, nX = 0;
     int uo = pass ? o.u_ptr[b] : 0, wo = pass ? o.w_ptr[b] : 0, xo = pass ? o.x_ptr[b] : 0;
     unsigned long long pairs = 0;
@@ -440,7 +465,7 @@ __global__ void k_lists(TreeView tv, int nbox, int pass, ListOut o) {
             int e[3] = {pos[0] + d / 9 - 1, pos[1] + (d / 3) % 3 - 1, pos[2] + d % 3 - 1};
             int w[3], sh[3];
             if (!wrap_pos(tv.per, l, e, w, sh)) continue;
-            int nb = lookup(tv, l, w);
+            int nb = lookup(tv, l, w, prob);
             if (nb >= 0) {
                 if (is_leaf(tv, nb)) {
                     if (pass) {
@@ -485,7 +510,7 @@ __global__ void k_lists(TreeView tv, int nbox, int pass, ListOut o) {
                 }
             } else {
                 int sh2[3];
-                int a = coarse_ancestor(tv, l, e, sh2);
+                int a = coarse_ancestor(tv, l, e, sh2, prob);
                 if (a < 0) continue;
                 unsigned char cd = code3(sh2);
                 bool dup = false;
@@ -514,7 +539,7 @@ __global__ void k_lists(TreeView tv, int nbox, int pass, ListOut o) {
             int e[3] = {pp[0] + dd[0], pp[1] + dd[1], pp[2] + dd[2]};
             int w[3], sh[3];
             if (!wrap_pos(tv.per, l - 1, e, w, sh)) continue;
-            int a = lookup(tv, l - 1, w);
+            int a = lookup(tv, l - 1, w, prob);
             if (a >= 0 && !is_leaf(tv, a)) {
                 // V list: children of this colleague of the parent
                 if (pass) {
@@ -532,7 +557,7 @@ __global__ void k_lists(TreeView tv, int nbox, int pass, ListOut o) {
                 continue;
             }
             int sh2[3] = {sh[0], sh[1], sh[2]};
-            if (a < 0) a = coarse_ancestor(tv, l - 1, e, sh2);
+            if (a < 0) a = coarse_ancestor(tv, l - 1, e, sh2, prob);
             if (a < 0) continue;  // empty region
             if (adjacent(tv.bpos[a], sh2, B)) continue;
             unsigned char cd = code3(sh2);
@@ -620,6 +645,9 @@ void build_lists(Plan &P, cudaStream_t s) {
 void sort_points(Plan &P, const double *src, const double *dens, const double *trg, cudaStream_t s) {
     const int D = P.depth_max;
     long long S = P.S, T = P.T;
+    int pbits = 0;
+    while ((1LL << pbits) < P.nprob) pbits++;
+    const int key_bits = 3 * D + pbits;  // problem index above the Morton bits
     P.err.reserve(4);
     PK_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int) * 4, s));
     P.keyS.reserve(S + 1);
@@ -632,17 +660,24 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
     xn.reserve(3 * std::max(S, T) + 3);
     if (S) {
         count_launch(), k_keys<<<blocks(S, 256), 256, 0, s>>>(src, S, P.lo[0], P.lo[1], P.lo[2], P.L, P.periodic, D, xn.p,
-                                              P.keyS.p, P.idxS.p, P.err.p);
-        radix_sort(P.keyS, P.idxS, P.keyS2, P.idxS2, P.hist, (int)S, 3 * D, s);
+                                              P.keyS.p, P.idxS.p, P.err.p, P.nprob > 1 ? P.soff.p : nullptr,
+                                              P.nprob);
+        radix_sort(P.keyS, P.idxS, P.keyS2, P.idxS2, P.hist, (int)S, key_bits, s);
         count_launch(), k_gather3<<<blocks(S, 256), 256, 0, s>>>(xn.p, P.idxS.p, S, P.xs.p);
         int nk = P.nrhs * P.k;
         P.dens_s.reserve((size_t)S * nk);
         count_launch(), k_gather_dens<<<blocks(S * nk, 256), 256, 0, s>>>(dens, P.idxS.p, S, P.nrhs, P.k, P.dens_s.p);
     }
-    if (T) {
+    if (T && trg == src && T == S && P.same_offsets) {
+        // targets are the sources: same keys, order and coordinates
+        PK_CUDA(cudaMemcpyAsync(P.keyT.p, P.keyS.p, sizeof(unsigned long long) * T, cudaMemcpyDeviceToDevice, s));
+        PK_CUDA(cudaMemcpyAsync(P.idxT.p, P.idxS.p, sizeof(int) * T, cudaMemcpyDeviceToDevice, s));
+        PK_CUDA(cudaMemcpyAsync(P.xt.p, P.xs.p, sizeof(double) * 3 * T, cudaMemcpyDeviceToDevice, s));
+    } else if (T) {
         count_launch(), k_keys<<<blocks(T, 256), 256, 0, s>>>(trg, T, P.lo[0], P.lo[1], P.lo[2], P.L, P.periodic, D, xn.p,
-                                              P.keyT.p, P.idxT.p, P.err.p);
-        radix_sort(P.keyT, P.idxT, P.keyT2, P.idxT2, P.hist, (int)T, 3 * D, s);
+                                              P.keyT.p, P.idxT.p, P.err.p, P.nprob > 1 ? P.toff.p : nullptr,
+                                              P.nprob);
+        radix_sort(P.keyT, P.idxT, P.keyT2, P.idxT2, P.hist, (int)T, key_bits, s);
         count_launch(), k_gather3<<<blocks(T, 256), 256, 0, s>>>(xn.p, P.idxT.p, T, P.xt.p);
     }
     PK_CUDA(cudaStreamSynchronize(s));

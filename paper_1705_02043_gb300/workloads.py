@@ -31,6 +31,8 @@ def make_neutral(values: np.ndarray) -> np.ndarray:
     """
     v = np.array(values, dtype=np.float64, copy=True)
     squeeze = v.ndim == 1
+    if v.shape[0] == 0:
+        return v
     if squeeze:
         v = v[:, None]
     v = np.round(v * _Q) / _Q
@@ -154,3 +156,18 @@ def multi_problem_sizes(nprob: int = 256, seed: int = 0, lo: int = 1024, hi: int
     """Problem sizes log-uniform in [lo, hi] (rounded), one per problem."""
     rng = _rng(seed)
     return np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=nprob))).astype(np.int64)
+
+
+def multi_laplace_tp(nprob: int = 256, seed: int = 0, lo: int = 1024, hi: int = 65536, sizes=None):
+    """Independent Laplace problems, concatenated: sizes log-uniform in [lo, hi]
+    (or given), problem i uniform in the unit cube with neutral charges U[-1,1]
+    drawn with seed + i.  Returns points [S][3], charges [S], CSR offsets [nprob+1]."""
+    n = multi_problem_sizes(nprob, seed, lo, hi) if sizes is None else np.asarray(sizes, dtype=np.int64)
+    xs, qs = [], []
+    for i, m in enumerate(n):
+        x, q = laplace_uniform(int(m), seed=seed + i)
+        xs.append(x)
+        qs.append(q[0])
+    off = np.zeros(len(n) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(n)
+    return np.concatenate(xs) if xs else np.zeros((0, 3)), np.concatenate(qs) if qs else np.zeros(0), off

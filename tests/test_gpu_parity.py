@@ -156,7 +156,7 @@ def test_error_codes(cache):
         run(1, 7, y, np.ones((300, 3)), y, p=4, cache_dir=cache)
     assert e.value.name == "INVALID_ARG"
     with pytest.raises(pk.PKIFMMError) as e:
-        pk.PeriodicKIFMM(1, 3, p=6)
+        pk.PeriodicKIFMM(1, 6, p=6)  # doubly periodic in y and z is not built
     assert e.value.name == "UNSUPPORTED"
 
 

@@ -113,7 +113,48 @@ def test_root_operator_matches_oracle_sp():
         assert np.max(np.abs(M[:, j] - M[:, jj] - ref)) < 1e-12
 
 
-@pytest.mark.parametrize("kernel,periodic", [(0, 7), (1, 7), (0, 1)])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_root_operator_matches_oracle_dp(kernel):
+    """Doubly periodic (x, y): the library sums the in-plane Fourier modes in
+    closed form, the oracle by the trapezoid rule in k_z.  Compare neutral
+    combinations (column differences): the sheet term's constant cancels."""
+    p = 4
+    x = _surface(p)
+    M = pk.pkifmm_root_operator(kernel, 3, p, 2)
+    k = 1 if kernel == 0 else 3
+    for j, jj in ((0, 5), (3, 20), (11, len(x) - 1)):
+        for b in range(k):
+            f = np.zeros(3)
+            f[b] = 1.0
+            if kernel == 0:
+                ref = oracle.laplace_dp(x[[j, jj]], np.array([1.0, -1.0]), x)
+                ref = ref - (_near_sum(0, x, x[j], 1.0, 3) - _near_sum(0, x, x[jj], 1.0, 3))
+            else:
+                ref = oracle.stokes_dp(x[[j, jj]], np.stack([f, -f]), x)
+                ref = (ref - (_near_sum(1, x, x[j], f, 3) - _near_sum(1, x, x[jj], f, 3))).ravel()
+            got = M[:, k * j + b] - M[:, k * jj + b]
+            assert np.max(np.abs(got - ref)) < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_root_operator_matches_oracle_sp_stokes(axis):
+    """Singly periodic Stokes: neutral combinations (column differences),
+    library (explicit n <= 512 + Euler-Maclaurin) vs oracle."""
+    p = 4
+    x = _surface(p)
+    per = 1 << axis
+    M = pk.pkifmm_root_operator(1, per, p, 2)
+    for j, jj in ((0, 5), (3, 20), (11, len(x) - 1)):
+        for b in range(3):
+            f = np.zeros(3)
+            f[b] = 1.0
+            ref = oracle.stokes_sp(x[[j, jj]], np.stack([f, -f]), x, axis=axis)
+            ref = (ref - (_near_sum(1, x, x[j], f, per) - _near_sum(1, x, x[jj], f, per))).ravel()
+            got = M[:, 3 * j + b] - M[:, 3 * jj + b]
+            assert np.max(np.abs(got - ref)) < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("kernel,periodic", [(0, 7), (1, 7), (0, 1), (1, 2), (0, 3), (1, 3)])
 def test_root_operator_independent_of_ell(kernel, periodic):
     """Folding layers 2..ell back in makes the operator independent of ell
     (Sec. 3.5: the results do not depend on ell)."""
@@ -126,7 +167,7 @@ def test_root_operator_independent_of_ell(kernel, periodic):
 
 def test_unsupported_and_invalid_arguments():
     with pytest.raises(pk.PKIFMMError) as e:
-        pk.pkifmm_root_operator(1, 3, 4, 2)  # Stokes DP not built
+        pk.pkifmm_root_operator(1, 5, 4, 2)  # doubly periodic in x and z: not built
     assert e.value.name == "UNSUPPORTED"
     with pytest.raises(pk.PKIFMMError) as e:
         pk.pkifmm_root_operator(0, 7, 1, 2)
