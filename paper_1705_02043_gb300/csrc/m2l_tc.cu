@@ -46,7 +46,6 @@ constexpr int TC_SLACK = 16384;
 constexpr int TC_SMEM = TC_CTRL_BYTES + TC_STAGES * TC_STAGE_BYTES + TC_SLACK + 1024;
 constexpr int TC_THREADS = 288;                    // 4 producer warps, 1 MMA warp, 4 epilogue warps
 constexpr int TC_TMEM_COLS = 512;                  // 2 buffers x (hi*hi, cross terms) x 128 columns
-constexpr int TC_LAG = 5;                          // cp.async groups kept in flight
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 struct TcState {
@@ -70,6 +69,8 @@ struct TcState {
     size_t gtiles_cap = 0;
     int *gboxes = nullptr;
     size_t gboxes_cap = 0;
+    int *lmap = nullptr;                 // position -> box maps of the partial grid levels (-1: no box)
+    size_t lmap_cap = 0;
 };
 
 // ---------------- PTX helpers ----------------
@@ -200,8 +201,9 @@ struct TcArgs {
     float *chk;                            // [nbox*nrhs][kn]
     const float *amax;                     // max |phi|
     int kn, KP, nrhs, zero_row, kexp;
-    // grid mode (a level where every box exists): Phi as 8 parity sub-grids with a 2-box halo
+    // grid mode (a level dense enough for 8 parity sub-grids of Phi with a 2-box halo)
     int grid, lvl_begin, zd, bx, by, bz, rb;
+    const int *lmap;                       // Morton position -> box, -1 if absent; null: every box exists
     int *err;
 };
 
@@ -256,8 +258,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int x = b % a.bx, y = (b / a.bx) % a.by, z = b / (a.bx * a.by);
             const int px = (cls & 1) + 2 * (tile.y + x), py = (cls >> 1 & 1) + 2 * (tile.z + y),
                       pz = (cls >> 2 & 1) + 2 * (tile.w + z);
-            const int box = a.lvl_begin + (int)morton3_dev(px, py, pz);
-            drow[n] = (long long)box * a.nrhs + (tile.x >> 3) * a.rb + rl;
+            const int m = (int)morton3_dev(px, py, pz);
+            const int box = a.lmap ? a.lmap[m] : a.lvl_begin + m;
+            drow[n] = box >= 0 ? (long long)box * a.nrhs + (tile.x >> 3) * a.rb + rl : -1;
             sbox[n] = box;
         } else if (n < nr) {
             int row = row0 + n, tb = row / a.nrhs, rhs = row % a.nrhs, box = a.tboxes[tb];
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int s = tid; s < kVSlots; s += TC_THREADS) {
         int any = 0;
         if (a.class_ops[cls * kVSlots + s] >= 0) {
-            if (a.grid) any = 1;  // missing sources are zero halo rows
+            if (a.grid) any = 1;  // missing sources are zero rows of the grids
             else
                 for (int n = 0; n < nr && !any; n++) any = a.v_slot[(long long)sbox[n] * kVSlots + s] >= 0;
         }
@@ -326,12 +329,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp < 4) {
         // ---- producers: gather Phi rows (cp.async) and TMA the operator tiles ----
+        // Each thread's row copies arrive on the stage's full barrier when
+        // they land (cp.async.mbarrier.arrive.noinc), so all stages stay in
+        // flight; the MMA thread fences the async proxy before reading them.
         const int r = tid;
         const int rhs = (row0 + r) % a.nrhs, box = sbox[r];
         const int ri = r & 7;
-        int it = 0, cur_si = -1, op = 0;
-        long long srow = 0;
-        for (; it < total; it++) {
+        int cur_si = -1, op = 0;
+        long long srow = -1;  // -1: no source box in this slot (zeros)
+        for (int it = 0; it < total; it++) {
             const int st = it % TC_STAGES;
             const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
             if (!mbar_wait(&empty[st], ph ^ 1u, a.err)) break;
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int s = act[si];
                 op = a.class_ops[cls * kVSlots + s];
                 int src = box >= 0 ? a.v_slot[(long long)box * kVSlots + s] : -1;
-                srow = src >= 0 ? (long long)src * a.nrhs + rhs : (long long)a.zero_row;
+                srow = src >= 0 ? (long long)src * a.nrhs + rhs : -1;
             }
             uint8_t *sb = stages + (size_t)st * TC_STAGE_BYTES;
             if (tid == 0) {
@@ -350,23 +356,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KP + m0, &full[st]);
             }
             uint8_t *rowdst = sb + 2 * TC_A_BYTES + (r >> 3) * 512 + ri * 64;
+            if (srow >= 0) {
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const __half *g = (h ? a.phi_lo : a.phi_hi) + srow * a.KP + k0;
-                uint8_t *d = rowdst + h * TC_B_BYTES;
+                for (int h = 0; h < 2; h++) {
+                    const __half *g = (h ? a.phi_lo : a.phi_hi) + srow * a.KP + k0;
+                    uint8_t *d = rowdst + h * TC_B_BYTES;
 #pragma unroll
-                for (int c = 0; c < 4; c++) cp_async16(d + ((c ^ ((ri >> 1) & 3)) << 4), g + c * 8);
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            if (it >= TC_LAG) {
-                asm volatile("cp.async.wait_group 5;" ::: "memory");
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&full[(it - TC_LAG) % TC_STAGES]);
+                    for (int c = 0; c < 4; c++) cp_async16(d + ((c ^ ((ri >> 1) & 3)) << 4), g + c * 8);
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st]))
+                             : "memory");
+            } else {
+                // absent source: zeros written here, no global read (a shared
+                // zero row read by every CTA would serialise on one L2 line)
+#pragma unroll
+                for (int h = 0; h < 2; h++)
+#pragma unroll
+                    for (int c = 0; c < 4; c++)
+                        *reinterpret_cast<uint4 *>(rowdst + h * TC_B_BYTES + (c << 4)) = make_uint4(0, 0, 0, 0);
+                mbar_arrive(&full[st]);  // release: orders the zero stores before the MMA's acquire
             }
         }
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int j = (it > TC_LAG ? it - TC_LAG : 0); j < it; j++) mbar_arrive(&full[j % TC_STAGES]);
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == 4) {
         // ---- MMA issuer: one slot per work accumulator ----
         if (lane == 0) {
@@ -383,6 +394,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         okm = false;
                         break;
                     }
+                    // rows written by cp.async (generic proxy) are read by the MMA (async proxy)
+                    if (!a.grid) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     tc_fence_after();
                     const uint32_t sb = smem_u32(stages + (size_t)st * TC_STAGE_BYTES);
 #pragma unroll
@@ -495,12 +508,22 @@ __global__ void k_phi_split(const float *__restrict__ up, long long rows, int kn
     lo[i] = __float2half_rn(x - __half2float(h));
 }
 
-// Phi of one full level as 8 parity sub-grids with a 2-box halo:
+// map[Morton position] = box for the cnt boxes of one level (map preset to -1)
+__global__ void k_level_map(const int4 *__restrict__ bpos, int lb, int cnt, int *__restrict__ map) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    int4 p = bpos[lb + i];
+    map[morton3_dev(p.x, p.y, p.z)] = lb + i;
+}
+
+// Phi of one level as 8 parity sub-grids with a 2-box halo:
 // row (((par * Zd + z') * Yd + y') * Xd + x') * nrhs + rhs holds the box at
 // position 2 (x' - 2) + (par & 1), ... (wrapped on periodic axes, zero outside
-// on free axes), scaled and split like k_phi_split.
-__global__ void k_phi_grid(const float *__restrict__ up, int lvl_begin, int n, int nrhs, int kn, int KP, unsigned per,
-                           const float *amax, long long rows, __half *__restrict__ hi, __half *__restrict__ lo) {
+// on free axes and where the level has no box), scaled and split like k_phi_split.
+// lmap (nullable): Morton position -> box at this level, -1 where no box exists.
+__global__ void k_phi_grid(const float *__restrict__ up, int lvl_begin, const int *__restrict__ lmap, int n, int nrhs,
+                           int kn, int KP, unsigned per, const float *amax, long long rows, __half *__restrict__ hi,
+                           __half *__restrict__ lo) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= rows * KP) return;
     const long long row = i / KP;
@@ -522,8 +545,9 @@ __global__ void k_phi_grid(const float *__restrict__ up, int lvl_begin, int n, i
     }
     float x = 0.f;
     if (inside && k < kn) {
-        const int box = lvl_begin + (int)morton3_dev(pos[0], pos[1], pos[2]);
-        x = ldexpf(up[((long long)box * nrhs + rhs) * kn + k], phi_exp(amax));
+        const int m = (int)morton3_dev(pos[0], pos[1], pos[2]);
+        const int box = lmap ? lmap[m] : lvl_begin + m;
+        if (box >= 0) x = ldexpf(up[((long long)box * nrhs + rhs) * kn + k], phi_exp(amax));
     }
     __half h = __float2half_rn(x);
     hi[i] = h;
@@ -565,6 +589,7 @@ void m2l_tc_release(Plan &P) {
     cudaFree(t->grid);
     cudaFree(t->gtiles);
     cudaFree(t->gboxes);
+    cudaFree(t->lmap);
     cudaFree(t->err);
     cudaFreeHost(t->err_host);
     if (t->ev[0]) cudaEventDestroy(t->ev[0]);
@@ -643,8 +668,11 @@ namespace {
 struct GridPlan {
     int level, n, bx, by, bz, rb;
     long long rows;
-    size_t off;  // element offset of the hi grid in TcState::grid
+    size_t off;            // element offset of the hi grid in TcState::grid
+    long long map_off;     // offset of the level's position map in TcState::lmap, -1 if the level is full
 };
+
+constexpr size_t kGridBytesMax = 24ull << 30;  // device memory the parity grids may take
 
 template <typename T>
 void grow(T *&p, size_t &cap, size_t n) {
@@ -667,28 +695,47 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
     const int nlev = (int)lb.size() - 1;
     long long rows = (long long)P.tree.nbox * nr;
 
-    // levels where every box exists run with TMA-loaded operands (grid mode)
+    // levels holding at least a quarter of their 8^l boxes run with TMA-loaded
+    // operands (grid mode): the V-list source of a box at position p and slot
+    // offset o is the box at p + o if it exists, so parity grids with zero
+    // rows where no box exists reproduce the lists exactly
     std::vector<GridPlan> gp;
     std::vector<char> is_grid(nlev, 0);
     int rb = 0;
-    if (nr <= 128 && (nr & (nr - 1)) == 0) rb = nr;
-    size_t grid_elems = 0;
+    if (P.nprob == 1 && nr <= 128 && (nr & (nr - 1)) == 0) rb = nr;  // one tree: positions index one level
+    size_t grid_elems = 0, map_elems = 0;
     if (rb) {
         int e = 0;
         while ((1 << e) < 128 / rb) e++;
         const int ez = e / 3, ey = (e - ez) / 2, ex = e - ey - ez;
-        for (int l = 1; l < nlev; l++) {
+        for (int l = 1; l < nlev && l <= 9; l++) {
             long long cnt = lb[l + 1] - lb[l];
             const int n = 1 << l;
-            if (cnt != (1LL << (3 * l)) || (n / 2) < (1 << ex)) continue;
-            GridPlan g{l, n, 1 << ex, 1 << ey, 1 << ez, rb, 0, 0};
+            const long long full = 1LL << (3 * l);
+            if (cnt * 4 < full || (n / 2) < (1 << ex)) continue;
+            GridPlan g{l, n, 1 << ex, 1 << ey, 1 << ez, rb, 0, 0, -1};
             const long long d = n / 2 + 4;
             g.rows = 8 * d * d * d * nr;
+            if ((grid_elems + 2 * (size_t)g.rows * KP) * sizeof(__half) > kGridBytesMax) continue;
             g.off = grid_elems;
             grid_elems += 2 * (size_t)g.rows * KP;
+            if (cnt != full) {
+                g.map_off = (long long)map_elems;
+                map_elems += (size_t)full;
+            }
             gp.push_back(g);
             is_grid[l] = 1;
         }
+    }
+    if (map_elems) {
+        grow(t->lmap, t->lmap_cap, map_elems);
+        PK_CUDA(cudaMemsetAsync(t->lmap, 0xff, sizeof(int) * map_elems, s));
+        for (auto &g : gp)
+            if (g.map_off >= 0) {
+                const int cnt = lb[g.level + 1] - lb[g.level];
+                count_launch(), k_level_map<<<(cnt + 255) / 256, 256, 0, s>>>(P.tree.bpos.p, lb[g.level], cnt,
+                                                                              t->lmap + g.map_off);
+            }
     }
     PK_CUDA(cudaMemsetAsync(t->amax, 0, sizeof(float), s));
     count_launch(), k_amax<<<1024, 256, 0, s>>>(P.up32.p, rows * P.kn, t->amax);
@@ -708,16 +755,39 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         for (int r = 0; r < rows_c; r += TC_N)
             gtiles.push_back(make_int4(c, start * nr + r, std::min(TC_N, rows_c - r), 0));
     }
-    // grid tiles: (class | rblock << 3, i0, j0, k0) per level
+    // grid tiles: (class | rblock << 3, i0, j0, k0) per level; on partial
+    // levels only blocks holding a box with targets
     std::vector<int> gt_begin;
     for (auto &g : gp) {
         gt_begin.push_back((int)gtiles.size());
         const int h = g.n / 2;
+        std::vector<char> occ;  // [class][block] has a target box (partial levels)
+        const int bxn = h / g.bx, byn = h / g.by, bzn = h / g.bz;
+        if (g.map_off >= 0) {
+            const int cnt = lb[g.level + 1] - lb[g.level];
+            std::vector<int4> bp(cnt);
+            std::vector<int2> tr(cnt);
+            PK_CUDA(cudaMemcpyAsync(bp.data(), P.tree.bpos.p + lb[g.level], sizeof(int4) * cnt, cudaMemcpyDeviceToHost, s));
+            PK_CUDA(cudaMemcpyAsync(tr.data(), P.tree.trange.p + lb[g.level], sizeof(int2) * cnt, cudaMemcpyDeviceToHost, s));
+            PK_CUDA(cudaStreamSynchronize(s));
+            occ.assign((size_t)8 * bxn * byn * bzn, 0);
+            for (int i = 0; i < cnt; i++) {
+                if (tr[i].y <= tr[i].x) continue;
+                const int c = (bp[i].x & 1) | (bp[i].y & 1) << 1 | (bp[i].z & 1) << 2;
+                const int bi = (bp[i].x >> 1) / g.bx, bj = (bp[i].y >> 1) / g.by, bk = (bp[i].z >> 1) / g.bz;
+                occ[(((size_t)c * bzn + bk) * byn + bj) * bxn + bi] = 1;
+            }
+        }
         for (int c = 0; c < 8; c++)
             for (int r = 0; r < nr / g.rb; r++)
                 for (int k0 = 0; k0 < h; k0 += g.bz)
                     for (int j0 = 0; j0 < h; j0 += g.by)
-                        for (int i0 = 0; i0 < h; i0 += g.bx) gtiles.push_back(make_int4(c | r << 3, i0, j0, k0));
+                        for (int i0 = 0; i0 < h; i0 += g.bx) {
+                            if (!occ.empty() &&
+                                !occ[(((size_t)c * bzn + k0 / g.bz) * byn + j0 / g.by) * bxn + i0 / g.bx])
+                                continue;
+                            gtiles.push_back(make_int4(c | r << 3, i0, j0, k0));
+                        }
     }
     gt_begin.push_back((int)gtiles.size());
     grow(t->gtiles, t->gtiles_cap, gtiles.size() + 1);
@@ -761,7 +831,8 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
             __half *hi = t->grid + g.off, *lo = hi + (size_t)g.rows * KP;
             long long tot = g.rows * KP;
             count_launch(), k_phi_grid<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-                P.up32.p, lb[g.level], g.n, nr, P.kn, KP, P.periodic, t->amax, g.rows, hi, lo);
+                P.up32.p, lb[g.level], g.map_off >= 0 ? t->lmap + g.map_off : nullptr, g.n, nr, P.kn, KP,
+                P.periodic, t->amax, g.rows, hi, lo);
         }
     }
     PK_CUDA(cudaEventRecord(t->ev[0], s));
@@ -795,12 +866,14 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         a.grid = 1;
         a.tiles = t->gtiles + gt_begin[gi];
         a.lvl_begin = lb[g.level];
+        a.lmap = g.map_off >= 0 ? t->lmap + g.map_off : nullptr;
         a.zd = (int)d;
         a.bx = g.bx;
         a.by = g.by;
         a.bz = g.bz;
         a.rb = g.rb;
         const int ntl = gt_begin[gi + 1] - gt_begin[gi];
+        if (ntl == 0) continue;
         count_launch(), k_m2l_tc<<<ntl * mtiles, TC_THREADS, TC_SMEM, s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
         PK_CUDA(cudaGetLastError());
     }

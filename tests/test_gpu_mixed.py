@@ -92,3 +92,22 @@ def test_mixed_full_levels_tma_grid(nrhs, cache):
             d = rel_l2(um[r], u1)
             print(f"grid-mode nrhs={nrhs} column {r} vs single: {d:.3e}")
             assert d < 1e-6
+
+
+def test_mixed_partial_level_grid(cache):
+    """2^18 uniform points, leaf 64: level 5 holds about half of its 32,768
+    boxes, enough for parity grids with zero rows where no box exists (the
+    other V sources and targets are absent).  Same accuracy as the FP64 path."""
+    n = 1 << 18
+    x, f = w.stokes_uniform(n, seed=27)
+    um, plan = run(1, 7, x, f[0], x, p=8, leaf=64, precision=1, cache_dir=cache, return_plan=True)
+    st = plan.tree_stats()
+    plan.close()
+    assert st[2] == 5 and st[0] < 1 + 8 + 64 + 512 + 4096 + 32768  # level 5 is partial
+    ud = run(1, 7, x, f[0], x, p=8, leaf=64, precision=0, cache_dir=cache)
+    idx = _sample(n, 300)
+    ref = oracle.stokes_tp(x, f[0], x[idx])
+    em, ed = rel_l2(um[idx], ref), rel_l2(ud[idx], ref)
+    print(f"partial-level grid: mixed {em:.3e} fp64 {ed:.3e}")
+    assert em < 2e-5 and em < 1.5 * ed + 2e-6
+    assert rel_l2(um, ud) < 3e-5
