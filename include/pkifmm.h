@@ -139,6 +139,18 @@ int pkifmm_evaluate_batched(pkifmm_plan plan, int nprob, const int64_t *src_off,
                             const double *dens, const double *trg_xyz, double *pot,
                             void *cuda_stream);
 
+/* How the far field of the images beyond the near layers reaches the targets
+ * (Algorithm 2, Stage 2):
+ *   PKIFMM_FAR_L2L     (default) the root's downward equivalent density is
+ *                      passed down the tree by L2L with the rest (the L2L
+ *                      option of Sec. 4);
+ *   PKIFMM_FAR_DIRECT  step d: it is evaluated directly at every target,
+ *                      q_F = K(x_t, y^{B0,d}) phi^{B0,d}, in binary64, O(T p^2).
+ * Both give the same potentials up to the method's error.  Applies to later
+ * evaluations; INVALID_ARG for other modes.  No effect in free space. */
+enum { PKIFMM_FAR_L2L = 0, PKIFMM_FAR_DIRECT = 1 };
+int pkifmm_plan_set_far_field(pkifmm_plan plan, int mode);
+
 /* Leaf-size autotuner (the paper fixes s by hand, Sec. 3.6; no counterpart).
  * For each candidate leaf size s (candidates[0..ncand-1], each >= 1) the
  * plan evaluates the given batch (arguments as pkifmm_evaluate_batched) once

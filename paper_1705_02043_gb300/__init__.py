@@ -8,6 +8,7 @@ if it is missing.
 
 LAPLACE, STOKES = 0, 1
 FP64, MIXED = 0, 1
+FAR_L2L, FAR_DIRECT = 0, 1
 
 
 def __getattr__(name):

@@ -44,6 +44,7 @@ def load_library():
             lib.pkifmm_evaluate_host.argtypes = [P, i64, P, P, i64, P, P, P]
             lib.pkifmm_evaluate_batched.argtypes = [P, i, P, P, P, P, P, P, P]
             lib.pkifmm_autotune_leaf.argtypes = [P, i, P, P, P, P, P, P, P, i, i, P, P, P]
+            lib.pkifmm_plan_set_far_field.argtypes = [P, i]
             lib.pkifmm_last_stage_times.argtypes = [P, P, i]
             lib.pkifmm_tree_stats.argtypes = [P, P, i]
             lib.pkifmm_tree_export.argtypes = [P, P, P, P, P, P, P, P]
@@ -122,6 +123,10 @@ def pkifmm_autotune_leaf(plan, nprob, src_off, trg_off, src, dens, trg, pot, can
                                                _ptr(pot), _ptr(cand), len(cand), reps, _ptr(best), _ptr(ms),
                                                stream))
     return int(best[0]), ms
+
+
+def pkifmm_plan_set_far_field(plan, mode):
+    return _check(load_library().pkifmm_plan_set_far_field(plan, mode))
 
 
 def pkifmm_last_stage_times(plan):
@@ -269,6 +274,10 @@ class PeriodicKIFMM:
         pkifmm_evaluate_host(self.handle, src.shape[0], src, dens, trg.shape[0], trg, pot,
                              ctypes.c_void_p(stream) if stream else None)
         return pot
+
+    def set_far_field(self, mode):
+        """FAR_L2L (default) or FAR_DIRECT (Algorithm 2 step d)."""
+        pkifmm_plan_set_far_field(self.handle, mode)
 
     def stage_times(self):
         return pkifmm_last_stage_times(self.handle)

@@ -411,6 +411,12 @@ int pkifmm_autotune_leaf(pkifmm_plan plan, int nprob, const int64_t *src_off, co
     });
 }
 
+int pkifmm_plan_set_far_field(pkifmm_plan plan, int mode) {
+    if (!plan || (mode != PKIFMM_FAR_L2L && mode != PKIFMM_FAR_DIRECT)) return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
+    plan->P.far_direct = mode == PKIFMM_FAR_DIRECT;
+    return PKIFMM_OK;
+}
+
 int pkifmm_tree_stats(pkifmm_plan plan, int64_t *out, int max) {
     if (!plan || !out || max < 0) return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
     Tree &t = plan->P.tree;

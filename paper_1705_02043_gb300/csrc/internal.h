@@ -120,6 +120,8 @@ struct Plan {
     // evaluation workspace
     int64_t S = 0, T = 0;
     int nprob = 1;                              // independent problems in this evaluation
+    int far_direct = 0;                         // 1: far field by Algorithm 2 step d instead of L2L
+    DBuf<double> far64;                         // roots' downward equivalent densities (step d)
     DBuf<long long> soff, toff;                 // [nprob+1] CSR offsets of their points
     bool same_offsets = true;                   // soff == toff element by element
     DBuf<unsigned long long> keyS, keyT, keyS2, keyT2;

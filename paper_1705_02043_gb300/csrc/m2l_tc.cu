@@ -521,13 +521,12 @@ __global__ void k_level_map(const int4 *__restrict__ bpos, int lb, int cnt, int 
 // position 2 (x' - 2) + (par & 1), ... (wrapped on periodic axes, zero outside
 // on free axes and where the level has no box), scaled and split like k_phi_split.
 // lmap (nullable): Morton position -> box at this level, -1 where no box exists.
+// One block per grid row; the row's position is decoded once.
 __global__ void k_phi_grid(const float *__restrict__ up, int lvl_begin, const int *__restrict__ lmap, int n, int nrhs,
                            int kn, int KP, unsigned per, const float *amax, long long rows, __half *__restrict__ hi,
                            __half *__restrict__ lo) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= rows * KP) return;
-    const long long row = i / KP;
-    const int k = (int)(i % KP);
+    const long long row = blockIdx.x;
+    if (row >= rows) return;
     const int d = n / 2 + 4;
     long long rest = row / nrhs;
     const int rhs = (int)(row % nrhs);
@@ -543,15 +542,19 @@ __global__ void k_phi_grid(const float *__restrict__ up, int lvl_begin, const in
         if (per >> a & 1) pos[a] = ((pos[a] % n) + n) % n;
         else if (pos[a] < 0 || pos[a] >= n) inside = false;
     }
-    float x = 0.f;
-    if (inside && k < kn) {
+    int box = -1;
+    if (inside) {
         const int m = (int)morton3_dev(pos[0], pos[1], pos[2]);
-        const int box = lmap ? lmap[m] : lvl_begin + m;
-        if (box >= 0) x = ldexpf(up[((long long)box * nrhs + rhs) * kn + k], phi_exp(amax));
+        box = lmap ? lmap[m] : lvl_begin + m;
     }
-    __half h = __float2half_rn(x);
-    hi[i] = h;
-    lo[i] = __float2half_rn(x - __half2float(h));
+    const float *src = box >= 0 ? up + ((long long)box * nrhs + rhs) * kn : nullptr;
+    const int e = phi_exp(amax);
+    for (int k = threadIdx.x; k < KP; k += blockDim.x) {
+        const float x = (src && k < kn) ? ldexpf(src[k], e) : 0.f;
+        const __half h = __float2half_rn(x);
+        hi[row * KP + k] = h;
+        lo[row * KP + k] = __float2half_rn(x - __half2float(h));
+    }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -829,8 +832,7 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         grow(t->grid, t->grid_cap, grid_elems);
         for (auto &g : gp) {
             __half *hi = t->grid + g.off, *lo = hi + (size_t)g.rows * KP;
-            long long tot = g.rows * KP;
-            count_launch(), k_phi_grid<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+            count_launch(), k_phi_grid<<<(unsigned)g.rows, 128, 0, s>>>(
                 P.up32.p, lb[g.level], g.map_off >= 0 ? t->lmap + g.map_off : nullptr, g.n, nr, P.kn, KP,
                 P.periodic, t->amax, g.rows, hi, lo);
         }

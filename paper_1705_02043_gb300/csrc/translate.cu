@@ -564,7 +564,7 @@ static void gemm(const Task &t, const int *slot_table, int slot_stride, const T 
     using Small = GemmSmall<T>;
     const int bm = std::is_same<T, float>::value ? Big::BM : GB_M;  // rows per task tile (make_task)
     const long long big_blocks = (long long)t.ntiles * ((kn + Big::BN - 1) / Big::BN) * ((bm + Big::BM - 1) / Big::BM);
-    if (big_blocks < 2 * 152) {
+    if (big_blocks < 152 / 2) {  // fewer large tiles than half the SMs
         dim3 g(t.ntiles, (kn + Small::BN - 1) / Small::BN, (bm + Small::BM - 1) / Small::BM);
         count_launch(), k_slot_gemm<Small><<<g, 256, 0, s>>>(t.boxes.p, t.tiles.p, slot_table, slot_stride, t.nslots,
                                                               t.class_ops.p, ops, op_stride, src, dst, kn, nrhs, beta);
@@ -790,35 +790,47 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
 // (x, y, z) and R x K densities; the image offset of a source box is added to
 // the target once.  Each staged tile is summed in registers and added to the
 // running total with Kahan compensation.
-template <typename T, int K, int NT, int R>
-__global__ void __launch_bounds__(NT) k_leaf(
+template <typename T, int K, int NT, int R, int LPB>
+__global__ void __launch_bounds__(NT * LPB) k_leaf(
     const int *__restrict__ leaves, const int4 *__restrict__ bpos, const int2 *__restrict__ srange,
     const int2 *__restrict__ trange, const int *__restrict__ uptr, const int *__restrict__ ubox,
     const unsigned char *__restrict__ ush, const int *__restrict__ wptr, const int *__restrict__ wbox,
     const unsigned char *__restrict__ wsh, const V4<T> *__restrict__ yrel, const V4<T> *__restrict__ xrel,
     const T *__restrict__ dens, const T *__restrict__ up, const T *__restrict__ dn, int nrhs, int rhs0,
-    const T *__restrict__ g, int n, double *__restrict__ pot) {
-    __shared__ V4<T> sy[NT];
-    __shared__ T sphi[NT][R][K];
-    const int b = leaves[blockIdx.x];
+    const T *__restrict__ g, int n, int nleaves, double *__restrict__ pot) {
+    // LPB > 1 (NT = 32): one warp per leaf, each with its own staging tiles
+    static_assert(LPB == 1 || NT == 32, "leaves per block need warp-sized tiles");
+    __shared__ V4<T> sy_all[LPB][NT];
+    __shared__ T sphi_all[LPB][NT][R][K];
+    const int wl = LPB > 1 ? (int)(threadIdx.x >> 5) : 0;
+    const int li = blockIdx.x * LPB + wl;
+    if (li >= nleaves) return;  // whole warps (LPB > 1) or the whole block (LPB = 1)
+    const unsigned tid = LPB > 1 ? (threadIdx.x & 31) : threadIdx.x;
+    V4<T> *sy = sy_all[wl];
+    T(*sphi)[R][K] = sphi_all[wl];
+    auto sync = [] {
+        if constexpr (LPB > 1) __syncwarp();
+        else __syncthreads();
+    };
+    const int b = leaves[li];
     const int4 B = bpos[b];
     const T h = (T)exp2i(B.w);
     const int2 tr = trange[b];
     const int kn = n * K, nv = min(R, nrhs - rhs0);
     // stage surface points of a box of half-width sc around the origin, densities from phi rows
     auto stage_surface = [&](int j0, T sc, const T *phi) {
-        int j = j0 + threadIdx.x;
+        int j = j0 + tid;
         if (j < n) {
-            sy[threadIdx.x] = V4<T>{sc * g[3 * j], sc * g[3 * j + 1], sc * g[3 * j + 2], (T)0};
+            sy[tid] = V4<T>{sc * g[3 * j], sc * g[3 * j + 1], sc * g[3 * j + 2], (T)0};
 #pragma unroll
             for (int r = 0; r < R; r++)
 #pragma unroll
                 for (int a = 0; a < K; a++)
-                    sphi[threadIdx.x][r][a] = r < nv ? phi[(long long)r * kn + j * K + a] : (T)0;
+                    sphi[tid][r][a] = r < nv ? phi[(long long)r * kn + j * K + a] : (T)0;
         }
     };
     for (int t0 = tr.x; t0 < tr.y; t0 += NT) {
-        const int t = t0 + threadIdx.x;
+        const int t = t0 + tid;
         T x0 = 0, x1 = 0, x2 = 0;
         if (t < tr.y) {
             V4<T> v = xrel[t];
@@ -832,9 +844,9 @@ __global__ void __launch_bounds__(NT) k_leaf(
         {
             const T *phi = dn + ((long long)b * nrhs + rhs0) * kn;
             for (int j0 = 0; j0 < n; j0 += NT) {
-                __syncthreads();
+                sync();
                 stage_surface(j0, (T)1.475 * h, phi);
-                __syncthreads();
+                sync();
                 const int m = min(NT, n - j0);
                 for (int jj = 0; jj < m; jj++) {
                     const V4<T> y = sy[jj];
@@ -853,9 +865,9 @@ __global__ void __launch_bounds__(NT) k_leaf(
             const T xo0 = x0 + (T)off[0], xo1 = x1 + (T)off[1], xo2 = x2 + (T)off[2];
             const T *phi = up + ((long long)A * nrhs + rhs0) * kn;
             for (int j0 = 0; j0 < n; j0 += NT) {
-                __syncthreads();
+                sync();
                 stage_surface(j0, (T)(0.525 * exp2i(Ap.w)), phi);
-                __syncthreads();
+                sync();
                 const int m = min(NT, n - j0);
                 for (int jj = 0; jj < m; jj++) {
                     const V4<T> y = sy[jj];
@@ -873,18 +885,18 @@ __global__ void __launch_bounds__(NT) k_leaf(
             const T xo0 = x0 + (T)off[0], xo1 = x1 + (T)off[1], xo2 = x2 + (T)off[2];
             const int2 rg = srange[A];
             for (int s0 = rg.x; s0 < rg.y; s0 += NT) {
-                __syncthreads();
-                const int sidx = s0 + threadIdx.x;
+                sync();
+                const int sidx = s0 + tid;
                 if (sidx < rg.y) {
-                    sy[threadIdx.x] = yrel[sidx];
+                    sy[tid] = yrel[sidx];
 #pragma unroll
                     for (int r = 0; r < R; r++)
 #pragma unroll
                         for (int a = 0; a < K; a++)
-                            sphi[threadIdx.x][r][a] =
+                            sphi[tid][r][a] =
                                 r < nv ? dens[(long long)sidx * nrhs * K + (rhs0 + r) * K + a] : (T)0;
                 }
-                __syncthreads();
+                sync();
                 const int m = min(NT, rg.y - s0);
                 for (int j = 0; j < m; j++) {
                     const V4<T> y = sy[j];
@@ -1072,6 +1084,14 @@ static void downward_t(Plan &P, cudaStream_t s) {
         }
     gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_b(P), 0, B::chk(P).p, B::tmp(P).p, kn, nr, 0, s);
     gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_a(P), 0, B::tmp(P).p, B::dn(P).p, kn, nr, 0, s);
+    if (P.far_direct && P.periodic) {
+        // step d: keep the roots' downward equivalent densities (binary64) for the
+        // direct evaluation at the targets and do not pass them down
+        const long long rows = (long long)P.nprob * nr * kn;
+        P.far64.reserve(rows);
+        PK_CUDA(cudaMemcpyAsync(P.far64.p, P.dn64.p, sizeof(double) * rows, cudaMemcpyDeviceToDevice, s));
+        PK_CUDA(cudaMemsetAsync(B::dn(P).p, 0, sizeof(T) * rows, s));
+    }
     for (size_t l = 1; l < P.t_l2l.size(); l++)
         gemm<T>(P.t_l2l[l], P.tree.parent.p, 1, B::l2l(P), kn2, B::dn(P).p, B::dn(P).p, kn, nr, 1, s);
 }
@@ -1097,10 +1117,11 @@ static void leaves_t(Plan &P, cudaStream_t s) {
     // hold about s/2 targets); up to 4 density vectors per pass
     auto launch = [&](auto nt_tag, auto r_tag, int r0) {
         constexpr int NT = decltype(nt_tag)::value, R = decltype(r_tag)::value;
-        count_launch(), k_leaf<T, K, NT, R><<<P.n_leaves_trg, NT, 0, s>>>(
+        constexpr int LPB = NT == 32 ? 4 : 1;  // small leaves: one warp each, four per block
+        count_launch(), k_leaf<T, K, NT, R, LPB><<<(P.n_leaves_trg + LPB - 1) / LPB, NT * LPB, 0, s>>>(
                 P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
                 P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
-                B::dn(P).p, nr, r0, B::g(P).p, P.n, P.pot_s.p);
+                B::dn(P).p, nr, r0, B::g(P).p, P.n, P.n_leaves_trg, P.pot_s.p);
     };
     auto launch_r = [&](auto nt_tag, int r0) {
         if (nr - r0 == 1) launch(nt_tag, std::integral_constant<int, 1>{}, r0);
@@ -1115,6 +1136,30 @@ static void leaves_t(Plan &P, cudaStream_t s) {
         }
 }
 
+// Algorithm 2 step d: q_t += K(x_t, y^{B0,d}) phi^{B0,d}, the far field of
+// all images beyond the near layers evaluated directly from the root's
+// downward equivalent density (surface of half-width 1.475 around the
+// centre of the unit box), in binary64.  Problem of target t: its key prefix.
+template <int K>
+__global__ void k_far_direct(const double *__restrict__ xt, long long T, const unsigned long long *__restrict__ keyT,
+                             int key_shift, const double *__restrict__ far, const double *__restrict__ g, int n,
+                             int nrhs, double *__restrict__ pot_s) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const long long j = (long long)(keyT[t] >> key_shift);
+    const double x0 = xt[3 * t] - 0.5, x1 = xt[3 * t + 1] - 0.5, x2 = xt[3 * t + 2] - 0.5;
+    const int kn = n * K;
+    for (int r = 0; r < nrhs; r++) {
+        const double *phi = far + (j * nrhs + r) * kn;
+        double acc[K];
+        for (int a = 0; a < K; a++) acc[a] = 0.0;
+        for (int i = 0; i < n; i++)
+            Kern<double, K>::add(acc, x0 - 1.475 * g[3 * i], x1 - 1.475 * g[3 * i + 1], x2 - 1.475 * g[3 * i + 2],
+                                 phi + i * K);
+        for (int a = 0; a < K; a++) pot_s[(t * nrhs + r) * K + a] += acc[a];
+    }
+}
+
 void run_leaves(Plan &P, cudaStream_t s) {
     if (P.precision == PKIFMM_FP64) {
         if (P.k == 1) leaves_t<double, 1>(P, s);
@@ -1122,6 +1167,16 @@ void run_leaves(Plan &P, cudaStream_t s) {
     } else {
         if (P.k == 1) leaves_t<float, 1>(P, s);
         else leaves_t<float, 3>(P, s);
+    }
+    if (P.far_direct && P.periodic && P.T > 0) {
+        const int shift = P.nprob > 1 ? 3 * P.depth_max : 63;  // one problem: index 0
+        const unsigned nb = (unsigned)((P.T + 127) / 128);
+        if (P.k == 1)
+            count_launch(), k_far_direct<1><<<nb, 128, 0, s>>>(P.xt.p, P.T, P.keyT.p, shift, P.far64.p, P.g64.p, P.n,
+                                                                P.nrhs, P.pot_s.p);
+        else
+            count_launch(), k_far_direct<3><<<nb, 128, 0, s>>>(P.xt.p, P.T, P.keyT.p, shift, P.far64.p, P.g64.p, P.n,
+                                                                P.nrhs, P.pot_s.p);
     }
 }
 

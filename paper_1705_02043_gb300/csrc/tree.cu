@@ -272,28 +272,32 @@ __global__ void k_roots(int nprob, const long long *__restrict__ soff, const lon
     tr[j] = make_int2((int)toff[j], (int)toff[j + 1]);
 }
 
+// One warp per box: lanes 0-7 find where child c's sources start, lanes
+// 8-15 where its targets start (all 16 binary searches at once); child c ends
+// where child c + 1 starts, the last child at the box's end.
 __global__ void k_split(int lb, int le, int level, int D, int smax, const unsigned long long *__restrict__ bkey,
                         const int2 *__restrict__ srange, const int2 *__restrict__ trange,
                         const unsigned long long *__restrict__ keyS, const unsigned long long *__restrict__ keyT,
                         int2 *csr, int2 *ctr, int *cnt) {
-    int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= le) return;
-    int2 sr = srange[b], tr = trange[b];
-    int count = 0;
-    if ((sr.y - sr.x > smax || tr.y - tr.x > smax) && level < D) {
-        int sh = 3 * (D - level - 1);
-        unsigned long long pk = bkey[b];
-        for (int c = 0; c < 8; c++) {
-            unsigned long long ck = pk * 8 + c;
-            unsigned long long lo = ck << sh, hi = (ck + 1) << sh;
-            int s0 = lower_bound_key(keyS, sr.x, sr.y, lo), s1 = lower_bound_key(keyS, s0, sr.y, hi);
-            int t0 = lower_bound_key(keyT, tr.x, tr.y, lo), t1 = lower_bound_key(keyT, t0, tr.y, hi);
-            csr[(b - lb) * 8 + c] = make_int2(s0, s1);
-            ctr[(b - lb) * 8 + c] = make_int2(t0, t1);
-            if (s1 > s0 || t1 > t0) count++;
-        }
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int b = lb + (int)(gt >> 5), lane = threadIdx.x & 31;
+    if (b >= le) return;  // the whole warp shares b
+    const int2 sr = srange[b], tr = trange[b];
+    const bool split = (sr.y - sr.x > smax || tr.y - tr.x > smax) && level < D;
+    const int c = lane & 7;
+    int start = 0;
+    if (split && lane < 16) {
+        const unsigned long long lo = (bkey[b] * 8 + c) << (3 * (D - level - 1));
+        start = lane < 8 ? lower_bound_key(keyS, sr.x, sr.y, lo) : lower_bound_key(keyT, tr.x, tr.y, lo);
     }
-    cnt[b - lb] = count;
+    const int nxt = __shfl_down_sync(0xffffffffu, start, 1);
+    const int end = c == 7 ? (lane < 8 ? sr.y : tr.y) : nxt;
+    if (split && lane < 8) csr[(b - lb) * 8 + c] = make_int2(start, end);
+    if (split && lane >= 8 && lane < 16) ctr[(b - lb) * 8 + c] = make_int2(start, end);
+    const int nonempty = lane < 16 && end > start;
+    const int t_nonempty = __shfl_down_sync(0xffffffffu, nonempty, 8);  // lane c: child c's targets
+    const unsigned m = __ballot_sync(0xffffffffu, split && lane < 8 && (nonempty || t_nonempty));
+    if (lane == 0) cnt[b - lb] = __popc(m);
 }
 
 __global__ void k_emit(int lb, int le, const int *__restrict__ cnt, const int *__restrict__ off,
@@ -339,8 +343,9 @@ void build_tree(Plan &P, cudaStream_t s) {
         P.ctr.reserve((size_t)nl * 8);
         P.cnt.reserve(nl + 1);
         P.off.reserve(nl + 1);
-        count_launch(), k_split<<<blocks(nl, 128), 128, 0, s>>>(lb, le, level, D, P.leaf_max, t.key.p, t.srange.p, t.trange.p,
-                                                 P.keyS.p, P.keyT.p, P.csr.p, P.ctr.p, P.cnt.p);
+        count_launch(), k_split<<<blocks((long long)nl * 32, 128), 128, 0, s>>>(
+            lb, le, level, D, P.leaf_max, t.key.p, t.srange.p, t.trange.p, P.keyS.p, P.keyT.p, P.csr.p, P.ctr.p,
+            P.cnt.p);
         int total = exclusive_scan(P.cnt.p, P.off.p, nl, s);
         size_t need = (size_t)le + total;
         t.key.grow_keep(need, le, s);
@@ -582,9 +587,20 @@ __global__ void k_lists(TreeView tv, int nbox, int pass, ListOut o) {
     }
 }
 
+// count of V-slot entries: per-thread counts over a grid-stride loop, one atomic per block
 __global__ void k_count_v(const int *__restrict__ v_slot, long long n, unsigned long long *cnt) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n && v_slot[i] >= 0) atomicAdd(cnt, 1ULL);
+    __shared__ unsigned long long part[32];
+    unsigned long long c = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        c += v_slot[i] >= 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+        if (t) atomicAdd(cnt, t);
+    }
 }
 
 void build_lists(Plan &P, cudaStream_t s) {
@@ -629,8 +645,8 @@ void build_lists(Plan &P, cudaStream_t s) {
     o.v_slot = t.v_slot.p;
     o.pairs = pairs.p;
     count_launch(), k_lists<<<blocks(nb, 128), 128, 0, s>>>(tv, nb, 1, o);
-    count_launch(), k_count_v<<<blocks((long long)nb * kVSlots, 256), 256, 0, s>>>(t.v_slot.p, (long long)nb * kVSlots,
-                                                                     pairs.p + 1);
+    count_launch(), k_count_v<<<std::min<unsigned>(1024, blocks((long long)nb * kVSlots, 256)), 256, 0, s>>>(
+        t.v_slot.p, (long long)nb * kVSlots, pairs.p + 1);
     unsigned long long h[2];
     PK_CUDA(cudaMemcpyAsync(h, pairs.p, sizeof h, cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaStreamSynchronize(s));

@@ -172,3 +172,33 @@ def test_empty_inputs(cache):
     out = plan.evaluate(trg, torch.ones((1, 5, 3), dtype=torch.float64, device=dev), src)
     assert out.shape == (1, 0, 3)
     plan.close()
+
+
+@pytest.mark.parametrize("kernel,periodic,precision", [(1, 7, 0), (0, 7, 1), (1, 3, 0), (0, 1, 0)])
+def test_far_field_step_d_matches_l2l(kernel, periodic, precision, cache):
+    """Algorithm 2 step d (direct evaluation of the root's downward
+    equivalent density at the targets) and the L2L fold give the same
+    potentials up to the method's error, and both match the oracle."""
+    import torch
+    n = 3000
+    if kernel == 0:
+        x, q = w.laplace_uniform(n, seed=16)
+        d = q[0]
+    else:
+        x, f = w.stokes_uniform(n, seed=16)
+        d = f[0]
+    a = run(kernel, periodic, x, d, x, p=8, leaf=40, precision=precision, cache_dir=cache)
+    plan = pk.PeriodicKIFMM(kernel, periodic, p=8, leaf_max=40, precision=precision, cache_dir=cache)
+    plan.set_far_field(pk.FAR_DIRECT)
+    dev = torch.device("cuda:0")
+    k = 1 if kernel == 0 else 3
+    tx = torch.tensor(x, device=dev)
+    b = plan.evaluate(tx, torch.tensor(np.asarray(d).reshape(1, n, k), device=dev), tx).cpu().numpy()[0]
+    plan.close()
+    b = b[:, 0] if kernel == 0 else b
+    ref = oracle.periodic_sum(kernel, periodic, x, d, x)
+    tol = 2e-5 if precision else 1e-6
+    assert rel_l2(b, a) < tol
+    assert rel_l2(b, ref) < 3 * max(rel_l2(a, ref), 1e-7)
+    with pytest.raises(pk.PKIFMMError):
+        pk.pkifmm_plan_set_far_field(plan.handle if plan.handle else None, 7)
