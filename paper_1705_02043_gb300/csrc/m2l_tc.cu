@@ -16,7 +16,7 @@
 // nearest, into fp32 registers of the epilogue warps, while the next slot
 // accumulates in the other buffer.  Within a slot the large hi*hi products
 // and the 2^-11 smaller cross products go to separate accumulators, so the
-// large one takes only 2 KP/32 steps per slot.
+// large one takes only 2 KK/32 steps per slot.
 //
 // Pipeline (6 stages of 32 KB): warps 0-3 gather the Phi rows with 16-byte
 // cp.async into the 64B-swizzled K-major layout and one thread issues the TMA
@@ -49,11 +49,11 @@ constexpr int TC_TMEM_COLS = 512;                  // 2 buffers x (hi*hi, cross 
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 struct TcState {
-    int KP = 0;
-    __half *kop = nullptr;               // [2][316][KP][KP]  (hi, lo), scaled by 2^kexp
+    int KM = 0, KK = 0;                  // operator rows padded to 128 (M tiles), columns to 32 (K chunks)
+    __half *kop = nullptr;               // [2][316][KM][KK]  (hi, lo), scaled by 2^kexp
     int kexp = 0;
     float *amax = nullptr;               // max |phi| of the current evaluation
-    __half *phi = nullptr;        // [2][rows+1][KP]
+    __half *phi = nullptr;        // [2][rows+1][KK]
     size_t phi_rows = 0;
     CUtensorMap tmap[2];
     int4 *tiles = nullptr;
@@ -192,7 +192,7 @@ __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 // ---------------- kernel ----------------
 
 struct TcArgs {
-    const __half *phi_hi, *phi_lo;  // gather mode: [rows+1][KP], last row zero
+    const __half *phi_hi, *phi_lo;  // gather mode: [rows+1][KK], last row zero
     const int *tboxes;                     // gather mode: task boxes, class-major
     const int4 *tiles;                     // gather: (class, row0, nrows, 0); grid: (class | rblock << 3, i0, j0, k0)
     const int *v_slot;                     // [nbox][189]
@@ -200,7 +200,7 @@ struct TcArgs {
     const int *slot_off;                   // [8][189][3] box offsets of the V slots
     float *chk;                            // [nbox*nrhs][kn]
     const float *amax;                     // max |phi|
-    int kn, KP, nrhs, zero_row, kexp;
+    int kn, KM, KK, nrhs, zero_row, kexp;
     // grid mode (a level dense enough for 8 parity sub-grids of Phi with a 2-box halo)
     int grid, lvl_begin, zd, bx, by, bz, rb;
     const int *lmap;                       // Morton position -> box, -1 if absent; null: every box exists
@@ -227,12 +227,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // consecutive CTAs: the M tiles of one column tile (they share the
     // gathered rows), then the next column tile of the same octant class
     // (same operator stream), so one class fills a wave
-    const int mtiles = a.KP / TC_M;
+    const int mtiles = a.KM / TC_M;
     const int4 tile = a.tiles[blockIdx.x / mtiles];
     const int cls = a.grid ? (tile.x & 7) : tile.x;
     const int row0 = a.grid ? 0 : tile.y, nr = a.grid ? TC_N : tile.z;
     const int m0 = (blockIdx.x % mtiles) * TC_M;
-    const int kchunks = a.KP / TC_K;
+    const int kchunks = a.KK / TC_K;
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; s++) {
@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 uint8_t *sb = stages + (size_t)st * TC_STAGE_BYTES;
                 mbar_expect_tx(&full[st], (uint32_t)(2 * TC_A_BYTES + 2 * TC_B_BYTES));
-                tma_load_2d(sb, &tA_hi, k0, op * a.KP + m0, &full[st]);
-                tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KP + m0, &full[st]);
+                tma_load_2d(sb, &tA_hi, k0, op * a.KM + m0, &full[st]);
+                tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KM + m0, &full[st]);
                 const int r0 = (tile.x >> 3) * a.rb;
                 tma_load_5d(sb + 2 * TC_A_BYTES, &tB_hi, k0, r0, cx, cy, cz, &full[st]);
                 tma_load_5d(sb + 2 * TC_A_BYTES + TC_B_BYTES, &tB_lo, k0, r0, cx, cy, cz, &full[st]);
@@ -352,14 +352,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint8_t *sb = stages + (size_t)st * TC_STAGE_BYTES;
             if (tid == 0) {
                 mbar_expect_tx(&full[st], (uint32_t)(2 * TC_A_BYTES));
-                tma_load_2d(sb, &tA_hi, k0, op * a.KP + m0, &full[st]);
-                tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KP + m0, &full[st]);
+                tma_load_2d(sb, &tA_hi, k0, op * a.KM + m0, &full[st]);
+                tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KM + m0, &full[st]);
             }
             uint8_t *rowdst = sb + 2 * TC_A_BYTES + (r >> 3) * 512 + ri * 64;
             if (srow >= 0) {
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    const __half *g = (h ? a.phi_lo : a.phi_hi) + srow * a.KP + k0;
+                    const __half *g = (h ? a.phi_lo : a.phi_hi) + srow * a.KK + k0;
                     uint8_t *d = rowdst + h * TC_B_BYTES;
 #pragma unroll
                     for (int c = 0; c < 4; c++) cp_async16(d + ((c ^ ((ri >> 1) & 3)) << 4), g + c * 8);
@@ -461,15 +461,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 // ---------------- set-up and launch ----------------
 
-// K_o * 2^kexp split into fp16 hi/lo, padded to KP x KP: out[h][op][i][j]
-__global__ void k_kop_split(int kernel, int n, int KP, int kexp, const double *__restrict__ g,
+// K_o * 2^kexp split into fp16 hi/lo, padded to KM x KK: out[h][op][i][j]
+__global__ void k_kop_split(int kernel, int n, int KM, int KK, int kexp, const double *__restrict__ g,
                             const int *__restrict__ offs, __half *__restrict__ out) {
     const int kk = kernel == 0 ? 1 : 3, kn = n * kk;
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long total = (long long)kM2LOps * KP * KP;
+    long long total = (long long)kM2LOps * KM * KK;
     if (i >= total) return;
-    int m = (int)(i / ((long long)KP * KP));
-    int rem = (int)(i % ((long long)KP * KP)), r = rem / KP, c = rem % KP;
+    int m = (int)(i / ((long long)KM * KK));
+    int rem = (int)(i % ((long long)KM * KK)), r = rem / KK, c = rem % KK;
     double v = 0.0;
     if (r < kn && c < kn) {
         int pa = r / kk, ca = r % kk, pb = c / kk, cb = c % kk;
@@ -494,7 +494,7 @@ __global__ void k_amax(const float *__restrict__ x, long long n, float *amax) {
     if ((threadIdx.x & 31) == 0) atomicMax((int *)amax, __float_as_int(m));  // non-negative floats order as ints
 }
 
-// upward densities (fp32 rows of kn) * 2^e -> fp16 hi/lo rows of KP, plus one zero row
+// upward densities (fp32 rows of kn) * 2^e -> fp16 hi/lo rows of KP (= KK), plus one zero row
 __global__ void k_phi_split(const float *__restrict__ up, long long rows, int kn, int KP, const float *amax,
                             __half *__restrict__ hi, __half *__restrict__ lo) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -605,12 +605,13 @@ void m2l_tc_prepare(Plan &P) {
     if (!tc_supported()) throw Error(PKIFMM_ERR_UNSUPPORTED, "MIXED path needs an sm_103 GPU (tcgen05)");
     TcState *t = new TcState;
     P.tc = t;
-    t->KP = (P.kn + TC_M - 1) / TC_M * TC_M;
+    t->KM = (P.kn + TC_M - 1) / TC_M * TC_M;
+    t->KK = (P.kn + TC_K - 1) / TC_K * TC_K;
     // |K_o| <= 1/0.95 (Laplace) or 2/(8 pi 0.95) (Stokes) over the 316 offsets
     // (closest points 0.95 box edges apart): scale the largest entry to about 2^12
     t->kexp = P.kernel == 0 ? 12 : 15;
-    const int KP = t->KP;
-    size_t nk = (size_t)kM2LOps * KP * KP;
+    const int KM = t->KM, KK = t->KK;
+    size_t nk = (size_t)kM2LOps * KM * KK;
     PK_CUDA(cudaMalloc(&t->kop, 2 * nk * sizeof(__half)));
     std::vector<int> offs;
     for (int x = -3; x <= 3; x++)
@@ -624,15 +625,15 @@ void m2l_tc_prepare(Plan &P) {
     int *doffs = nullptr;
     PK_CUDA(cudaMalloc(&doffs, sizeof(int) * offs.size()));
     PK_CUDA(cudaMemcpy(doffs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice));
-    count_launch(), k_kop_split<<<(unsigned)((nk + 255) / 256), 256>>>(P.kernel, P.n, KP, t->kexp, P.g64.p, doffs,
+    count_launch(), k_kop_split<<<(unsigned)((nk + 255) / 256), 256>>>(P.kernel, P.n, KM, KK, t->kexp, P.g64.p, doffs,
                                                                         t->kop);
     PK_CUDA(cudaGetLastError());
     PK_CUDA(cudaDeviceSynchronize());
     cudaFree(doffs);
     EncodeTiledFn enc = encode_fn();
     for (int h = 0; h < 2; h++) {
-        cuuint64_t dims[2] = {(cuuint64_t)KP, (cuuint64_t)kM2LOps * KP};
-        cuuint64_t strides[1] = {(cuuint64_t)KP * 2};
+        cuuint64_t dims[2] = {(cuuint64_t)KK, (cuuint64_t)kM2LOps * KM};
+        cuuint64_t strides[1] = {(cuuint64_t)KK * 2};
         cuuint32_t box[2] = {TC_K, TC_M};
         cuuint32_t estr[2] = {1, 1};
         CUresult r = enc(&t->tmap[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, t->kop + h * nk, dims, strides, box, estr,
@@ -693,15 +694,17 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
     if (!t) return false;
     const Task &task = P.t_m2l;
     if (task.nrows == 0) return true;
-    const int KP = t->KP, nr = P.nrhs, mtiles = KP / TC_M;
+    const int KK = t->KK, nr = P.nrhs, mtiles = t->KM / TC_M;
     const std::vector<int> &lb = P.tree.lvl_begin;
     const int nlev = (int)lb.size() - 1;
     long long rows = (long long)P.tree.nbox * nr;
 
-    // levels holding at least a quarter of their 8^l boxes run with TMA-loaded
+    // levels holding at least 70% of their 8^l boxes run with TMA-loaded
     // operands (grid mode): the V-list source of a box at position p and slot
     // offset o is the box at p + o if it exists, so parity grids with zero
-    // rows where no box exists reproduce the lists exactly
+    // rows where no box exists reproduce the lists exactly.  Below that the
+    // gather path, about 1.5x slower per tile, wins (measured: a level 48% full
+    // took 32.7 ms in grid mode, 22.8 ms gathered).
     std::vector<GridPlan> gp;
     std::vector<char> is_grid(nlev, 0);
     int rb = 0;
@@ -715,13 +718,13 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
             long long cnt = lb[l + 1] - lb[l];
             const int n = 1 << l;
             const long long full = 1LL << (3 * l);
-            if (cnt * 4 < full || (n / 2) < (1 << ex)) continue;
+            if (cnt * 10 < full * 7 || (n / 2) < (1 << ex)) continue;
             GridPlan g{l, n, 1 << ex, 1 << ey, 1 << ez, rb, 0, 0, -1};
             const long long d = n / 2 + 4;
             g.rows = 8 * d * d * d * nr;
-            if ((grid_elems + 2 * (size_t)g.rows * KP) * sizeof(__half) > kGridBytesMax) continue;
+            if ((grid_elems + 2 * (size_t)g.rows * KK) * sizeof(__half) > kGridBytesMax) continue;
             g.off = grid_elems;
-            grid_elems += 2 * (size_t)g.rows * KP;
+            grid_elems += 2 * (size_t)g.rows * KK;
             if (cnt != full) {
                 g.map_off = (long long)map_elems;
                 map_elems += (size_t)full;
@@ -808,7 +811,8 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
     a.chk = P.chk32.p;
     a.amax = t->amax;
     a.kn = P.kn;
-    a.KP = KP;
+    a.KM = t->KM;
+    a.KK = KK;
     a.nrhs = nr;
     a.zero_row = (int)rows;
     a.kexp = t->kexp;
@@ -821,26 +825,26 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
             cudaFree(t->phi);
             t->phi = nullptr;
             t->phi_rows = (size_t)(rows + 1) + (size_t)(rows + 1) / 4;
-            PK_CUDA(cudaMalloc(&t->phi, 2 * t->phi_rows * KP * sizeof(__half)));
+            PK_CUDA(cudaMalloc(&t->phi, 2 * t->phi_rows * KK * sizeof(__half)));
         }
-        long long tot = (rows + 1) * KP;
+        long long tot = (rows + 1) * KK;
         count_launch(), k_phi_split<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-            P.up32.p, rows, P.kn, KP, t->amax, t->phi, t->phi + t->phi_rows * KP);
+            P.up32.p, rows, P.kn, KK, t->amax, t->phi, t->phi + t->phi_rows * KK);
     }
     // parity grids for grid mode
     if (!gp.empty()) {
         grow(t->grid, t->grid_cap, grid_elems);
         for (auto &g : gp) {
-            __half *hi = t->grid + g.off, *lo = hi + (size_t)g.rows * KP;
+            __half *hi = t->grid + g.off, *lo = hi + (size_t)g.rows * KK;
             count_launch(), k_phi_grid<<<(unsigned)g.rows, 128, 0, s>>>(
-                P.up32.p, lb[g.level], g.map_off >= 0 ? t->lmap + g.map_off : nullptr, g.n, nr, P.kn, KP,
+                P.up32.p, lb[g.level], g.map_off >= 0 ? t->lmap + g.map_off : nullptr, g.n, nr, P.kn, KK,
                 P.periodic, t->amax, g.rows, hi, lo);
         }
     }
     PK_CUDA(cudaEventRecord(t->ev[0], s));
     if (ngather_tiles > 0) {
         a.phi_hi = t->phi;
-        a.phi_lo = t->phi + t->phi_rows * KP;
+        a.phi_lo = t->phi + t->phi_rows * KK;
         a.tboxes = t->gboxes;
         a.tiles = t->gtiles;
         a.grid = 0;
@@ -854,9 +858,9 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         const cuuint64_t d = (cuuint64_t)(g.n / 2 + 4);
         CUtensorMap mb[2];
         for (int h = 0; h < 2; h++) {
-            __half *base = t->grid + g.off + (size_t)h * g.rows * KP;
-            cuuint64_t dims[5] = {(cuuint64_t)KP, (cuuint64_t)nr, d, d, 8 * d};
-            cuuint64_t row = (cuuint64_t)KP * 2;
+            __half *base = t->grid + g.off + (size_t)h * g.rows * KK;
+            cuuint64_t dims[5] = {(cuuint64_t)KK, (cuuint64_t)nr, d, d, 8 * d};
+            cuuint64_t row = (cuuint64_t)KK * 2;
             cuuint64_t strides[4] = {row, row * nr, row * nr * d, row * nr * d * d};
             cuuint32_t box[5] = {TC_K, (cuuint32_t)g.rb, (cuuint32_t)g.bx, (cuuint32_t)g.by, (cuuint32_t)g.bz};
             cuuint32_t estr[5] = {1, 1, 1, 1, 1};

@@ -588,6 +588,10 @@ static void gemm(const Task &t, const int *slot_table, int slot_stride, const T 
 template <typename T>
 struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };  // one 16-byte (binary32) access
 
+// 1/sqrt(r2) for r2 > 0 known (no coincidence test)
+__device__ __forceinline__ float rsqrt_nz(float r2) { return rsqrtf(r2); }
+__device__ __forceinline__ double rsqrt_nz(double r2) { return 1.0 / sqrt(r2); }
+
 __device__ __forceinline__ double exp2i(int l) { return ldexp(1.0, -l); }
 
 // leaf-relative coordinates: rel[i] = x[i] - centre(leaf)
@@ -618,7 +622,10 @@ constexpr int KS_T = 128;  // threads of the kernel-sum blocks
 
 template <typename T, int K, int R>
 struct LeafAcc {
+    // Sums without the kernel's constant factor (1 for Laplace, 1/8pi for
+    // Stokes), applied once to each result (scale()).
     T acc[R][K], tot[R][K], cmp[R][K];
+    static constexpr double kScale = K == 1 ? 1.0 : 0.039788735772973836;  // 1/(8 pi)
     __device__ void init() {
 #pragma unroll
         for (int r = 0; r < R; r++)
@@ -636,27 +643,31 @@ struct LeafAcc {
                 acc[r][a] = 0;
             }
     }
-    // one source at offset d = x - y with densities f[r][a]
+    // one source at offset d = x - y with densities f[r][a]; SELF: the source
+    // may coincide with the target (then it contributes nothing)
+    template <bool SELF>
     __device__ __forceinline__ void add(T dx, T dy, T dz, const T (*f)[K]) {
-        const T ir = inv_sqrt(dx * dx + dy * dy + dz * dz);
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        T ir;
+        if constexpr (SELF) ir = inv_sqrt(r2);
+        else ir = rsqrt_nz(r2);
         if constexpr (K == 1) {
 #pragma unroll
             for (int r = 0; r < R; r++) acc[r][0] += ir * f[r][0];
         } else {
-            const T cir = (T)0.039788735772973836 * ir;  // 1/(8 pi r)
-            const T c3 = cir * ir * ir;
+            // (I/r + d d^T/r^3) f = (f + d (f.d)/r^2) / r
+            const T ir2 = ir * ir;
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                const T fr = (f[r][0] * dx + f[r][1] * dy + f[r][2] * dz) * c3;
-                acc[r][0] += f[r][0] * cir + dx * fr;
-                acc[r][1] += f[r][1] * cir + dy * fr;
-                acc[r][2] += f[r][2] * cir + dz * fr;
+                const T t = (f[r][0] * dx + f[r][1] * dy + f[r][2] * dz) * ir2;
+                acc[r][0] += ir * (f[r][0] + dx * t);
+                acc[r][1] += ir * (f[r][1] + dy * t);
+                acc[r][2] += ir * (f[r][2] + dz * t);
             }
         }
     }
 };
 
-// S2M: q~u[B][rhs][i] = h sum_{s in B} K(1.475 h g_i - yrel_s) phi_s
 template <typename T, int K, int R>
 __global__ void __launch_bounds__(KS_T) k_s2m(const int *__restrict__ leaves, const int4 *__restrict__ bpos,
                                               const int2 *__restrict__ srange, const V4<T> *__restrict__ yrel,
@@ -694,7 +705,7 @@ __global__ void __launch_bounds__(KS_T) k_s2m(const int *__restrict__ leaves, co
             int m = min(KS_T, r.y - s0);
             for (int j = 0; j < m; j++) {
                 const V4<T> y = sy[j];
-                L.add(x0 - y.x, x1 - y.y, x2 - y.z, sphi[j]);
+                L.template add<false>(x0 - y.x, x1 - y.y, x2 - y.z, sphi[j]);
             }
         }
         if (i < n) {
@@ -703,7 +714,7 @@ __global__ void __launch_bounds__(KS_T) k_s2m(const int *__restrict__ leaves, co
                 if (q < nv)
 #pragma unroll
                     for (int a = 0; a < K; a++)
-                        chk[((long long)b * nrhs + rhs0 + q) * kn + i * K + a] = h * L.acc[q][a];
+                        chk[((long long)b * nrhs + rhs0 + q) * kn + i * K + a] = h * (T)LeafAcc<T, K, R>::kScale * L.acc[q][a];
         }
     }
 }
@@ -768,7 +779,7 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
                 int m = min(KS_T, r.y - s0);
                 for (int j = 0; j < m; j++) {
                     const V4<T> y = sy[j];
-                    L.add(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
+                    L.template add<false>(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
                 }
             }
         }
@@ -778,7 +789,7 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
                 if (q < nv)
 #pragma unroll
                     for (int a = 0; a < K; a++)
-                        chk[((long long)b * nrhs + rhs0 + q) * kn + i * K + a] += h * L.acc[q][a];
+                        chk[((long long)b * nrhs + rhs0 + q) * kn + i * K + a] += h * (T)LeafAcc<T, K, R>::kScale * L.acc[q][a];
         }
     }
 }
@@ -850,7 +861,7 @@ __global__ void __launch_bounds__(NT * LPB) k_leaf(
                 const int m = min(NT, n - j0);
                 for (int jj = 0; jj < m; jj++) {
                     const V4<T> y = sy[jj];
-                    L.add(x0 - y.x, x1 - y.y, x2 - y.z, sphi[jj]);
+                    L.template add<false>(x0 - y.x, x1 - y.y, x2 - y.z, sphi[jj]);
                 }
                 L.flush();
             }
@@ -871,7 +882,7 @@ __global__ void __launch_bounds__(NT * LPB) k_leaf(
                 const int m = min(NT, n - j0);
                 for (int jj = 0; jj < m; jj++) {
                     const V4<T> y = sy[jj];
-                    L.add(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[jj]);
+                    L.template add<false>(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[jj]);
                 }
                 L.flush();
             }
@@ -900,7 +911,7 @@ __global__ void __launch_bounds__(NT * LPB) k_leaf(
                 const int m = min(NT, rg.y - s0);
                 for (int j = 0; j < m; j++) {
                     const V4<T> y = sy[j];
-                    L.add(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
+                    L.template add<true>(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
                 }
                 L.flush();
             }
@@ -911,7 +922,7 @@ __global__ void __launch_bounds__(NT * LPB) k_leaf(
                 if (r < nv)
 #pragma unroll
                     for (int a = 0; a < K; a++)
-                        pot[(long long)t * nrhs * K + (rhs0 + r) * K + a] = (double)L.tot[r][a] - (double)L.cmp[r][a];
+                        pot[(long long)t * nrhs * K + (rhs0 + r) * K + a] = ((double)L.tot[r][a] - (double)L.cmp[r][a]) * LeafAcc<T, K, R>::kScale;
         }
     }
 }
@@ -1117,7 +1128,9 @@ static void leaves_t(Plan &P, cudaStream_t s) {
     // hold about s/2 targets); up to 4 density vectors per pass
     auto launch = [&](auto nt_tag, auto r_tag, int r0) {
         constexpr int NT = decltype(nt_tag)::value, R = decltype(r_tag)::value;
-        constexpr int LPB = NT == 32 ? 4 : 1;  // small leaves: one warp each, four per block
+        // one leaf per block: with several leaves per block (one warp each) a
+        // block holds its slot until its slowest leaf is done (measured slower)
+        constexpr int LPB = 1;
         count_launch(), k_leaf<T, K, NT, R, LPB><<<(P.n_leaves_trg + LPB - 1) / LPB, NT * LPB, 0, s>>>(
                 P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
                 P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
