@@ -646,6 +646,11 @@ void pkifmm_plan_destroy(pkifmm_plan plan) {
     P.slot_of.release();
     P.csr.release();
     P.ctr.release();
+    P.soff.release();
+    P.toff.release();
+    P.far64.release();
+    if (P.stage_h) cudaFreeHost(P.stage_h);
+    if (P.stage_ev) cudaEventDestroy(P.stage_ev);
     Task *ts[] = {&P.t_uc2e, &P.t_m2l, &P.t_dc2e, &P.t_root};
     for (auto *t : ts) {
         t->boxes.release();

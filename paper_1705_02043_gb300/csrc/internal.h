@@ -115,12 +115,17 @@ struct Plan {
     DBuf<double> uc2e_a, uc2e_b, dc2e_a, dc2e_b, m2m, l2l, m2l, root;
     DBuf<float> uc2e_a32, uc2e_b32, dc2e_a32, dc2e_b32, m2m32, l2l32, m2l32;
     DBuf<int> class_slot_op;                    // [8][189] M2L op index per class slot
+    std::vector<int> h_class_slot_op;           // host copy
     DBuf<short> slot_of;                        // [8][343] slot of offset o, -1 if none
 
     // evaluation workspace
     int64_t S = 0, T = 0;
     int nprob = 1;                              // independent problems in this evaluation
     int far_direct = 0;                         // 1: far field by Algorithm 2 step d instead of L2L
+    char *stage_h = nullptr;                    // pinned staging for per-evaluation task uploads
+    size_t stage_cap = 0;
+    cudaEvent_t stage_ev = nullptr;
+    bool stage_ev_live = false;
     DBuf<double> far64;                         // roots' downward equivalent densities (step d)
     DBuf<long long> soff, toff;                 // [nprob+1] CSR offsets of their points
     bool same_offsets = true;                   // soff == toff element by element

@@ -28,6 +28,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -37,13 +38,13 @@ namespace pk {
 constexpr int TC_N = 128;                          // (box, rhs) columns per CTA
 constexpr int TC_M = 128;                          // kn rows per CTA
 constexpr int TC_K = 32;                           // K chunk: 64 bytes of fp16 per row
-constexpr int TC_STAGES = 6;
+constexpr int TC_STAGES = 6;                        // pipeline depth (the default instantiation)
 constexpr int TC_A_BYTES = TC_M * TC_K * 2;        // 8 KB per split
 constexpr int TC_B_BYTES = TC_N * TC_K * 2;        // 8 KB per split
 constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 32 KB
 constexpr int TC_CTRL_BYTES = 4096;
 constexpr int TC_SLACK = 16384;
-constexpr int TC_SMEM = TC_CTRL_BYTES + TC_STAGES * TC_STAGE_BYTES + TC_SLACK + 1024;
+constexpr int tc_smem(int stages) { return TC_CTRL_BYTES + stages * TC_STAGE_BYTES + TC_SLACK + 1024; }
 constexpr int TC_THREADS = 288;                    // 4 producer warps, 1 MMA warp, 4 epilogue warps
 constexpr int TC_TMEM_COLS = 512;                  // 2 buffers x (hi*hi, cross terms) x 128 columns
 constexpr long long TC_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
@@ -71,6 +72,7 @@ struct TcState {
     size_t gboxes_cap = 0;
     int *lmap = nullptr;                 // position -> box maps of the partial grid levels (-1: no box)
     size_t lmap_cap = 0;
+    int stages = 6;                      // pipeline depth of the launched instantiation
 };
 
 // ---------------- PTX helpers ----------------
@@ -154,8 +156,10 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
            | ((uint64_t)4 << 61);              // layout: 64-byte swizzle
 }
 
-// kind::f16 instruction descriptor: f16 x f16 -> f32, both K-major, M = 128, N = 128.
+// kind::f16 instruction descriptors: f16 x f16 -> f32, both K-major, M = 128,
+// N = 128 or N = 256 (B_hi and B_lo, adjacent in shared memory, as one operand).
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+constexpr uint32_t kIdesc2 = (1u << 4) | ((uint32_t)((2 * TC_N) >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 
 // power-of-two exponent that brings max |phi| just below 2^14
 __device__ __forceinline__ int phi_exp(const float *amax) {
@@ -166,11 +170,12 @@ __device__ __forceinline__ int phi_exp(const float *amax) {
     return 14 - e;
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc,
+                                       uint32_t idesc = kIdesc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
             d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
 }
 
@@ -207,14 +212,15 @@ struct TcArgs {
     int *err;
 };
 
+template <int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
              const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = (uint64_t *)smem;               // [5]
-    uint64_t *empty = full + TC_STAGES;              // [5]
-    uint64_t *wfull = empty + TC_STAGES;             // [2] work accumulator ready
+    uint64_t *full = (uint64_t *)smem;               // [STAGES]
+    uint64_t *empty = full + STAGES;              // [STAGES]
+    uint64_t *wfull = empty + STAGES;             // [2] work accumulator ready
     uint64_t *wfree = wfull + 2;                     // [2] work accumulator drained
     uint32_t *tmem_slot = (uint32_t *)(wfree + 2);
     int *nact_s = (int *)(tmem_slot + 1);
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int kchunks = a.KK / TC_K;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; s++) {
+        for (int s = 0; s < STAGES; s++) {
             mbar_init(&full[s], a.grid ? 1 : 128);
             mbar_init(&empty[s], 1);
         }
@@ -301,8 +307,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (tid == 0) {
             int cur_si = -1, op = 0, cx = 0, cy = 0, cz = 0;
             for (int it = 0; it < total; it++) {
-                const int st = it % TC_STAGES;
-                const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+                const int st = it % STAGES;
+                const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                 if (!mbar_wait(&empty[st], ph ^ 1u, a.err)) break;
                 const int si = it / kchunks, k0 = (it % kchunks) * TC_K;
                 if (si != cur_si) {
@@ -338,8 +344,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int cur_si = -1, op = 0;
         long long srow = -1;  // -1: no source box in this slot (zeros)
         for (int it = 0; it < total; it++) {
-            const int st = it % TC_STAGES;
-            const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+            const int st = it % STAGES;
+            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
             if (!mbar_wait(&empty[st], ph ^ 1u, a.err)) break;
             const int si = it / kchunks, k0 = (it % kchunks) * TC_K;
             if (si != cur_si) {  // new slot: its operator and this row's source
@@ -387,10 +393,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int wb = si & 1;
                 if (!mbar_wait(&wfree[wb], ((uint32_t)(si >> 1) & 1u) ^ 1u, a.err)) break;
                 tc_fence_after();
-                const uint32_t dbig = tmem + wb * TC_N, dsmall = tmem + 2 * TC_N + wb * TC_N;
+                // buffer wb: columns [256 wb, 256 wb + 128) hold hi*hi, the next 128 the cross terms
+                const uint32_t dbig = tmem + wb * 2 * TC_N, dsmall = dbig + TC_N;
                 for (int kc = 0; kc < kchunks; kc++, it++) {
-                    const int st = it % TC_STAGES;
-                    if (!mbar_wait(&full[st], (uint32_t)(it / TC_STAGES) & 1u, a.err)) {
+                    const int st = it % STAGES;
+                    if (!mbar_wait(&full[st], (uint32_t)(it / STAGES) & 1u, a.err)) {
                         okm = false;
                         break;
                     }
@@ -399,15 +406,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const uint32_t sb = smem_u32(stages + (size_t)st * TC_STAGE_BYTES);
 #pragma unroll
-                    for (int term = 0; term < 3; term++) {
-                        const int ah = term == 2, bh = term == 1;  // (hi,hi), (hi,lo), (lo,hi)
-#pragma unroll
-                        for (int k16 = 0; k16 < 2; k16++) {
-                            uint64_t ad = smem_desc_sw64(sb + ah * TC_A_BYTES + k16 * 32);
-                            uint64_t bd = smem_desc_sw64(sb + 2 * TC_A_BYTES + bh * TC_B_BYTES + k16 * 32);
-                            if (term == 0) tc_mma(dbig, ad, bd, (kc | k16) ? 1u : 0u);
-                            else tc_mma(dsmall, ad, bd, (kc | (term - 1) | k16) ? 1u : 0u);
-                        }
+                    for (int k16 = 0; k16 < 2; k16++) {
+                        const uint64_t a_hi = smem_desc_sw64(sb + k16 * 32);
+                        const uint64_t a_lo = smem_desc_sw64(sb + TC_A_BYTES + k16 * 32);
+                        const uint64_t b_hl = smem_desc_sw64(sb + 2 * TC_A_BYTES + k16 * 32);  // B_hi then B_lo
+                        // A_hi [B_hi | B_lo] -> [hi*hi | hi*lo] in one N = 256 MMA, then lo*hi onto the cross terms
+                        tc_mma(dbig, a_hi, b_hl, (kc | k16) ? 1u : 0u, kIdesc2);
+                        tc_mma(dsmall, a_lo, b_hl, 1u);
                     }
                     tc_commit(&empty[st]);
                 }
@@ -431,9 +436,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int c0 = 0; c0 < TC_N; c0 += 16) {
                 uint32_t v[16], u[16];
-                const uint32_t ta = tmem + ((uint32_t)(sp * 32) << 16) + wb * TC_N + c0;
+                const uint32_t ta = tmem + ((uint32_t)(sp * 32) << 16) + wb * 2 * TC_N + c0;
                 tc_ld16_nowait(ta, v);
-                tc_ld16_nowait(ta + 2 * TC_N, u);
+                tc_ld16_nowait(ta + TC_N, u);
                 tc_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 16; j++) acc[c0 + j] += __uint_as_float(v[j]) + __uint_as_float(u[j]);
@@ -664,7 +669,12 @@ void m2l_tc_prepare(Plan &P) {
     PK_CUDA(cudaMallocHost(&t->err_host, sizeof(int)));
     PK_CUDA(cudaEventCreate(&t->ev[0]));
     PK_CUDA(cudaEventCreate(&t->ev[1]));
-    PK_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    PK_CUDA(cudaFuncSetAttribute(k_m2l_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(4)));
+    PK_CUDA(cudaFuncSetAttribute(k_m2l_tc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(6)));
+    // pipeline depth: 6 stages (about 192 KB of operands in flight); 4 for timing comparisons
+    t->stages = 6;
+    if (const char *e = std::getenv("PKIFMM_M2L_STAGES"))
+        if (std::atoi(e) == 4) t->stages = 4;
 }
 
 namespace {
@@ -848,8 +858,12 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         a.tboxes = t->gboxes;
         a.tiles = t->gtiles;
         a.grid = 0;
-        count_launch(), k_m2l_tc<<<ngather_tiles * mtiles, TC_THREADS, TC_SMEM, s>>>(t->tmap[0], t->tmap[1], t->tmap[0],
-                                                                                     t->tmap[1], a);
+        if (t->stages == 4)
+            count_launch(), k_m2l_tc<4><<<ngather_tiles * mtiles, TC_THREADS, tc_smem(4), s>>>(t->tmap[0], t->tmap[1],
+                                                                                              t->tmap[0], t->tmap[1], a);
+        else
+            count_launch(), k_m2l_tc<6><<<ngather_tiles * mtiles, TC_THREADS, tc_smem(6), s>>>(t->tmap[0], t->tmap[1],
+                                                                                              t->tmap[0], t->tmap[1], a);
         PK_CUDA(cudaGetLastError());
     }
     EncodeTiledFn enc = encode_fn();
@@ -880,7 +894,10 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         a.rb = g.rb;
         const int ntl = gt_begin[gi + 1] - gt_begin[gi];
         if (ntl == 0) continue;
-        count_launch(), k_m2l_tc<<<ntl * mtiles, TC_THREADS, TC_SMEM, s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
+        if (t->stages == 4)
+            count_launch(), k_m2l_tc<4><<<ntl * mtiles, TC_THREADS, tc_smem(4), s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
+        else
+            count_launch(), k_m2l_tc<6><<<ntl * mtiles, TC_THREADS, tc_smem(6), s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
         PK_CUDA(cudaGetLastError());
     }
     PK_CUDA(cudaEventRecord(t->ev[1], s));

@@ -98,6 +98,7 @@ void upload_operators(Plan &P) {
     PK_CUDA(cudaMemcpy(P.slot_of.p, slot_of.data(), sizeof(short) * slot_of.size(), cudaMemcpyHostToDevice));
     P.class_slot_op.reserve(cls_op.size());
     PK_CUDA(cudaMemcpy(P.class_slot_op.p, cls_op.data(), sizeof(int) * cls_op.size(), cudaMemcpyHostToDevice));
+    P.h_class_slot_op = cls_op;
     DBuf<int> doffs;
     doffs.reserve(offs.size());
     PK_CUDA(cudaMemcpy(doffs.p, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice));
@@ -305,8 +306,43 @@ struct HostTree {
 };
 
 // boxes: per class list of dst boxes
+// Host-built task arrays are packed into one pinned buffer and copied with
+// one asynchronous copy per array (no stream synchronisation per task).
+struct Uploads {
+    std::vector<char> pack;
+    struct Item {
+        void *dst;
+        size_t off, bytes;
+    };
+    std::vector<Item> items;
+    template <typename T>
+    void add(void *dst, const T *src, size_t n) {
+        if (!n) return;
+        size_t off = (pack.size() + 15) & ~(size_t)15;
+        pack.resize(off + sizeof(T) * n);
+        std::memcpy(pack.data() + off, src, sizeof(T) * n);
+        items.push_back({dst, off, sizeof(T) * n});
+    }
+    void flush(Plan &P, cudaStream_t s) {
+        if (pack.empty()) return;
+        if (P.stage_ev_live) PK_CUDA(cudaEventSynchronize(P.stage_ev));  // the previous copies read the buffer
+        if (pack.size() > P.stage_cap) {
+            if (P.stage_h) PK_CUDA(cudaFreeHost(P.stage_h));
+            P.stage_h = nullptr;
+            P.stage_cap = pack.size() + pack.size() / 2;
+            PK_CUDA(cudaHostAlloc(&P.stage_h, P.stage_cap, cudaHostAllocDefault));
+        }
+        std::memcpy(P.stage_h, pack.data(), pack.size());
+        for (auto &it : items)
+            PK_CUDA(cudaMemcpyAsync(it.dst, P.stage_h + it.off, it.bytes, cudaMemcpyHostToDevice, s));
+        if (!P.stage_ev) PK_CUDA(cudaEventCreateWithFlags(&P.stage_ev, cudaEventDisableTiming));
+        PK_CUDA(cudaEventRecord(P.stage_ev, s));
+        P.stage_ev_live = true;
+    }
+};
+
 static void make_task(Task &t, const std::vector<std::vector<int>> &by_class, int nslots,
-                      const std::vector<int> &class_ops, int nrhs, cudaStream_t s, int bm = GB_M) {
+                      const std::vector<int> &class_ops, int nrhs, Uploads &up, int bm = GB_M) {
     t.nclass = (int)by_class.size();
     t.nslots = nslots;
     t.h_boxes.clear();
@@ -324,17 +360,14 @@ static void make_task(Task &t, const std::vector<std::vector<int>> &by_class, in
     t.boxes.reserve(t.h_boxes.size() + 1);
     t.tiles.reserve(tiles.size() + 1);
     t.class_ops.reserve(class_ops.size() + 1);
-    if (!t.h_boxes.empty())
-        PK_CUDA(cudaMemcpyAsync(t.boxes.p, t.h_boxes.data(), sizeof(int) * t.h_boxes.size(), cudaMemcpyHostToDevice, s));
-    if (!tiles.empty())
-        PK_CUDA(cudaMemcpyAsync(t.tiles.p, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
-    PK_CUDA(cudaMemcpyAsync(t.class_ops.p, class_ops.data(), sizeof(int) * class_ops.size(), cudaMemcpyHostToDevice, s));
-    PK_CUDA(cudaStreamSynchronize(s));  // host vectors are about to go out of scope
+    up.add(t.boxes.p, t.h_boxes.data(), t.h_boxes.size());
+    up.add(t.tiles.p, tiles.data(), tiles.size());
+    up.add(t.class_ops.p, class_ops.data(), class_ops.size());
 }
 
-static void upload_list(DBuf<int> &d, const std::vector<int> &v, cudaStream_t s) {
+static void upload_list(DBuf<int> &d, const std::vector<int> &v, Uploads &up) {
     d.reserve(v.size() + 1);
-    if (!v.empty()) PK_CUDA(cudaMemcpyAsync(d.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
+    up.add(d.p, v.data(), v.size());
 }
 
 void build_tasks(Plan &P, cudaStream_t s) {
@@ -346,12 +379,15 @@ void build_tasks(Plan &P, cudaStream_t s) {
     H.parent.resize(nb);
     H.sr.resize(nb);
     H.tr.resize(nb);
+    std::vector<int> xptr(nb + 1);
     PK_CUDA(cudaMemcpyAsync(H.bpos.data(), t.bpos.p, sizeof(int4) * nb, cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaMemcpyAsync(H.child.data(), t.child.p, sizeof(int) * 8 * (size_t)nb, cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaMemcpyAsync(H.parent.data(), t.parent.p, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaMemcpyAsync(H.sr.data(), t.srange.p, sizeof(int2) * nb, cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaMemcpyAsync(H.tr.data(), t.trange.p, sizeof(int2) * nb, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaMemcpyAsync(xptr.data(), t.x_ptr.p, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaStreamSynchronize(s));
+    Uploads up;
     const int nr = P.nrhs;
     std::vector<int> leaves_src, leaves_trg;
     t.nleaf = 0;
@@ -363,22 +399,19 @@ void build_tasks(Plan &P, cudaStream_t s) {
     }
     P.n_leaves_src = (int)leaves_src.size();
     P.n_leaves_trg = (int)leaves_trg.size();
-    upload_list(P.leaves_src, leaves_src, s);
-    upload_list(P.leaves_trg, leaves_trg, s);
+    upload_list(P.leaves_src, leaves_src, up);
+    upload_list(P.leaves_trg, leaves_trg, up);
     // X-list boxes (with targets and a non-empty X list)
-    std::vector<int> xptr(nb + 1);
-    PK_CUDA(cudaMemcpyAsync(xptr.data(), t.x_ptr.p, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
-    PK_CUDA(cudaStreamSynchronize(s));
     std::vector<int> xb;
     for (int b = 0; b < nb; b++)
         if (xptr[b + 1] > xptr[b] && H.has_trg(b)) xb.push_back(b);
     P.n_xboxes = (int)xb.size();
-    upload_list(P.xboxes, xb, s);
+    upload_list(P.xboxes, xb, up);
 
     bool mixed = P.precision == PKIFMM_MIXED;
     const int bm = mixed ? GemmCfg<float>::BM : GemmCfg<double>::BM;
     // UC2E over leaves with sources
-    make_task(P.t_uc2e, {leaves_src}, 1, {0}, nr, s, bm);
+    make_task(P.t_uc2e, {leaves_src}, 1, {0}, nr, up, bm);
     // M2M per level: non-leaf boxes with sources
     int depth = (int)t.lvl_begin.size() - 1;
     P.t_m2m.resize(depth);
@@ -388,30 +421,27 @@ void build_tasks(Plan &P, cudaStream_t s) {
         std::vector<int> v;
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
             if (!H.leaf(b) && H.has_src(b)) v.push_back(b);
-        make_task(P.t_m2m[l], {v}, 8, ops8, nr, s, bm);
+        make_task(P.t_m2m[l], {v}, 8, ops8, nr, up, bm);
     }
-    // root
-    make_task(P.t_root, {{0}}, 1, {0}, nr, s);
     // M2L: boxes of level >= 1 with targets, by octant class
     std::vector<std::vector<int>> byc(8);
     for (int b = P.nprob; b < nb; b++)  // boxes 0..nprob-1 are the problems' roots
         if (H.has_trg(b)) byc[H.octant(b)].push_back(b);
-    std::vector<int> cls_op(8 * kVSlots);
-    PK_CUDA(cudaMemcpy(cls_op.data(), P.class_slot_op.p, sizeof(int) * cls_op.size(), cudaMemcpyDeviceToHost));
-    make_task(P.t_m2l, byc, kVSlots, cls_op, nr, s, bm);
-    // DC2E over boxes with targets (root separately in binary64 for MIXED)
+    make_task(P.t_m2l, byc, kVSlots, P.h_class_slot_op, nr, up, bm);
+    // DC2E over boxes with targets (roots separately in binary64 for MIXED)
     std::vector<int> dc;
     for (int b = (mixed ? P.nprob : 0); b < nb; b++)
         if (H.has_trg(b)) dc.push_back(b);
-    make_task(P.t_dc2e, {dc}, 1, {0}, nr, s, bm);
+    make_task(P.t_dc2e, {dc}, 1, {0}, nr, up, bm);
     // L2L per level >= 1, by octant class
     P.t_l2l.resize(depth);
     for (int l = 1; l < depth; l++) {
         std::vector<std::vector<int>> bc(8);
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
             if (H.has_trg(b)) bc[H.octant(b)].push_back(b);
-        make_task(P.t_l2l[l], bc, 1, ops8, nr, s, bm);
+        make_task(P.t_l2l[l], bc, 1, ops8, nr, up, bm);
     }
+    up.flush(P, s);
 }
 
 // Large binary32 slot GEMM: a 128 x 128 output tile per CTA, 16 K per step,

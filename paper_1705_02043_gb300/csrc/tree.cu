@@ -79,8 +79,8 @@ __global__ void k_scan_fix_total(int *out, const int *in, int n) {
 }
 
 // Exclusive scan of in[0..n) into out[0..n], out[n] = total.  Returns the
-// total (synchronises the stream).
-int exclusive_scan(const int *in, int *out, int n, cudaStream_t s) {
+// total (synchronises the stream) when `want_total`, else 0 without waiting.
+int exclusive_scan(const int *in, int *out, int n, cudaStream_t s, bool want_total = true) {
     if (n <= 0) {
         PK_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
         return 0;
@@ -91,14 +91,15 @@ int exclusive_scan(const int *in, int *out, int n, cudaStream_t s) {
     PK_CUDA(cudaMallocAsync(&boff, sizeof(int) * (nb + 1), s));
     count_launch(), k_scan_block<<<nb, 1024, 0, s>>>(in, out, bsum, n);
     if (nb > 1) {
-        exclusive_scan(bsum, boff, nb, s);
+        exclusive_scan(bsum, boff, nb, s, false);
         count_launch(), k_scan_add<<<nb, 1024, 0, s>>>(out, boff, n, nullptr);
     }
     count_launch(), k_scan_fix_total<<<1, 1, 0, s>>>(out, in, n);
-    int total = 0;
-    PK_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaFreeAsync(bsum, s));
     PK_CUDA(cudaFreeAsync(boff, s));
+    if (!want_total) return 0;
+    int total = 0;
+    PK_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaStreamSynchronize(s));
     return total;
 }
@@ -217,7 +218,7 @@ static void radix_sort(DBuf<unsigned long long> &k, DBuf<int> &v, DBuf<unsigned 
     int *h = hist.p, *ho = hist.p + 16 * nb + 1;
     for (int sh = 0; sh < bits; sh += 4) {
         count_launch(), k_rs_count<<<nb, RS_T, 0, s>>>(ka, n, sh, h, nb);
-        exclusive_scan(h, ho, 16 * nb, s);
+        exclusive_scan(h, ho, 16 * nb, s, false);  // the radix sort needs no total
         count_launch(), k_rs_scatter<<<nb, RS_T, 0, s>>>(ka, va, kb, vb, n, sh, ho, nb);
         std::swap(ka, kb);
         std::swap(va, vb);
