@@ -16,10 +16,10 @@
 // nearest, into fp32 registers of the epilogue warps, while the next slot
 // accumulates in the other buffer.  Within a slot the large hi*hi products
 // and the 2^-11 smaller cross products go to separate accumulators, so the
-// large one takes only 2 KK/32 steps per slot.
+// large one takes only KK/16 steps per slot.
 //
-// Pipeline (6 stages of 32 KB): warps 0-3 gather the Phi rows with 16-byte
-// cp.async into the 64B-swizzled K-major layout and one thread issues the TMA
+// Pipeline (3 stages of 64 KB): warps 0-3 gather the Phi rows with 16-byte
+// cp.async into the 128B-swizzled K-major layout and one thread issues the TMA
 // loads of the K_o tiles; warp 4 issues tcgen05.mma from one thread and frees
 // each stage with tcgen05.commit; warps 5-8 drain the work accumulators and
 // finally write the check potentials.  Every mbarrier wait is bounded in time;
@@ -37,10 +37,10 @@ namespace pk {
 
 constexpr int TC_N = 128;                          // (box, rhs) columns per CTA
 constexpr int TC_M = 128;                          // kn rows per CTA
-constexpr int TC_K = 32;                           // K chunk: 64 bytes of fp16 per row
-constexpr int TC_STAGES = 6;                        // pipeline depth (the default instantiation)
-constexpr int TC_A_BYTES = TC_M * TC_K * 2;        // 8 KB per split
-constexpr int TC_B_BYTES = TC_N * TC_K * 2;        // 8 KB per split
+constexpr int TC_K = 64;                           // K chunk: 128 bytes of fp16 per row (128-byte swizzle)
+constexpr int TC_STAGES = 3;                        // pipeline depth (the default instantiation)
+constexpr int TC_A_BYTES = TC_M * TC_K * 2;        // 16 KB per split
+constexpr int TC_B_BYTES = TC_N * TC_K * 2;        // 16 KB per split
 constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 32 KB
 constexpr int TC_CTRL_BYTES = 4096;
 constexpr int TC_SLACK = 16384;
@@ -72,7 +72,7 @@ struct TcState {
     size_t gboxes_cap = 0;
     int *lmap = nullptr;                 // position -> box maps of the partial grid levels (-1: no box)
     size_t lmap_cap = 0;
-    int stages = 6;                      // pipeline depth of the launched instantiation
+    int stages = 3;                      // pipeline depth of the launched instantiation
 };
 
 // ---------------- PTX helpers ----------------
@@ -147,13 +147,13 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-// K-major operand with 64-byte rows, 64B swizzle: 8-row atoms of 512 bytes.
-__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+// K-major operand with 128-byte rows, 128B swizzle: 8-row atoms of 1024 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     return (uint64_t)((addr >> 4) & 0x3FFF)    // start address
            | ((uint64_t)1 << 16)               // leading byte offset (unused for swizzled K-major)
-           | ((uint64_t)(512 >> 4) << 32)      // stride byte offset: 8 rows x 64 B
+           | ((uint64_t)(1024 >> 4) << 32)     // stride byte offset: 8 rows x 128 B
            | ((uint64_t)1 << 46)               // descriptor version
-           | ((uint64_t)4 << 61);              // layout: 64-byte swizzle
+           | ((uint64_t)2 << 61);              // layout: 128-byte swizzle
 }
 
 // kind::f16 instruction descriptors: f16 x f16 -> f32, both K-major, M = 128,
@@ -361,14 +361,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tma_load_2d(sb, &tA_hi, k0, op * a.KM + m0, &full[st]);
                 tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KM + m0, &full[st]);
             }
-            uint8_t *rowdst = sb + 2 * TC_A_BYTES + (r >> 3) * 512 + ri * 64;
+            // 128-byte swizzle: row r at (r / 8) * 1024 + (r % 8) * 128, 16-byte chunk c at c ^ (r % 8)
+            uint8_t *rowdst = sb + 2 * TC_A_BYTES + (r >> 3) * 1024 + ri * 128;
             if (srow >= 0) {
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
                     const __half *g = (h ? a.phi_lo : a.phi_hi) + srow * a.KK + k0;
                     uint8_t *d = rowdst + h * TC_B_BYTES;
 #pragma unroll
-                    for (int c = 0; c < 4; c++) cp_async16(d + ((c ^ ((ri >> 1) & 3)) << 4), g + c * 8);
+                    for (int c = 0; c < 8; c++) cp_async16(d + ((c ^ ri) << 4), g + c * 8);
                 }
                 asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st]))
                              : "memory");
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int h = 0; h < 2; h++)
 #pragma unroll
-                    for (int c = 0; c < 4; c++)
+                    for (int c = 0; c < 8; c++)
                         *reinterpret_cast<uint4 *>(rowdst + h * TC_B_BYTES + (c << 4)) = make_uint4(0, 0, 0, 0);
                 mbar_arrive(&full[st]);  // release: orders the zero stores before the MMA's acquire
             }
@@ -406,10 +407,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const uint32_t sb = smem_u32(stages + (size_t)st * TC_STAGE_BYTES);
 #pragma unroll
-                    for (int k16 = 0; k16 < 2; k16++) {
-                        const uint64_t a_hi = smem_desc_sw64(sb + k16 * 32);
-                        const uint64_t a_lo = smem_desc_sw64(sb + TC_A_BYTES + k16 * 32);
-                        const uint64_t b_hl = smem_desc_sw64(sb + 2 * TC_A_BYTES + k16 * 32);  // B_hi then B_lo
+                    for (int k16 = 0; k16 < TC_K / 16; k16++) {
+                        const uint64_t a_hi = smem_desc_sw128(sb + k16 * 32);
+                        const uint64_t a_lo = smem_desc_sw128(sb + TC_A_BYTES + k16 * 32);
+                        const uint64_t b_hl = smem_desc_sw128(sb + 2 * TC_A_BYTES + k16 * 32);  // B_hi then B_lo
                         // A_hi [B_hi | B_lo] -> [hi*hi | hi*lo] in one N = 256 MMA, then lo*hi onto the cross terms
                         tc_mma(dbig, a_hi, b_hl, (kc | k16) ? 1u : 0u, kIdesc2);
                         tc_mma(dsmall, a_lo, b_hl, 1u);
@@ -642,7 +643,7 @@ void m2l_tc_prepare(Plan &P) {
         cuuint32_t box[2] = {TC_K, TC_M};
         cuuint32_t estr[2] = {1, 1};
         CUresult r = enc(&t->tmap[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, t->kop + h * nk, dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) throw Error(PKIFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
@@ -669,12 +670,12 @@ void m2l_tc_prepare(Plan &P) {
     PK_CUDA(cudaMallocHost(&t->err_host, sizeof(int)));
     PK_CUDA(cudaEventCreate(&t->ev[0]));
     PK_CUDA(cudaEventCreate(&t->ev[1]));
-    PK_CUDA(cudaFuncSetAttribute(k_m2l_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(4)));
-    PK_CUDA(cudaFuncSetAttribute(k_m2l_tc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(6)));
-    // pipeline depth: 6 stages (about 192 KB of operands in flight); 4 for timing comparisons
-    t->stages = 6;
+    PK_CUDA(cudaFuncSetAttribute(k_m2l_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(2)));
+    PK_CUDA(cudaFuncSetAttribute(k_m2l_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(3)));
+    // pipeline depth: 3 stages of 64 KB (192 KB of operands in flight); 2 for timing comparisons
+    t->stages = 3;
     if (const char *e = std::getenv("PKIFMM_M2L_STAGES"))
-        if (std::atoi(e) == 4) t->stages = 4;
+        if (std::atoi(e) == 2) t->stages = 2;
 }
 
 namespace {
@@ -858,11 +859,11 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         a.tboxes = t->gboxes;
         a.tiles = t->gtiles;
         a.grid = 0;
-        if (t->stages == 4)
-            count_launch(), k_m2l_tc<4><<<ngather_tiles * mtiles, TC_THREADS, tc_smem(4), s>>>(t->tmap[0], t->tmap[1],
+        if (t->stages == 2)
+            count_launch(), k_m2l_tc<2><<<ngather_tiles * mtiles, TC_THREADS, tc_smem(2), s>>>(t->tmap[0], t->tmap[1],
                                                                                               t->tmap[0], t->tmap[1], a);
         else
-            count_launch(), k_m2l_tc<6><<<ngather_tiles * mtiles, TC_THREADS, tc_smem(6), s>>>(t->tmap[0], t->tmap[1],
+            count_launch(), k_m2l_tc<3><<<ngather_tiles * mtiles, TC_THREADS, tc_smem(3), s>>>(t->tmap[0], t->tmap[1],
                                                                                               t->tmap[0], t->tmap[1], a);
         PK_CUDA(cudaGetLastError());
     }
@@ -879,7 +880,7 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
             cuuint32_t box[5] = {TC_K, (cuuint32_t)g.rb, (cuuint32_t)g.bx, (cuuint32_t)g.by, (cuuint32_t)g.bz};
             cuuint32_t estr[5] = {1, 1, 1, 1, 1};
             CUresult r = enc(&mb[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, base, dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) throw Error(PKIFMM_ERR_CUDA, "cuTensorMapEncodeTiled (level grid) failed");
         }
@@ -894,10 +895,10 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         a.rb = g.rb;
         const int ntl = gt_begin[gi + 1] - gt_begin[gi];
         if (ntl == 0) continue;
-        if (t->stages == 4)
-            count_launch(), k_m2l_tc<4><<<ntl * mtiles, TC_THREADS, tc_smem(4), s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
+        if (t->stages == 2)
+            count_launch(), k_m2l_tc<2><<<ntl * mtiles, TC_THREADS, tc_smem(2), s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
         else
-            count_launch(), k_m2l_tc<6><<<ntl * mtiles, TC_THREADS, tc_smem(6), s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
+            count_launch(), k_m2l_tc<3><<<ntl * mtiles, TC_THREADS, tc_smem(3), s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
         PK_CUDA(cudaGetLastError());
     }
     PK_CUDA(cudaEventRecord(t->ev[1], s));
