@@ -296,7 +296,8 @@ def main():
         achieved = flops / (m2l_avg / 1e3) / 1e12
         peak = pk_.get("bf16_tflops_sustained", 1700.0)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": m2l_traffic(workload_name(args.workload, wl, args.n, args.p, args.leaf)),
                 "kernel": "k_m2l_tc: M2L (V list), split-fp16 x3 tcgen05",
                 "peak_source": f"bf16_tflops_sustained ({src}), same rate as fp16",
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": m2l_avg,
@@ -365,6 +366,23 @@ def main():
         dist.destroy_process_group()
     if result is not None:
         print(json.dumps(result), flush=True)
+
+
+def m2l_traffic(workload_name):
+    """DRAM bytes (read + write) of one evaluation's M2L launches from the committed
+    ncu note for this workload, or None when there is none or the kernel source has
+    changed since it was taken (the note records the source's SHA-256)."""
+    import hashlib
+    note = os.path.join(ROOT, "profiles", f"m2l_tc_traffic_{workload_name}.md")
+    src = os.path.join(ROOT, "paper_1705_02043_gb300", "csrc", "m2l_tc.cu")
+    try:
+        fields = dict(l.split(":", 1) for l in open(note).read().splitlines() if l.startswith(("source_sha256:", "dram_bytes_per_evaluation:")))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if fields["source_sha256"].strip() != sha:
+            return None
+        return float(fields["dram_bytes_per_evaluation"].strip())
+    except Exception:
+        return None
 
 
 def plan_uses_tensor_cores():

@@ -73,6 +73,8 @@ struct TcState {
     int *lmap = nullptr;                 // position -> box maps of the partial grid levels (-1: no box)
     size_t lmap_cap = 0;
     int stages = 3;                      // pipeline depth of the launched instantiation
+    cudaStream_t side[3] = {};           // the per-level launches run concurrently (disjoint outputs)
+    cudaEvent_t fork = nullptr, join[3] = {};
 };
 
 // ---------------- PTX helpers ----------------
@@ -209,6 +211,7 @@ struct TcArgs {
     // grid mode (a level dense enough for 8 parity sub-grids of Phi with a 2-box halo)
     int grid, lvl_begin, zd, bx, by, bz, rb;
     const int *lmap;                       // Morton position -> box, -1 if absent; null: every box exists
+    int boxg;                              // gather mode by boxes: a box's nrhs source rows by one 2D TMA
     int *err;
 };
 
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; s++) {
-            mbar_init(&full[s], a.grid ? 1 : 128);
+            mbar_init(&full[s], a.grid ? 1 : (a.boxg ? 32 : 128));
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; b++) {
@@ -333,6 +336,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 mbar_arrive(&full[st]);
             }
         }
+    } else if (warp == 0 && a.boxg) {
+        // ---- producer (gather by boxes, nrhs >= 8): warp 0.  Lane j < 128/nrhs owns
+        // target box j (rows j nrhs .. j nrhs + nrhs - 1 of the tile); its source
+        // box's nrhs rows are contiguous in Phi, one 2D TMA per split; absent
+        // sources are zero-filled by the warp.  Lane 0 adds the operator tiles.
+        const int nbx = TC_N / a.nrhs;
+        const int tbox = lane < nbx ? sbox[lane * a.nrhs] : -1;
+        int cur_si = -1, op = 0, src = -1;
+        for (int it = 0; it < total; it++) {
+            const int st = it % STAGES;
+            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+            const bool ok = mbar_wait(&empty[st], ph ^ 1u, a.err);  // every lane acquires the free stage
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const int si = it / kchunks, k0 = (it % kchunks) * TC_K;
+            if (si != cur_si) {
+                cur_si = si;
+                const int s = act[si];
+                op = a.class_ops[cls * kVSlots + s];
+                src = tbox >= 0 ? a.v_slot[(long long)tbox * kVSlots + s] : -1;
+            }
+            const unsigned present = __ballot_sync(0xffffffffu, lane < nbx && src >= 0);
+            uint8_t *sb = stages + (size_t)st * TC_STAGE_BYTES;
+            const uint32_t rows_b = (uint32_t)a.nrhs * TC_K * 2;  // bytes of one box's rows, one split
+            if (lane == 0) {
+                mbar_expect_tx(&full[st], (uint32_t)(2 * TC_A_BYTES) + 2u * rows_b * (uint32_t)__popc(present));
+                tma_load_2d(sb, &tA_hi, k0, op * a.KM + m0, &full[st]);
+                tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KM + m0, &full[st]);
+            }
+            __syncwarp();
+            if (lane < nbx && src >= 0) {
+                uint8_t *d = sb + 2 * TC_A_BYTES + (size_t)lane * rows_b;
+                tma_load_2d(d, &tB_hi, k0, src * a.nrhs, &full[st]);
+                tma_load_2d(d + TC_B_BYTES, &tB_lo, k0, src * a.nrhs, &full[st]);
+            }
+            // zero rows of absent sources (16-byte stores spread over the warp)
+            const unsigned absent = ~present & ((nbx >= 32) ? 0xffffffffu : ((1u << nbx) - 1u));
+            for (unsigned m = absent; m; m &= m - 1) {
+                const int j = __ffs(m) - 1;
+                uint8_t *d = sb + 2 * TC_A_BYTES + (size_t)j * rows_b;
+                for (uint32_t o = (uint32_t)lane * 16; o < rows_b; o += 32 * 16) {
+                    *reinterpret_cast<uint4 *>(d + o) = make_uint4(0, 0, 0, 0);
+                    *reinterpret_cast<uint4 *>(d + TC_B_BYTES + o) = make_uint4(0, 0, 0, 0);
+                }
+            }
+            mbar_arrive(&full[st]);  // 32 arrivals (+ the expected bytes)
+        }
+    } else if (warp < 4 && a.boxg) {
+        // idle producer warps in box-gather mode
     } else if (warp < 4) {
         // ---- producers: gather Phi rows (cp.async) and TMA the operator tiles ----
         // Each thread's row copies arrive on the stage's full barrier when
@@ -599,6 +650,11 @@ void m2l_tc_release(Plan &P) {
     cudaFree(t->gtiles);
     cudaFree(t->gboxes);
     cudaFree(t->lmap);
+    for (int i = 0; i < 3; i++) {
+        if (t->side[i]) cudaStreamDestroy(t->side[i]);
+        if (t->join[i]) cudaEventDestroy(t->join[i]);
+    }
+    if (t->fork) cudaEventDestroy(t->fork);
     cudaFree(t->err);
     cudaFreeHost(t->err_host);
     if (t->ev[0]) cudaEventDestroy(t->ev[0]);
@@ -853,21 +909,50 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         }
     }
     PK_CUDA(cudaEventRecord(t->ev[0], s));
+    // the gather launch and the grid launches (one per level) write disjoint check
+    // rows: run them on side streams so small launches and wave tails overlap
+    if (!t->fork) {
+        PK_CUDA(cudaEventCreateWithFlags(&t->fork, cudaEventDisableTiming));
+        for (int i = 0; i < 3; i++) {
+            PK_CUDA(cudaStreamCreateWithFlags(&t->side[i], cudaStreamNonBlocking));
+            PK_CUDA(cudaEventCreateWithFlags(&t->join[i], cudaEventDisableTiming));
+        }
+    }
+    PK_CUDA(cudaEventRecord(t->fork, s));
+    for (int i = 0; i < 3; i++) PK_CUDA(cudaStreamWaitEvent(t->side[i], t->fork, 0));
+    int nlaunch = 0;
+    EncodeTiledFn enc = encode_fn();
     if (ngather_tiles > 0) {
         a.phi_hi = t->phi;
         a.phi_lo = t->phi + t->phi_rows * KK;
         a.tboxes = t->gboxes;
         a.tiles = t->gtiles;
         a.grid = 0;
+        // several vectors per box: a box's source rows are contiguous, one 2D TMA each
+        a.boxg = (nr >= 8 && TC_N % nr == 0) ? 1 : 0;
+        CUtensorMap pm[2] = {t->tmap[0], t->tmap[1]};
+        if (a.boxg) {
+            for (int h = 0; h < 2; h++) {
+                cuuint64_t dims[2] = {(cuuint64_t)KK, (cuuint64_t)(rows + 1)};
+                cuuint64_t strides[1] = {(cuuint64_t)KK * 2};
+                cuuint32_t box[2] = {TC_K, (cuuint32_t)nr};
+                cuuint32_t estr[2] = {1, 1};
+                CUresult r = enc(&pm[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void *)(t->phi + (size_t)h * t->phi_rows * KK), dims, strides, box,
+                                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) throw Error(PKIFMM_ERR_CUDA, "cuTensorMapEncodeTiled (Phi rows) failed");
+            }
+        }
+        cudaStream_t ls = t->side[nlaunch++ % 3];
         if (t->stages == 2)
-            count_launch(), k_m2l_tc<2><<<ngather_tiles * mtiles, TC_THREADS, tc_smem(2), s>>>(t->tmap[0], t->tmap[1],
-                                                                                              t->tmap[0], t->tmap[1], a);
+            count_launch(), k_m2l_tc<2><<<ngather_tiles * mtiles, TC_THREADS, tc_smem(2), ls>>>(t->tmap[0], t->tmap[1],
+                                                                                               pm[0], pm[1], a);
         else
-            count_launch(), k_m2l_tc<3><<<ngather_tiles * mtiles, TC_THREADS, tc_smem(3), s>>>(t->tmap[0], t->tmap[1],
-                                                                                              t->tmap[0], t->tmap[1], a);
+            count_launch(), k_m2l_tc<3><<<ngather_tiles * mtiles, TC_THREADS, tc_smem(3), ls>>>(t->tmap[0], t->tmap[1],
+                                                                                               pm[0], pm[1], a);
         PK_CUDA(cudaGetLastError());
+        a.boxg = 0;
     }
-    EncodeTiledFn enc = encode_fn();
     for (size_t gi = 0; gi < gp.size(); gi++) {
         const GridPlan &g = gp[gi];
         const cuuint64_t d = (cuuint64_t)(g.n / 2 + 4);
@@ -895,11 +980,16 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         a.rb = g.rb;
         const int ntl = gt_begin[gi + 1] - gt_begin[gi];
         if (ntl == 0) continue;
+        cudaStream_t ls = t->side[nlaunch++ % 3];
         if (t->stages == 2)
-            count_launch(), k_m2l_tc<2><<<ntl * mtiles, TC_THREADS, tc_smem(2), s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
+            count_launch(), k_m2l_tc<2><<<ntl * mtiles, TC_THREADS, tc_smem(2), ls>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
         else
-            count_launch(), k_m2l_tc<3><<<ntl * mtiles, TC_THREADS, tc_smem(3), s>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
+            count_launch(), k_m2l_tc<3><<<ntl * mtiles, TC_THREADS, tc_smem(3), ls>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
         PK_CUDA(cudaGetLastError());
+    }
+    for (int i = 0; i < 3; i++) {
+        PK_CUDA(cudaEventRecord(t->join[i], t->side[i]));
+        PK_CUDA(cudaStreamWaitEvent(s, t->join[i], 0));
     }
     PK_CUDA(cudaEventRecord(t->ev[1], s));
     PK_CUDA(cudaMemcpyAsync(t->err_host, t->err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -111,3 +111,22 @@ def test_mixed_partial_level_grid(cache):
     print(f"partial-level grid: mixed {em:.3e} fp64 {ed:.3e}")
     assert em < 2e-5 and em < 1.5 * ed + 2e-6
     assert rel_l2(um, ud) < 3e-5
+
+
+def test_mixed_box_gather_eight_vectors(cache):
+    """8 density vectors on an adaptive tree (clustered points: levels are
+    sparse, so M2L gathers its sources); with several vectors per box a source
+    box's rows are loaded by one 2D TMA.  Every column matches its
+    single-vector evaluation and the oracle."""
+    n = 20000
+    x, _ = w.clustered_slab(n, seed=28, nclusters=8, sigma=0.05, zlo=0.0, zhi=1.0, kdim=3)
+    _, f = w.stokes_uniform(n, seed=29, nrhs=8)
+    u8 = run(1, 7, x, f, x, p=6, leaf=40, depth=10, precision=1, cache_dir=cache)
+    idx = _sample(n, 200)
+    for r in (0, 3, 7):
+        u1 = run(1, 7, x, f[r], x, p=6, leaf=40, depth=10, precision=1, cache_dir=cache)
+        assert rel_l2(u8[r], u1) < 2e-5
+    ref = oracle.stokes_tp(x, f[0], x[idx])
+    e = rel_l2(u8[0][idx], ref)
+    print(f"box gather nrhs=8: rel_l2 {e:.3e}")
+    assert e < 3e-4  # p = 6
