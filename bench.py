@@ -93,6 +93,8 @@ WORKLOADS = {
     "stokes_dp_slab": dict(kernel=1, periodic=3, n=1 << 22, p=10, leaf=64, depth=12, nrhs=1, sample=128),
     "stokes_tp_batch16": dict(kernel=1, periodic=7, n=1 << 21, p=8, leaf=64, depth=10, nrhs=16, sample=128),
     "laplace_tp_multi": dict(kernel=0, periodic=7, n=256, p=6, leaf=32, depth=10, nrhs=1, sample=32),
+    "stokes_chebyshev": dict(kernel=1, periodic=7, n=97, p=8, leaf=64, depth=12, nrhs=1, sample=128),
+    "stokes_lognormal": dict(kernel=1, periodic=7, n=97 ** 3, p=8, leaf=64, depth=12, nrhs=1, sample=128),
 }
 
 
@@ -111,7 +113,22 @@ def workload(name, n, seed):
     if name == "laplace_tp_multi":
         x, q, off = w.multi_laplace_tp(n, seed=seed)
         return x, q[None, :, None], off, f"{n} problems, N log-uniform in [1024, 65536], neutral U[-1,1] charges"
+    if name in ("stokes_chebyshev", "stokes_lognormal"):
+        # the point sets of the paper's Stokes timing tests, forces U[-0.5, 0.5)^3 with zero net
+        if name == "stokes_chebyshev":
+            x = w.chebyshev_grid(n)
+            desc = f"{n}^3 Chebyshev grid (both ends; on free axes scaled by 1 - 2^-20 into [0, 1))"
+            if PERIODIC_OVERRIDE is not None and PERIODIC_OVERRIDE != 7:
+                x = x * (1.0 - 2.0 ** -20)
+        else:
+            x = w.lognormal_points(n, seed=seed)
+            desc = f"{n} points, each coordinate lognormal(0.2, 0.5) wrapped mod 1"
+        f = w.make_neutral(np.random.default_rng(seed).uniform(-0.5, 0.5, size=(len(x), 3)))
+        return x, f[None], None, desc + ", U[-0.5, 0.5)^3 forces, zero net"
     raise ValueError(name)
+
+
+PERIODIC_OVERRIDE = None  # --periodic for the paper-shaped workloads
 
 
 def oracle_sum(kernel, periodic, x, d, xt):
@@ -140,14 +157,16 @@ def oracle_sample(wl, x, d, off, nsample, rng):
 def workload_name(name, wl, n, p, leaf):
     if name == "laplace_tp_multi":
         return f"laplace_tp_multi_{n}problems_p{p}"
+    if name in ("stokes_chebyshev", "stokes_lognormal"):
+        per = {0: "free", 1: "spx", 2: "spy", 4: "spz", 3: "dpxy", 7: "tp"}[wl["periodic"]]
+        return f"{name}_{per}_N{n ** 3 if name == 'stokes_chebyshev' else n}_p{p}_leaf{leaf}"
     return f"{name}_N{n}_p{p}_leaf{leaf}" + (f"_nrhs{wl['nrhs']}" if wl["nrhs"] > 1 else "")
 
 
-def run_reference(args, rank, world):
+def run_reference(args, rank, world, wl):
     """Reference arm: the FP64 oracle on a bounded target sample per step."""
     if rank != 0:
         return
-    wl = WORKLOADS[args.workload]
     x, d, off, desc = workload(args.workload, args.n, 0)
     rng = np.random.default_rng(123)
     times, ntg = [], 0
@@ -184,8 +203,16 @@ def main():
     ap.add_argument("--sample", type=int, default=None, help="oracle targets for accuracy / cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=64, help="oracle targets per reference step")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison step")
+    ap.add_argument("--periodic", type=int, default=None, choices=[0, 1, 2, 4, 3, 7],
+                    help="periodic axes for stokes_chebyshev / stokes_lognormal (bit 0 = x)")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.periodic is not None:
+        if not args.workload.startswith("stokes_chebyshev") and not args.workload.startswith("stokes_lognormal"):
+            ap.error("--periodic applies to the paper-shaped workloads only")
+        wl["periodic"] = args.periodic
+        global PERIODIC_OVERRIDE
+        PERIODIC_OVERRIDE = args.periodic
     args.n = args.n or wl["n"]
     args.p = args.p or wl["p"]
     args.leaf = args.leaf or wl["leaf"]
@@ -194,7 +221,7 @@ def main():
 
     rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
-        run_reference(args, rank, world)
+        run_reference(args, rank, world, wl)
         return
 
     import torch
