@@ -831,29 +831,22 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
 // (x, y, z) and R x K densities; the image offset of a source box is added to
 // the target once.  Each staged tile is summed in registers and added to the
 // running total with Kahan compensation.
-template <typename T, int K, int NT, int R, int LPB>
-__global__ void __launch_bounds__(NT * LPB) k_leaf(
+template <typename T, int K, int NT, int R, int TPT>
+__global__ void __launch_bounds__(NT) k_leaf(
     const int *__restrict__ leaves, const int4 *__restrict__ bpos, const int2 *__restrict__ srange,
     const int2 *__restrict__ trange, const int *__restrict__ uptr, const int *__restrict__ ubox,
     const unsigned char *__restrict__ ush, const int *__restrict__ wptr, const int *__restrict__ wbox,
     const unsigned char *__restrict__ wsh, const V4<T> *__restrict__ yrel, const V4<T> *__restrict__ xrel,
     const T *__restrict__ dens, const T *__restrict__ up, const T *__restrict__ dn, int nrhs, int rhs0,
-    const T *__restrict__ g, int n, int nleaves, double *__restrict__ pot) {
-    // LPB > 1 (NT = 32): one warp per leaf, each with its own staging tiles
-    static_assert(LPB == 1 || NT == 32, "leaves per block need warp-sized tiles");
-    __shared__ V4<T> sy_all[LPB][NT];
-    __shared__ T sphi_all[LPB][NT][R][K];
-    const int wl = LPB > 1 ? (int)(threadIdx.x >> 5) : 0;
-    const int li = blockIdx.x * LPB + wl;
-    if (li >= nleaves) return;  // whole warps (LPB > 1) or the whole block (LPB = 1)
-    const unsigned tid = LPB > 1 ? (threadIdx.x & 31) : threadIdx.x;
-    V4<T> *sy = sy_all[wl];
-    T(*sphi)[R][K] = sphi_all[wl];
-    auto sync = [] {
-        if constexpr (LPB > 1) __syncwarp();
-        else __syncthreads();
-    };
-    const int b = leaves[li];
+    const T *__restrict__ g, int n, double *__restrict__ pot) {
+    // one block per target leaf; up to TPT targets per thread (NT * TPT per
+    // pass) while more than NT remain, so each staged source serves them all
+    __shared__ V4<T> sy[NT];
+    __shared__ T sphi[NT][R][K];
+    const unsigned tid = threadIdx.x;
+    // one density value per source (Laplace, one vector): it rides in the source's fourth lane
+    constexpr bool PACK = K == 1 && R == 1;
+    const int b = leaves[blockIdx.x];
     const int4 B = bpos[b];
     const T h = (T)exp2i(B.w);
     const int2 tr = trange[b];
@@ -862,38 +855,52 @@ __global__ void __launch_bounds__(NT * LPB) k_leaf(
     auto stage_surface = [&](int j0, T sc, const T *phi) {
         int j = j0 + tid;
         if (j < n) {
-            sy[tid] = V4<T>{sc * g[3 * j], sc * g[3 * j + 1], sc * g[3 * j + 2], (T)0};
+            sy[tid] = V4<T>{sc * g[3 * j], sc * g[3 * j + 1], sc * g[3 * j + 2], PACK ? phi[j] : (T)0};
+            if constexpr (!PACK) {
 #pragma unroll
-            for (int r = 0; r < R; r++)
+                for (int r = 0; r < R; r++)
 #pragma unroll
-                for (int a = 0; a < K; a++)
-                    sphi[tid][r][a] = r < nv ? phi[(long long)r * kn + j * K + a] : (T)0;
+                    for (int a = 0; a < K; a++)
+                        sphi[tid][r][a] = r < nv ? phi[(long long)r * kn + j * K + a] : (T)0;
+            }
         }
     };
-    for (int t0 = tr.x; t0 < tr.y; t0 += NT) {
-        const int t = t0 + tid;
-        T x0 = 0, x1 = 0, x2 = 0;
-        if (t < tr.y) {
-            V4<T> v = xrel[t];
-            x0 = v.x;
-            x1 = v.y;
-            x2 = v.z;
+    // one pass over the sources for NT * Q targets (Q = 1 or 2)
+    auto pass = [&](auto q_tag, int t0) {
+        constexpr int Q = decltype(q_tag)::value;
+        T xs[Q][3];
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            const int t = t0 + (int)tid + q * NT;
+            xs[q][0] = xs[q][1] = xs[q][2] = 0;
+            if (t < tr.y) {
+                V4<T> v = xrel[t];
+                xs[q][0] = v.x;
+                xs[q][1] = v.y;
+                xs[q][2] = v.z;
+            }
         }
-        LeafAcc<T, K, R> L;
-        L.init();
+        LeafAcc<T, K, R> L[Q];
+#pragma unroll
+        for (int q = 0; q < Q; q++) L[q].init();
         // L2T from the downward equivalent surface (edge 2.95 h)
         {
             const T *phi = dn + ((long long)b * nrhs + rhs0) * kn;
             for (int j0 = 0; j0 < n; j0 += NT) {
-                sync();
+                __syncthreads();
                 stage_surface(j0, (T)1.475 * h, phi);
-                sync();
+                __syncthreads();
                 const int m = min(NT, n - j0);
                 for (int jj = 0; jj < m; jj++) {
                     const V4<T> y = sy[jj];
-                    L.template add<false>(x0 - y.x, x1 - y.y, x2 - y.z, sphi[jj]);
+                    const T fw[1][1] = {{y.w}};
+#pragma unroll
+                    for (int q = 0; q < Q; q++)
+                        L[q].template add<false>(xs[q][0] - y.x, xs[q][1] - y.y, xs[q][2] - y.z,
+                                                 PACK ? (const T(*)[K])fw : sphi[jj]);
                 }
-                L.flush();
+#pragma unroll
+                for (int q = 0; q < Q; q++) L[q].flush();
             }
         }
         // W list: upward equivalent surfaces (edge 1.05 h_A) of finer boxes
@@ -903,18 +910,26 @@ __global__ void __launch_bounds__(NT * LPB) k_leaf(
             int4 Ap = bpos[A];
             double off[3];
             centre_offset(B, Ap, sh, off);
-            const T xo0 = x0 + (T)off[0], xo1 = x1 + (T)off[1], xo2 = x2 + (T)off[2];
+            T xo[Q][3];
+#pragma unroll
+            for (int q = 0; q < Q; q++)
+                for (int c = 0; c < 3; c++) xo[q][c] = xs[q][c] + (T)off[c];
             const T *phi = up + ((long long)A * nrhs + rhs0) * kn;
             for (int j0 = 0; j0 < n; j0 += NT) {
-                sync();
+                __syncthreads();
                 stage_surface(j0, (T)(0.525 * exp2i(Ap.w)), phi);
-                sync();
+                __syncthreads();
                 const int m = min(NT, n - j0);
                 for (int jj = 0; jj < m; jj++) {
                     const V4<T> y = sy[jj];
-                    L.template add<false>(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[jj]);
+                    const T fw[1][1] = {{y.w}};
+#pragma unroll
+                    for (int q = 0; q < Q; q++)
+                        L[q].template add<false>(xo[q][0] - y.x, xo[q][1] - y.y, xo[q][2] - y.z,
+                                                 PACK ? (const T(*)[K])fw : sphi[jj]);
                 }
-                L.flush();
+#pragma unroll
+                for (int q = 0; q < Q; q++) L[q].flush();
             }
         }
         // U list: direct sums, periodic images through the shift
@@ -923,36 +938,63 @@ __global__ void __launch_bounds__(NT * LPB) k_leaf(
             decode_shift(ush[e], sh);
             double off[3];
             centre_offset(B, bpos[A], sh, off);
-            const T xo0 = x0 + (T)off[0], xo1 = x1 + (T)off[1], xo2 = x2 + (T)off[2];
+            T xo[Q][3];
+#pragma unroll
+            for (int q = 0; q < Q; q++)
+                for (int c = 0; c < 3; c++) xo[q][c] = xs[q][c] + (T)off[c];
             const int2 rg = srange[A];
             for (int s0 = rg.x; s0 < rg.y; s0 += NT) {
-                sync();
+                __syncthreads();
                 const int sidx = s0 + tid;
                 if (sidx < rg.y) {
-                    sy[tid] = yrel[sidx];
+                    V4<T> v = yrel[sidx];
+                    if constexpr (PACK) {
+                        v.w = dens[(long long)sidx * nrhs + rhs0];
+                    } else {
 #pragma unroll
-                    for (int r = 0; r < R; r++)
+                        for (int r = 0; r < R; r++)
 #pragma unroll
-                        for (int a = 0; a < K; a++)
-                            sphi[tid][r][a] =
-                                r < nv ? dens[(long long)sidx * nrhs * K + (rhs0 + r) * K + a] : (T)0;
+                            for (int a = 0; a < K; a++)
+                                sphi[tid][r][a] =
+                                    r < nv ? dens[(long long)sidx * nrhs * K + (rhs0 + r) * K + a] : (T)0;
+                    }
+                    sy[tid] = v;
                 }
-                sync();
+                __syncthreads();
                 const int m = min(NT, rg.y - s0);
                 for (int j = 0; j < m; j++) {
                     const V4<T> y = sy[j];
-                    L.template add<true>(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
+                    const T fw[1][1] = {{y.w}};
+#pragma unroll
+                    for (int q = 0; q < Q; q++)
+                        L[q].template add<true>(xo[q][0] - y.x, xo[q][1] - y.y, xo[q][2] - y.z,
+                                                PACK ? (const T(*)[K])fw : sphi[j]);
                 }
-                L.flush();
+#pragma unroll
+                for (int q = 0; q < Q; q++) L[q].flush();
             }
         }
-        if (t < tr.y) {
 #pragma unroll
-            for (int r = 0; r < R; r++)
-                if (r < nv)
+        for (int q = 0; q < Q; q++) {
+            const int t = t0 + (int)tid + q * NT;
+            if (t < tr.y) {
 #pragma unroll
-                    for (int a = 0; a < K; a++)
-                        pot[(long long)t * nrhs * K + (rhs0 + r) * K + a] = ((double)L.tot[r][a] - (double)L.cmp[r][a]) * LeafAcc<T, K, R>::kScale;
+                for (int r = 0; r < R; r++)
+                    if (r < nv)
+#pragma unroll
+                        for (int a = 0; a < K; a++)
+                            pot[(long long)t * nrhs * K + (rhs0 + r) * K + a] =
+                                ((double)L[q].tot[r][a] - (double)L[q].cmp[r][a]) * LeafAcc<T, K, R>::kScale;
+            }
+        }
+    };
+    for (int t0 = tr.x; t0 < tr.y;) {
+        if (TPT > 1 && tr.y - t0 > NT) {  // block-uniform: more than NT targets left
+            pass(std::integral_constant<int, TPT>{}, t0);
+            t0 += NT * TPT;
+        } else {
+            pass(std::integral_constant<int, 1>{}, t0);
+            t0 += NT;
         }
     }
 }
@@ -1158,13 +1200,15 @@ static void leaves_t(Plan &P, cudaStream_t s) {
     // hold about s/2 targets); up to 4 density vectors per pass
     auto launch = [&](auto nt_tag, auto r_tag, int r0) {
         constexpr int NT = decltype(nt_tag)::value, R = decltype(r_tag)::value;
-        // one leaf per block: with several leaves per block (one warp each) a
-        // block holds its slot until its slowest leaf is done (measured slower)
-        constexpr int LPB = 1;
-        count_launch(), k_leaf<T, K, NT, R, LPB><<<(P.n_leaves_trg + LPB - 1) / LPB, NT * LPB, 0, s>>>(
+        // one leaf per block (several leaves per block, one warp each, was measured
+        // slower: a block holds its slot until its slowest leaf is done); two
+        // targets per thread for up to two vectors, so a leaf of up to 2 NT
+        // targets takes one pass over its sources
+        constexpr int TPT = R <= 2 ? 2 : 1;
+        count_launch(), k_leaf<T, K, NT, R, TPT><<<P.n_leaves_trg, NT, 0, s>>>(
                 P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
                 P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
-                B::dn(P).p, nr, r0, B::g(P).p, P.n, P.n_leaves_trg, P.pot_s.p);
+                B::dn(P).p, nr, r0, B::g(P).p, P.n, P.pot_s.p);
     };
     auto launch_r = [&](auto nt_tag, int r0) {
         if (nr - r0 == 1) launch(nt_tag, std::integral_constant<int, 1>{}, r0);
