@@ -22,8 +22,12 @@
  *     requires).
  *   - Stokes TP: Hasimoto split (Sec. 3.4): Fourier weight
  *     (1 + k^2/4xi^2) exp(-k^2/4xi^2) (I - k k^T/k^2)/k^2, k = 0 removed
- *     (zero mean flow, Eq. (flowvolume)); the real-space kernel follows from
- *     it in closed form (derivation in the design doc).
+ *     (zero mean flow, Eq. (flowvolume)); the real-space kernel follows in
+ *     closed form: with S = (I lap - grad grad) r the smooth part is
+ *     (I lap - grad grad) B, B' = erf(xi r), B'' = (2 xi/sqrt(pi)) e^{-xi^2 r^2},
+ *     leaving I (erfc(xi r)/r - 2xi/sqrt(pi) e^{-xi^2 r^2})
+ *     + (r r^T/r^2)(erfc(xi r)/r + 2xi/sqrt(pi) e^{-xi^2 r^2}) (over 8 pi) in real
+ *     space and the self term -(4 xi/sqrt(pi))/(8 pi).
  *   - Laplace SP: direct symmetric image sum |n| <= M with a per-pair
  *     regularisation -2 H_M and an Euler-Maclaurin tail (Sec. 3.2 notes the
  *     neutral direct sum converges like 1/n^2); the pair-independent constant
