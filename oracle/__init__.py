@@ -70,6 +70,7 @@ def _load():
             lib.orc_free.argtypes = [i, l, P, P, l, P, P]
             lib.orc_laplace_tp.argtypes = [l, P, P, l, P, d, d, d, i, d, P]
             lib.orc_stokes_tp.argtypes = [l, P, P, l, P, d, d, d, i, d, P]
+            lib.orc_stokes_tp_beenakker.argtypes = [l, P, P, l, P, d, d, d, i, d, P]
             lib.orc_laplace_sp.argtypes = [l, P, P, l, P, i, d, l, P]
             lib.orc_dp.argtypes = [i, l, P, P, l, P, d, d, d, d, d, P]
             lib.orc_stokes_sp.argtypes = [l, P, P, l, P, i, d, l, P]
@@ -129,6 +130,18 @@ def stokes_tp(src, f, trg, L: float = 1.0, xi=None, rc=None) -> np.ndarray:
     y, x, phi = _c(src), _c(trg), _c(f).reshape(-1, 3)
     out = np.zeros((len(x), 3))
     _load().orc_stokes_tp(len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), L, xi, rc, mmax, kc, _ptr(out))
+    return out
+
+
+def stokes_tp_beenakker(src, f, trg, L: float = 1.0, xi=None, rc=None) -> np.ndarray:
+    """Stokes TP by the Beenakker split (a second derivation of the same sum,
+    used to pin the Hasimoto one)."""
+    xi, rc, mmax, kc = ewald_params(xi, rc)
+    kc = 15.0 * xi  # the k^4 weight decays more slowly
+    mmax = int(np.ceil(kc / (2 * np.pi)))
+    y, x, phi = _c(src), _c(trg), _c(f).reshape(-1, 3)
+    out = np.zeros((len(x), 3))
+    _load().orc_stokes_tp_beenakker(len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), L, xi, rc, mmax, kc, _ptr(out))
     return out
 
 

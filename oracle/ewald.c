@@ -193,9 +193,29 @@ void orc_laplace_tp(long S, const double *y, const double *phi, long T, const do
     free(m); free(re); free(im); free(wk);
 }
 
-/* Stokes TP Ewald, Hasimoto split, zero mean flow.  Same parameters. */
+/* Stokes TP Ewald, zero mean flow.  split = 0: Hasimoto (Fourier weight
+ * (1 + a) e^{-a}, a = k^2/4xi^2); split = 1: Beenakker (weight
+ * (1 + a + 2a^2) e^{-a}, i.e. (1 + k^2/4xi^2 + k^4/8xi^4) e^{-k^2/4xi^2}).  The
+ * Beenakker smooth part adds B_x = -e^{-xi^2 r^2}/(8 xi pi^{3/2}) to the
+ * biharmonic potential B (S = (I lap - grad grad) B), which moves
+ * 2 g0 e^{-xi^2 r^2} [I (1 - xi^2 r^2) + r r^T xi^2] / (8 pi) from the real-space
+ * kernel to the smooth part and adds -2 g0/(8 pi) to the self term
+ * (g0 = 2 xi/sqrt(pi)).  Same other parameters. */
+static void stokes_tp_split(long S, const double *y, const double *f, long T, const double *x,
+                            double L, double xi, double rc, int mmax, double kc, int split, double *u);
+
 void orc_stokes_tp(long S, const double *y, const double *f, long T, const double *x,
                    double L, double xi, double rc, int mmax, double kc, double *u) {
+    stokes_tp_split(S, y, f, T, x, L, xi, rc, mmax, kc, 0, u);
+}
+
+void orc_stokes_tp_beenakker(long S, const double *y, const double *f, long T, const double *x,
+                             double L, double xi, double rc, int mmax, double kc, double *u) {
+    stokes_tp_split(S, y, f, T, x, L, xi, rc, mmax, kc, 1, u);
+}
+
+static void stokes_tp_split(long S, const double *y, const double *f, long T, const double *x,
+                            double L, double xi, double rc, int mmax, double kc, int split, double *u) {
     int *m; long nm = half_space_modes(mmax, kc, &m);
     double *re = (double *)malloc(sizeof(double) * nm * 3), *im = (double *)malloc(sizeof(double) * nm * 3);
     structure_factors(S, y, f, 3, L, mmax, nm, m, re, im);
@@ -203,11 +223,11 @@ void orc_stokes_tp(long S, const double *y, const double *f, long T, const doubl
     for (long i = 0; i < nm; i++) {
         double k2 = 4.0 * M_PI * M_PI * (double)(m[3 * i] * m[3 * i] + m[3 * i + 1] * m[3 * i + 1] + m[3 * i + 2] * m[3 * i + 2]);
         double a = k2 / (4.0 * xi * xi);
-        wk[i] = 2.0 * (1.0 + a) * exp(-a) / k2; /* x2: +m and -m; 8 pi / 8 pi = 1 */
+        wk[i] = 2.0 * (1.0 + a + (split ? 2.0 * a * a : 0.0)) * exp(-a) / k2; /* x2: +m and -m; 8 pi / 8 pi = 1 */
     }
     int nr = rc > 0.5 ? (int)ceil(rc - 0.5) : 0;
     double rc2 = rc * rc, c8 = 1.0 / (8.0 * M_PI), g0 = 2.0 * xi / sqrt(M_PI);
-    double self = -c8 * 4.0 * xi / sqrt(M_PI);
+    double self = -c8 * 4.0 * xi / sqrt(M_PI) - (split ? 2.0 * c8 * g0 : 0.0);
 #pragma omp parallel for schedule(dynamic, 4)
     for (long t = 0; t < T; t++) {
         acc_t a[3] = {{0, 0}, {0, 0}, {0, 0}};
@@ -227,6 +247,10 @@ void orc_stokes_tp(long S, const double *y, const double *f, long T, const doubl
                         if (r2 >= rc2) continue;
                         double rr = sqrt(r2), ec = erfc(xi * rr) / rr, ga = g0 * exp(-xi * xi * r2);
                         double cI = ec - ga, cR = (ec + ga) / r2; /* I and r r^T coefficients */
+                        if (split) { /* minus the part that moved to the smooth side */
+                            cI -= 2.0 * ga * (1.0 - xi * xi * r2);
+                            cR -= 2.0 * ga * xi * xi;
+                        }
                         double df = d[0] * fs[0] + d[1] * fs[1] + d[2] * fs[2];
                         for (int i = 0; i < 3; i++) acc_add(&a[i], c8 * (cI * fs[i] + cR * d[i] * df));
                     }

@@ -284,3 +284,21 @@ def test_error_metrics_definitions():
     assert m["max_abs"] == 1.0 and m["mean_abs"] == 0.375
     assert m["rms"] == pytest.approx(math.sqrt(1.25 / 4))
     assert m["rel_l2"] == pytest.approx(math.sqrt(1.25) / math.sqrt(1 + 6.25 + 9 + 9))
+
+
+def test_stokes_tp_hasimoto_matches_beenakker_split():
+    """Two splits of the same triply periodic Stokes sum (Hasimoto's Fourier
+    weight (1 + a) e^{-a}, Beenakker's (1 + a + 2a^2) e^{-a}, a = k^2/4xi^2,
+    each with its own real-space kernel and self term) give the same
+    velocities, with and without a net force."""
+    rng = np.random.default_rng(31)
+    y = rng.random((60, 3))
+    x = rng.random((8, 3))
+    for neutral in (False, True):
+        f = rng.standard_normal((60, 3))
+        if neutral:
+            f -= f.mean(0)
+        h = oracle.stokes_tp(y, f, x)
+        for rc in (0.8, 1.2):
+            b = oracle.stokes_tp_beenakker(y, f, x, rc=rc)
+            assert np.abs(b - h).max() < 1e-13 * np.abs(h).max()
