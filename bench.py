@@ -385,6 +385,7 @@ def main():
                                  stages)),
             "tree": dict(zip(["boxes", "leaves", "depth", "U", "V", "W", "X", "p2p_pairs"], stats)),
             "autotune": tuned,
+            "p2p": p2p_block(kernel, args.p, ntrg, nrhs, stats, stages[6], clocks, pk_),
             "clocks": clocks,
         }
     plan.close()
@@ -393,6 +394,22 @@ def main():
         dist.destroy_process_group()
     if result is not None:
         print(json.dumps(result), flush=True)
+
+
+def p2p_block(kernel, p, ntrg, nrhs, stats, leaves_ms, clocks, pk_):
+    """Leaf stage as kernel-sum throughput: U-list source-target pairs plus the L2T
+    pairs (n surface points per target), per density vector; FMA-pipe operations
+    per pair as the leaf kernel issues them (Stokes 17, Laplace 8, plus one rsqrt);
+    fraction of the FP32 FMA-pipe issue peak (152 SMs x 128 lanes per clock).
+    W-list pairs are not counted (a lower bound)."""
+    n = 6 * (p - 1) ** 2 + 2
+    pairs = (stats[7] + ntrg * n) * nrhs
+    ops = 8 if kernel == 0 else 17
+    mhz = (clocks or {}).get("sm_mhz") or pk_.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * mhz * 1e6
+    rate = pairs / (leaves_ms / 1e3) if leaves_ms > 0 else 0.0
+    return {"pairs": pairs, "leaves_ms": leaves_ms, "pairs_per_s": rate, "fma_pipe_ops_per_pair": ops,
+            "fma_pipe_peak_ops_per_s": peak, "frac": rate * ops / peak}
 
 
 def m2l_traffic(workload_name):

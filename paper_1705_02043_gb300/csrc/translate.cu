@@ -891,6 +891,7 @@ __global__ void __launch_bounds__(NT) k_leaf(
                 stage_surface(j0, (T)1.475 * h, phi);
                 __syncthreads();
                 const int m = min(NT, n - j0);
+#pragma unroll 4
                 for (int jj = 0; jj < m; jj++) {
                     const V4<T> y = sy[jj];
                     const T fw[1][1] = {{y.w}};
@@ -920,6 +921,7 @@ __global__ void __launch_bounds__(NT) k_leaf(
                 stage_surface(j0, (T)(0.525 * exp2i(Ap.w)), phi);
                 __syncthreads();
                 const int m = min(NT, n - j0);
+#pragma unroll 4
                 for (int jj = 0; jj < m; jj++) {
                     const V4<T> y = sy[jj];
                     const T fw[1][1] = {{y.w}};
@@ -962,6 +964,7 @@ __global__ void __launch_bounds__(NT) k_leaf(
                 }
                 __syncthreads();
                 const int m = min(NT, rg.y - s0);
+#pragma unroll 4
                 for (int j = 0; j < m; j++) {
                     const V4<T> y = sy[j];
                     const T fw[1][1] = {{y.w}};
