@@ -199,6 +199,8 @@ def main():
     ap.add_argument("--workload", default="stokes_tp", choices=sorted(WORKLOADS))
     ap.add_argument("--n", type=int, default=None, help="points (problems for laplace_tp_multi)")
     ap.add_argument("--p", type=int, default=None)
+    ap.add_argument("--ell", type=int, default=2, choices=[1, 2, 3],
+                    help="image layers summed directly in the root operator (Sec. 3.6 varies 1..3)")
     ap.add_argument("--leaf", type=int, default=None)
     ap.add_argument("--sample", type=int, default=None, help="oracle targets for accuracy / cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=64, help="oracle targets per reference step")
@@ -243,7 +245,7 @@ def main():
     x, d, off, desc = workload(args.workload, args.n, rank)
     ntrg = len(x)
     cache = os.path.join(ROOT, "_build_cache")
-    plan = pk.PeriodicKIFMM(kernel, periodic, p=args.p, leaf_max=args.leaf, depth_max=wl["depth"],
+    plan = pk.PeriodicKIFMM(kernel, periodic, p=args.p, ell=args.ell, leaf_max=args.leaf, depth_max=wl["depth"],
                             precision=pk.MIXED, nrhs=nrhs, cache_dir=cache)
     tx, td = torch.tensor(x, device=dev), torch.tensor(np.ascontiguousarray(d), device=dev)
     out = torch.empty((nrhs, ntrg, k), dtype=torch.float64, device=dev)
@@ -337,8 +339,8 @@ def main():
         err = __import__("oracle").error_metrics(u[0][idx], ref)
         fp64 = None
         if not args.no_fp64:
-            p64 = pk.PeriodicKIFMM(kernel, periodic, p=args.p, leaf_max=args.leaf, depth_max=wl["depth"],
-                                   precision=pk.FP64, nrhs=nrhs, cache_dir=cache)
+            p64 = pk.PeriodicKIFMM(kernel, periodic, p=args.p, ell=args.ell, leaf_max=args.leaf,
+                                   depth_max=wl["depth"], precision=pk.FP64, nrhs=nrhs, cache_dir=cache)
             o64 = torch.empty_like(out)
 
             def ev64():
@@ -367,7 +369,7 @@ def main():
             "config": {"workload": workload_name(args.workload, wl, args.n, args.p, args.leaf),
                        "kernel": "stokes" if kernel == 1 else "laplace",
                        "periodic": {7: "xyz", 3: "xy", 0: "none"}.get(periodic, str(periodic)),
-                       "N": ntrg, "p": args.p, "leaf_max": args.leaf, "depth_max": wl["depth"], "nrhs": nrhs,
+                       "N": ntrg, "p": args.p, "ell": args.ell, "leaf_max": args.leaf, "depth_max": wl["depth"], "nrhs": nrhs,
                        "problems": 1 if off is None else len(off) - 1,
                        "precision": "mixed", "parallelism": f"{world} independent problems",
                        "l2": "256 MiB buffer written between timed steps"},

@@ -650,6 +650,7 @@ void pkifmm_plan_destroy(pkifmm_plan plan) {
     P.toff.release();
     P.far64.release();
     if (P.stage_h) cudaFreeHost(P.stage_h);
+    if (P.down_h) cudaFreeHost(P.down_h);
     if (P.stage_ev) cudaEventDestroy(P.stage_ev);
     Task *ts[] = {&P.t_uc2e, &P.t_m2l, &P.t_dc2e, &P.t_root};
     for (auto *t : ts) {

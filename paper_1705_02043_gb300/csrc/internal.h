@@ -126,6 +126,8 @@ struct Plan {
     size_t stage_cap = 0;
     cudaEvent_t stage_ev = nullptr;
     bool stage_ev_live = false;
+    char *down_h = nullptr;                     // pinned buffer for the tree read back each evaluation
+    size_t down_cap = 0;
     DBuf<double> far64;                         // roots' downward equivalent densities (step d)
     DBuf<long long> soff, toff;                 // [nprob+1] CSR offsets of their points
     bool same_offsets = true;                   // soff == toff element by element

@@ -291,10 +291,10 @@ static void matvec64(const double *M, const double *x, double *y, int n, int nrh
 
 // ---------------- tasks ----------------
 
-struct HostTree {
-    std::vector<int4> bpos;
-    std::vector<int> child, parent;
-    std::vector<int2> sr, tr;
+struct HostTree {  // views of the tree read back into pinned host memory
+    const int4 *bpos = nullptr;
+    const int *child = nullptr, *parent = nullptr;
+    const int2 *sr = nullptr, *tr = nullptr;
     bool leaf(int b) const {
         for (int c = 0; c < 8; c++)
             if (child[8 * (size_t)b + c] >= 0) return false;
@@ -373,20 +373,34 @@ static void upload_list(DBuf<int> &d, const std::vector<int> &v, Uploads &up) {
 void build_tasks(Plan &P, cudaStream_t s) {
     Tree &t = P.tree;
     int nb = t.nbox;
-    HostTree H;
-    H.bpos.resize(nb);
-    H.child.resize((size_t)nb * 8);
-    H.parent.resize(nb);
-    H.sr.resize(nb);
-    H.tr.resize(nb);
-    std::vector<int> xptr(nb + 1);
-    PK_CUDA(cudaMemcpyAsync(H.bpos.data(), t.bpos.p, sizeof(int4) * nb, cudaMemcpyDeviceToHost, s));
-    PK_CUDA(cudaMemcpyAsync(H.child.data(), t.child.p, sizeof(int) * 8 * (size_t)nb, cudaMemcpyDeviceToHost, s));
-    PK_CUDA(cudaMemcpyAsync(H.parent.data(), t.parent.p, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
-    PK_CUDA(cudaMemcpyAsync(H.sr.data(), t.srange.p, sizeof(int2) * nb, cudaMemcpyDeviceToHost, s));
-    PK_CUDA(cudaMemcpyAsync(H.tr.data(), t.trange.p, sizeof(int2) * nb, cudaMemcpyDeviceToHost, s));
-    PK_CUDA(cudaMemcpyAsync(xptr.data(), t.x_ptr.p, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
+    // the tree comes back through one pinned buffer (pageable copies are staged
+    // by the driver and several times slower)
+    const size_t nbz = (size_t)nb;
+    const size_t b_bpos = 0, b_child = b_bpos + sizeof(int4) * nbz, b_par = b_child + sizeof(int) * 8 * nbz,
+                 b_sr = b_par + sizeof(int) * nbz, b_tr = b_sr + sizeof(int2) * nbz, b_x = b_tr + sizeof(int2) * nbz,
+                 b_end = b_x + sizeof(int) * (nbz + 1);
+    if (P.stage_ev_live) PK_CUDA(cudaEventSynchronize(P.stage_ev));  // uploads of the last evaluation done
+    if (b_end > P.down_cap) {
+        if (P.down_h) PK_CUDA(cudaFreeHost(P.down_h));
+        P.down_h = nullptr;
+        P.down_cap = b_end + b_end / 2;
+        PK_CUDA(cudaHostAlloc(&P.down_h, P.down_cap, cudaHostAllocDefault));
+    }
+    char *dh = P.down_h;
+    PK_CUDA(cudaMemcpyAsync(dh + b_bpos, t.bpos.p, sizeof(int4) * nbz, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaMemcpyAsync(dh + b_child, t.child.p, sizeof(int) * 8 * nbz, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaMemcpyAsync(dh + b_par, t.parent.p, sizeof(int) * nbz, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaMemcpyAsync(dh + b_sr, t.srange.p, sizeof(int2) * nbz, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaMemcpyAsync(dh + b_tr, t.trange.p, sizeof(int2) * nbz, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaMemcpyAsync(dh + b_x, t.x_ptr.p, sizeof(int) * (nbz + 1), cudaMemcpyDeviceToHost, s));
     PK_CUDA(cudaStreamSynchronize(s));
+    HostTree H;
+    H.bpos = (const int4 *)(dh + b_bpos);
+    H.child = (const int *)(dh + b_child);
+    H.parent = (const int *)(dh + b_par);
+    H.sr = (const int2 *)(dh + b_sr);
+    H.tr = (const int2 *)(dh + b_tr);
+    const int *xptr = (const int *)(dh + b_x);
     Uploads up;
     const int nr = P.nrhs;
     std::vector<int> leaves_src, leaves_trg;

@@ -39,7 +39,7 @@ def _oracle_tree(src, trg, periodic, leaf, depth):
     return boxes, keys, lists
 
 
-@pytest.mark.parametrize("periodic", [7, 1, 4, 0])
+@pytest.mark.parametrize("periodic", [7, 3, 1, 4, 0])
 def test_tree_and_lists_bit_exact(periodic):
     trg, _ = w.clustered_slab(400, seed=21, nclusters=4, sigma=0.05, zlo=0.0, zhi=1.0, kdim=1)
     src = w.uniform_points(150, seed=22)
