@@ -190,6 +190,37 @@ def run_reference(args, rank, world, wl):
     }), flush=True)
 
 
+def run_precompute(args, wl, pk):
+    """Stage 1 timing (the precompute of Algorithm 2; Sec. 3.6 tabulates it on CPUs)."""
+    from paper_1705_02043_gb300 import _binding as pkb
+    import torch
+    kernel, periodic = wl["kernel"], wl["periodic"]
+    torch.cuda.init()
+    dev = pkb.pkifmm_precompute_operators(kernel, periodic, args.p, args.ell, pk.MIXED, 1, want_ops=False)
+    dev_s, ph = dev[4], dev[5]
+    host_s = (pkb.pkifmm_precompute_operators(kernel, periodic, args.p, args.ell, pk.MIXED, 0, want_ops=False)[4]
+              if args.precompute_host else None)
+    t0 = time.perf_counter()
+    plan = pk.PeriodicKIFMM(kernel, periodic, p=args.p, ell=args.ell, leaf_max=args.leaf, depth_max=wl["depth"],
+                            precision=pk.MIXED, nrhs=wl["nrhs"], cache_dir=None)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    plan.close()
+    kn = (6 * (args.p - 1) ** 2 + 2) * (1 if kernel == 0 else 3)
+    print(json.dumps({
+        "metric": "Stage 1 precompute time (surface SVD, M2M/L2L, root far-field table), device build",
+        "value": dev_s, "unit": "s", "n_gpus": 1, "higher_is_better": False, "dtype": "f64",
+        "data": "none (operators depend only on kernel, periodicity, p, ell)",
+        "config": {"workload": f"precompute_{'stokes' if kernel else 'laplace'}_per{periodic}_p{args.p}_ell{args.ell}",
+                   "kernel": "stokes" if kernel else "laplace", "periodic": periodic, "p": args.p, "ell": args.ell,
+                   "kn": kn},
+        "device_phases_s": {"svd": ph[0], "m2m_l2l": ph[1], "root_table": ph[2]}, "jacobi_sweeps": int(ph[3]),
+        "host_s": host_s, "host_threads": os.cpu_count() if host_s is not None else None,
+        "plan_create_s": plan_s,
+        "plan_create_covers": "device Stage 1 + the 316 M2L operators + uploads, no cache",
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -205,6 +236,9 @@ def main():
     ap.add_argument("--sample", type=int, default=None, help="oracle targets for accuracy / cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=64, help="oracle targets per reference step")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison step")
+    ap.add_argument("--precompute-host", action="store_true", help="also time Stage 1 built on the host")
+    ap.add_argument("--precompute-only", action="store_true",
+                    help="time Stage 1 alone for the workload's kernel, periodicity, p and ell (one JSON line)")
     ap.add_argument("--periodic", type=int, default=None, choices=[0, 1, 2, 4, 3, 7],
                     help="periodic axes for stokes_chebyshev / stokes_lognormal (bit 0 = x)")
     args = ap.parse_args()
@@ -229,6 +263,10 @@ def main():
     import torch
     import paper_1705_02043_gb300 as pk
     from paper_1705_02043_gb300 import multi
+    if args.precompute_only:
+        if rank == 0:
+            run_precompute(args, wl, pk)
+        return
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -361,6 +399,17 @@ def main():
                     "rel_l2": __import__("oracle").error_metrics(o64.cpu().numpy()[0][idx], ref)["rel_l2"],
                     "stage_ms": p64.stage_times().tolist()}
             p64.close()
+        # Stage 1 (precompute) timed on its own, device build and optionally host build
+        from paper_1705_02043_gb300 import _binding as pkb
+        dev_pre = pkb.pkifmm_precompute_operators(kernel, periodic, args.p, args.ell, pk.MIXED, 1, want_ops=False)
+        pre = {"device_s": dev_pre[4],
+               "device_phases_s": {"svd": dev_pre[5][0], "m2m_l2l": dev_pre[5][1], "root_table": dev_pre[5][2]},
+               "jacobi_sweeps": int(dev_pre[5][3]),
+               "host_s": (pkb.pkifmm_precompute_operators(kernel, periodic, args.p, args.ell, pk.MIXED, 0,
+                                                          want_ops=False)[4] if args.precompute_host else None),
+               "host_threads": os.cpu_count() if args.precompute_host else None,
+               "covers": "surface SVD, M2M/L2L, root far-field table (the M2L operators are formed on the "
+                         "device at plan creation in both builds)"}
         result = {
             "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
@@ -383,6 +432,7 @@ def main():
                                        f"first density vector"},
             "accuracy": {"vs": "FP64 Ewald oracle", "targets": int(len(idx)), "density_vector": 0, **err},
             "fp64_path": fp64,
+            "precompute": pre,
             "stage_ms": dict(zip(["sort", "tree_lists", "upward", "root", "m2l", "downward", "leaves", "total"],
                                  stages)),
             "tree": dict(zip(["boxes", "leaves", "depth", "U", "V", "W", "X", "p2p_pairs"], stats)),

@@ -61,6 +61,10 @@ enum { PKIFMM_LAPLACE = 0, PKIFMM_STOKES = 1 };
  *         sm_103 GPU. */
 enum { PKIFMM_FP64 = 0, PKIFMM_MIXED = 1 };
 
+/* OR-ed into `precision` of pkifmm_plan_create: build Stage 1 on the host
+ * (OpenMP) instead of the device. */
+enum { PKIFMM_PRECOMPUTE_HOST = 0x100 };
+
 enum {
     PKIFMM_OK = 0,
     PKIFMM_ERR_INVALID_ARG = -1,  /* bad argument (sizes, NULL, NaN coordinate) */
@@ -86,11 +90,14 @@ enum {
  *   leaf_max       s: a box splits while it holds more than s sources or
  *                  more than s targets (Sec. 2.2 notation)
  *   depth_max      deepest octree level, 1..16
- *   precision      PKIFMM_FP64 or PKIFMM_MIXED
+ *   precision      PKIFMM_FP64 or PKIFMM_MIXED, optionally | PKIFMM_PRECOMPUTE_HOST
  *   nrhs           density vectors evaluated together on one geometry (>= 1)
  *   cache_dir      directory for the operator cache (NULL: no cache)
- * Runs on the host (SVD, Ewald sums; seconds) and uploads the operators to
- * the current CUDA device.  On success *out owns them. */
+ * Stage 1 runs on the current CUDA device by default (binary64 kernels: the
+ * surface matrices, the one-sided Jacobi SVD, the M2M / L2L products, the
+ * K^{P,F} table of the root operator), or on the host with
+ * PKIFMM_PRECOMPUTE_HOST; both give the same operators up to rounding.  The
+ * operators stay on the current device.  On success *out owns them. */
 int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes,
                        const double box_lo[3], double box_len, int p, int ell,
                        int leaf_max, int depth_max, int precision, int nrhs,
@@ -239,6 +246,27 @@ int pkifmm_root_operator(int kernel, unsigned periodic_axes, int p, int ell, dou
  * for a non-finite coordinate). */
 int pkifmm_morton_order_noalloc(int64_t n, const double *xyz, const double box_lo[3], double box_len,
                                 unsigned periodic_axes, int depth, int32_t *perm, void *cuda_stream);
+
+/* Stage 1 alone (Algorithm 2; Sec. 2.2-2.3, 3.1), without a plan, for
+ * comparing and timing the host (where = 0) and device (where = 1) builds.
+ * kernel, periodic_axes, p, ell, precision as for pkifmm_plan_create (the
+ * precision selects the SVD cut-off: FP64 2^-52 kn, MIXED 1e-7).  Host output
+ * buffers, each may be NULL:
+ *   s_out      [kn]          singular values of the upward check-to-equivalent
+ *                            matrix K(1.475 g, 0.525 g), descending
+ *   m2m_out    [8][kn][kn]   child-octant -> parent upward densities
+ *   l2l_out    [8][kn][kn]   parent -> child-octant downward densities
+ *   root_out   [kn][kn]      root far-field operator (periodic masks only)
+ *   seconds_out              wall time of the build (the device build counts
+ *                            its transfers, not CUDA context creation)
+ *   phases_out [4]           device build only: seconds of the SVD, of the
+ *                            M2M / L2L products, of the root table, then the
+ *                            number of Jacobi sweeps
+ * kn = 6(p-1)^2 + 2 for Laplace, 3 times that for Stokes.  Nothing is cached. */
+int pkifmm_precompute_operators(int kernel, unsigned periodic_axes, int p, int ell,
+                                int precision, int where, double *s_out, double *m2m_out,
+                                double *l2l_out, double *root_out, double *seconds_out,
+                                double *phases_out);
 
 void pkifmm_plan_destroy(pkifmm_plan plan);
 const char *pkifmm_strerror(int code);

@@ -52,6 +52,7 @@ def load_library():
             lib.pkifmm_surface_singular_values.argtypes = [i, i, P]
             lib.pkifmm_backward_error.argtypes = [i, i, P]
             lib.pkifmm_root_operator.argtypes = [i, u, i, i, P]
+            lib.pkifmm_precompute_operators.argtypes = [i, u, i, i, i, i, P, P, P, P, P, P]
             lib.pkifmm_plan_destroy.argtypes = [P]
             lib.pkifmm_plan_destroy.restype = None
             lib.pkifmm_strerror.argtypes = [i]
@@ -80,6 +81,8 @@ def _ptr(a):
         return a.ctypes.data_as(ctypes.c_void_p)
     return ctypes.c_void_p(a.data_ptr())  # torch tensor (device or host)
 
+
+PKIFMM_PRECOMPUTE_HOST = 0x100  # OR-ed into precision: Stage 1 on the host
 
 # ---- C-ABI functions, same names ----
 
@@ -186,6 +189,22 @@ def pkifmm_root_operator(kernel, periodic_axes, p, ell):
     return out
 
 
+def pkifmm_precompute_operators(kernel, periodic_axes, p, ell, precision, where, want_ops=True):
+    """Stage 1 without a plan on the host (where=0) or device (where=1).
+
+    Returns (S [kn], m2m [8,kn,kn] | None, l2l [8,kn,kn] | None, root [kn,kn] | None, seconds,
+    phases [svd_s, m2m_l2l_s, root_s, jacobi_sweeps] of the device build, zeros for the host build)."""
+    kn = (6 * (p - 1) ** 2 + 2) * (1 if kernel == 0 else 3)
+    S = np.zeros(kn)
+    m2m = np.zeros((8, kn, kn)) if want_ops else None
+    l2l = np.zeros((8, kn, kn)) if want_ops else None
+    root = np.zeros((kn, kn)) if (want_ops and periodic_axes) else None
+    sec, ph = np.zeros(1), np.zeros(4)
+    _check(load_library().pkifmm_precompute_operators(kernel, periodic_axes, p, ell, precision, where, _ptr(S),
+                                                      _ptr(m2m), _ptr(l2l), _ptr(root), _ptr(sec), _ptr(ph)))
+    return S, m2m, l2l, root, float(sec[0]), ph
+
+
 def pkifmm_morton_order_noalloc(n, xyz, box_lo, box_len, periodic_axes, depth, perm, stream=None):
     """Allocation-free stable Morton ordering; xyz [n,3] float64 and perm [n] int32 device tensors."""
     lo = np.ascontiguousarray(box_lo, dtype=np.float64)
@@ -214,12 +233,16 @@ class PeriodicKIFMM:
     """Owns a plan; evaluate() passes torch CUDA tensors' device pointers."""
 
     def __init__(self, kernel, periodic_axes, box_lo=(0.0, 0.0, 0.0), box_len=1.0, p=6, ell=2,
-                 leaf_max=64, depth_max=10, precision=0, nrhs=1, cache_dir=None):
+                 leaf_max=64, depth_max=10, precision=0, nrhs=1, cache_dir=None, precompute="device"):
+        """precompute: "device" (Stage 1 in CUDA kernels) or "host" (OpenMP)."""
+        if precompute not in ("device", "host"):
+            raise ValueError("precompute must be 'device' or 'host'")
         self.kernel, self.k, self.nrhs = kernel, (1 if kernel == 0 else 3), nrhs
         self.n = 6 * (p - 1) ** 2 + 2
         self.kn = self.n * self.k
+        flags = PKIFMM_PRECOMPUTE_HOST if precompute == "host" else 0
         self.handle = pkifmm_plan_create(kernel, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max,
-                                         precision, nrhs, cache_dir)
+                                         precision | flags, nrhs, cache_dir)
 
     def evaluate(self, src, dens, trg, pot=None, stream=None):
         """src [S,3], dens [nrhs,S,k], trg [T,3] float64 CUDA tensors -> pot [nrhs,T,k]."""

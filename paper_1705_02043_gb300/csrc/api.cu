@@ -248,6 +248,8 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, con
                        const char *cache_dir) {
     if (!out) return fail(PKIFMM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
+    const bool host_stage1 = (precision & PKIFMM_PRECOMPUTE_HOST) != 0;
+    precision &= ~PKIFMM_PRECOMPUTE_HOST;
     if (kernel != PKIFMM_LAPLACE && kernel != PKIFMM_STOKES) return fail(PKIFMM_ERR_INVALID_ARG, "kernel");
     if (periodic_axes > 7) return fail(PKIFMM_ERR_INVALID_ARG, "periodic_axes");
     if (!box_lo || !(box_len > 0) || !std::isfinite(box_len)) return fail(PKIFMM_ERR_INVALID_ARG, "box");
@@ -281,7 +283,8 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, con
             // the oracle (binary32 operators; see the tests).
             double eps = precision == PKIFMM_FP64 ? std::ldexp(1.0, -52) * P.kn : 1e-7;
             if (const char *e = std::getenv("PKIFMM_EPS_MIXED"); e && precision == PKIFMM_MIXED) eps = std::atof(e);
-            build_host_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
+            if (host_stage1) build_host_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
+            else build_device_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
             upload_operators(P);
             for (auto &e : P.ev) PK_CUDA(cudaEventCreate(&e));
             P.events = true;
@@ -608,6 +611,34 @@ int pkifmm_root_operator(int kernel, unsigned periodic_axes, int p, int ell, dou
     return guarded([&]() {
         auto M = root_operator(kernel, p, periodic_axes, ell, surface_grid(p));
         std::copy(M.begin(), M.end(), m_out);
+        return PKIFMM_OK;
+    });
+}
+
+int pkifmm_precompute_operators(int kernel, unsigned periodic_axes, int p, int ell, int precision, int where,
+                                double *s_out, double *m2m_out, double *l2l_out, double *root_out,
+                                double *seconds_out, double *phases_out) {
+    bool sp = periodic_axes == 1 || periodic_axes == 2 || periodic_axes == 4;
+    if ((kernel != 0 && kernel != 1) || p < 4 || p > 16 || ell < 1 || ell > 8 || (where != 0 && where != 1) ||
+        (precision != PKIFMM_FP64 && precision != PKIFMM_MIXED))
+        return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
+    if (!(periodic_axes == 0 || periodic_axes == 7 || periodic_axes == 3 || sp))
+        return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built");
+    return guarded([&]() {
+        HostOps o;
+        const int kn = surface_count(p) * (kernel ? 3 : 1);
+        const double eps = precision == PKIFMM_FP64 ? std::ldexp(1.0, -52) * kn : 1e-7;
+        if (where == 1) PK_CUDA(cudaFree(nullptr));  // context creation outside the timed build
+        const auto t0 = std::chrono::steady_clock::now();
+        if (where == 0) build_host_ops(o, kernel, p, periodic_axes, ell, eps, "");
+        else build_device_ops(o, kernel, p, periodic_axes, ell, eps, "", phases_out);
+        const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        const size_t kn2 = (size_t)kn * kn;
+        if (s_out) std::copy(o.S.begin(), o.S.end(), s_out);
+        if (m2m_out) std::copy(o.m2m.begin(), o.m2m.begin() + 8 * kn2, m2m_out);
+        if (l2l_out) std::copy(o.l2l.begin(), o.l2l.begin() + 8 * kn2, l2l_out);
+        if (root_out && periodic_axes) std::copy(o.root.begin(), o.root.end(), root_out);
+        if (seconds_out) *seconds_out = sec;
         return PKIFMM_OK;
     });
 }

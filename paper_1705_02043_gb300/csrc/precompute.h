@@ -43,6 +43,14 @@ struct HostOps {
     std::vector<double> root;       // [kn][kn] far-field check operator (periodic)
 };
 
+// Pieces shared by the host and device builds: field set-up and surface grid;
+// the operator cache (false / no-op for an empty directory); the
+// check-to-equivalent factors (V S+, U^T, U S+, V^T) from U, S, V and eps_rel.
+void init_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell, double eps_rel);
+bool load_cached_ops(HostOps &o, const std::string &cache_dir);
+void save_cached_ops(HostOps &o, const std::string &cache_dir);
+void c2e_factors(HostOps &o);
+
 // Build all host operators; throws std::runtime_error on failure.
 // cache_dir may be empty.
 void build_host_ops(HostOps &ops, int kernel, int p, unsigned periodic, int ell,
@@ -57,5 +65,15 @@ std::vector<double> root_operator(int kernel, int p, unsigned periodic, int ell,
                                   const std::vector<double> &g);
 
 void matmul(int m, int n, int kk, const double *A, const double *B, double *C);  // C = A B
+
+// The same operators built on the current CUDA device (precompute_dev.cu):
+// surface kernel matrices, the one-sided Jacobi SVD, the M2M / L2L products
+// and the root operator's far-field table in binary64 kernels; U, S, V and
+// the operators are copied back into `ops`.  Throws pk::Error on failure.
+// phases (may be null, 4 entries): seconds of the SVD, the M2M / L2L products
+// and the root table, then the number of Jacobi sweeps (the last one rotating
+// nothing); left untouched when the operators come from the cache.
+void build_device_ops(HostOps &ops, int kernel, int p, unsigned periodic, int ell,
+                      double eps_rel, const std::string &cache_dir, double *phases = nullptr);
 
 }  // namespace pk

@@ -6,7 +6,7 @@ import paper_1705_02043_gb300 as pk
 
 
 def run(kernel, periodic, src, dens, trg, p=6, leaf=32, depth=10, precision=0, ell=2,
-        lo=(0.0, 0.0, 0.0), L=1.0, cache_dir=None, return_plan=False):
+        lo=(0.0, 0.0, 0.0), L=1.0, cache_dir=None, return_plan=False, precompute="device"):
     """Evaluate on cuda:0; dens [S] / [S,3] / [nrhs,S,k]; returns numpy [nrhs?,T,k?]."""
     import torch
     k = 1 if kernel == 0 else 3
@@ -14,7 +14,8 @@ def run(kernel, periodic, src, dens, trg, p=6, leaf=32, depth=10, precision=0, e
     squeeze = d.ndim == (1 if k == 1 else 2)
     d = d.reshape(-1, len(src), k)
     nrhs = d.shape[0]
-    plan = pk.PeriodicKIFMM(kernel, periodic, lo, L, p, ell, leaf, depth, precision, nrhs, cache_dir)
+    plan = pk.PeriodicKIFMM(kernel, periodic, lo, L, p, ell, leaf, depth, precision, nrhs, cache_dir,
+                            precompute=precompute)
     dev = torch.device("cuda:0")
     ts = torch.tensor(np.asarray(src, np.float64), device=dev).contiguous()
     td = torch.tensor(d, device=dev).contiguous()

@@ -173,3 +173,21 @@ def test_unsupported_and_invalid_arguments():
         pk.pkifmm_root_operator(0, 7, 1, 2)
     assert e.value.name == "INVALID_ARG"
     assert pk.pkifmm_strerror(-3).startswith("compatibility")
+
+
+def test_precompute_entry_host_build():
+    # the plan-free Stage 1 entry point on the host: the same root operator as
+    # pkifmm_root_operator, singular values of Table 1's matrix, argument checks
+    from paper_1705_02043_gb300 import _binding as b
+    S, m2m, l2l, root, sec, _ = b.pkifmm_precompute_operators(1, 7, 5, 2, pk.FP64, 0)
+    assert sec > 0 and m2m.shape == (8, 294, 294) and l2l.shape == (8, 294, 294)
+    np.testing.assert_array_equal(root, b.pkifmm_root_operator(1, 7, 5, 2))
+    ref = np.zeros(294)
+    pk.load_library().pkifmm_surface_singular_values(1, 5, ref.ctypes.data_as(ctypes.c_void_p))
+    assert np.all(np.diff(S) <= 0) and np.abs(S - ref).max() <= 1e-13 * S[0]
+    S0, _, _, root0, _, _ = b.pkifmm_precompute_operators(0, 0, 5, 2, pk.FP64, 0, want_ops=False)
+    assert root0 is None and len(S0) == 98
+    with pytest.raises(pk.PKIFMMError):
+        b.pkifmm_precompute_operators(0, 7, 5, 2, pk.FP64, 2)
+    with pytest.raises(pk.PKIFMMError):
+        b.pkifmm_precompute_operators(0, 5, 5, 2, pk.FP64, 0)
