@@ -25,6 +25,15 @@ are made absolutely convergent with the conventions that fix the result
   modes by the trapezoid rule in k_z, the k_par = 0 term in closed form
   (requires neutral charges / zero net in-plane force).
 
+Derived quantities (the paper names the Stokes pressure kernel, R^3 -> R,
+beside the velocity kernel):
+
+* Laplace field: the gradient of each of the sums above at the target, term
+  by term (``laplace_gradient``, ``laplace_field``);
+* Stokes pressure p = f.r/(4 pi r^3) (mu = 1), summed as -(1/4 pi) div of the
+  periodic Laplace potentials of the three force components
+  (``stokes_pressure``; zero net force).
+
 Functions with no closed-form or brute-force pin say so in their docstring
 ("parity unpinned").
 """
@@ -74,6 +83,10 @@ def _load():
             lib.orc_laplace_sp.argtypes = [l, P, P, l, P, i, d, l, P]
             lib.orc_dp.argtypes = [i, l, P, P, l, P, d, d, d, d, d, P]
             lib.orc_stokes_sp.argtypes = [l, P, P, l, P, i, d, l, P]
+            lib.orc_laplace_grad_free.argtypes = [l, P, P, l, P, P]
+            lib.orc_laplace_tp_grad.argtypes = [l, P, P, l, P, d, d, d, i, d, P]
+            lib.orc_laplace_dp_grad.argtypes = [l, P, P, l, P, d, d, d, d, d, P]
+            lib.orc_laplace_sp_grad.argtypes = [l, P, P, l, P, i, d, l, P]
             _lib = lib
     return _lib
 
@@ -204,6 +217,47 @@ def periodic_sum(kernel: int, periodic_axes: int, src, dens, trg, L: float = 1.0
         ax = {1: 0, 2: 1, 4: 2}[periodic_axes]
         return laplace_sp(src, dens, trg, axis=ax, L=L) if kernel == LAPLACE else stokes_sp(src, dens, trg, ax, L)
     raise NotImplementedError(f"oracle: kernel {kernel} periodicity {periodic_axes}")
+
+
+def laplace_gradient(periodic_axes: int, src, q, trg, L: float = 1.0, xi=None, rc=None, M: int = 200) -> np.ndarray:
+    """Gradient at the targets of the periodic Laplace potential of
+    ``periodic_sum(LAPLACE, ...)``: each term of the same sums differentiated
+    with respect to the target.  Returns [T][3]."""
+    y, x, phi = _c(src), _c(trg), _c(q)
+    out = np.zeros((len(x), 3))
+    lib = _load()
+    if periodic_axes == 0:
+        lib.orc_laplace_grad_free(len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), _ptr(out))
+    elif periodic_axes == 7:
+        xi, rc, mmax, kc = ewald_params(xi, rc)
+        lib.orc_laplace_tp_grad(len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), L, xi, rc, mmax, kc, _ptr(out))
+    elif periodic_axes == 3:
+        xi, rc, _, kc = ewald_params(xi, rc)
+        zs = np.concatenate([y[:, 2], x[:, 2]]) if len(y) + len(x) else np.zeros(1)
+        H = (zs.max() - zs.min()) / L + 8.0
+        lib.orc_laplace_dp_grad(len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), L, xi, rc, kc, H, _ptr(out))
+    elif periodic_axes in (1, 2, 4):
+        ax = {1: 0, 2: 1, 4: 2}[periodic_axes]
+        lib.orc_laplace_sp_grad(len(y), _ptr(y), _ptr(phi), len(x), _ptr(x), ax, L, M, _ptr(out))
+    else:
+        raise NotImplementedError(f"oracle: Laplace gradient, periodicity {periodic_axes}")
+    return out
+
+
+def laplace_field(periodic_axes: int, src, q, trg, L: float = 1.0) -> np.ndarray:
+    """Potential and its gradient at the targets, [T][4] = (phi, d/dx, d/dy, d/dz)."""
+    return np.concatenate([periodic_sum(LAPLACE, periodic_axes, src, q, trg, L)[:, None],
+                           laplace_gradient(periodic_axes, src, q, trg, L)], axis=1)
+
+
+def stokes_pressure(periodic_axes: int, src, f, trg, L: float = 1.0) -> np.ndarray:
+    """Pressure of the Stokeslets (mu = 1): p = f.r/(4 pi r^3) per source,
+    i.e. p = -(1/4 pi) div Phi with Phi_a the Laplace (1/r) potential of the
+    charges f_a; periodic sums through the periodic Laplace gradient (zero
+    net force makes each f_a neutral).  Returns [T]."""
+    f = _c(f).reshape(-1, 3)
+    div = sum(laplace_gradient(periodic_axes, src, f[:, a], trg, L)[:, a] for a in range(3))
+    return -div / (4.0 * np.pi)
 
 
 def error_metrics(u, ref) -> dict:

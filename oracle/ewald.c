@@ -1,7 +1,7 @@
 /*
  * Oracle (test infrastructure only): plain FP64 periodic sums of the Laplace
  * and Stokes-velocity kernels, Eq. (pfmmDef) of Sec. 2.2 with the kernels of
- * Eq. (kexamples), Sec. 2.4.  Only tests/, the smoke check and the CPU
+ * Eq. (kexamples), Sec. 2.4, and of the Laplace field (gradient) at the end.  Only tests/, the smoke check and the CPU
  * baseline leg of the benchmark may call this code.  It shares nothing with
  * the CUDA library: it is written from the textbook definitions, with no
  * blocking, fusion or reordering beyond what those definitions state.
@@ -559,5 +559,175 @@ void orc_stokes_sp(long S, const double *y, const double *f, long T, const doubl
                 for (int j = 0; j < 3; j++) acc_add(&a[i], G[3 * i + j] * f[3 * s + j]);
         }
         for (int c = 0; c < 3; c++) u[3 * t + c] = acc_get(&a[c]) / L;
+    }
+}
+
+/* ---------- Laplace field: the gradient of the potential at the target ----------
+ * Each periodic sum above is differentiated term by term with respect to the
+ * target position (the sums converge uniformly away from the sources):
+ *   free space       grad (1/r) = -r / r^3;
+ *   real-space term  erfc(xi r)/r -> -(erfc(xi r) + g0 r e^{-xi^2 r^2}) r / r^3,
+ *                    g0 = 2 xi/sqrt(pi); the self term is a constant;
+ *   Fourier term     w (Re F cos th - Im F sin th), th = k.x
+ *                    -> -w k (Re F sin th + Im F cos th);
+ *   DP k_par = 0     d/dz of 4 pi [-(z/2) erf(xi z) - e^{-xi^2 z^2}/(2 xi sqrt(pi))]
+ *                    = -2 pi erf(xi z);
+ *   SP               the image sum term by term, and the Euler-Maclaurin tail
+ *                    (integral + g/2 - g'/12) differentiated in closed form in the
+ *                    axial offset a and the perpendicular offset rho.
+ * Output g[T][3]: unit-cell gradients divided by L^2 (physical units). */
+
+void orc_laplace_grad_free(long S, const double *y, const double *phi, long T, const double *x, double *g) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long t = 0; t < T; t++) {
+        acc_t a[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (long s = 0; s < S; s++) {
+            double d[3] = {x[3 * t] - y[3 * s], x[3 * t + 1] - y[3 * s + 1], x[3 * t + 2] - y[3 * s + 2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 == 0.0) continue;
+            double ir3 = 1.0 / (r2 * sqrt(r2));
+            for (int c = 0; c < 3; c++) acc_add(&a[c], -phi[s] * d[c] * ir3);
+        }
+        for (int c = 0; c < 3; c++) g[3 * t + c] = acc_get(&a[c]);
+    }
+}
+
+void orc_laplace_tp_grad(long S, const double *y, const double *phi, long T, const double *x,
+                         double L, double xi, double rc, int mmax, double kc, double *g) {
+    int *m; long nm = half_space_modes(mmax, kc, &m);
+    double *re = (double *)malloc(sizeof(double) * nm), *im = (double *)malloc(sizeof(double) * nm);
+    structure_factors(S, y, phi, 1, L, mmax, nm, m, re, im);
+    double *wk = (double *)malloc(sizeof(double) * nm);
+    for (long i = 0; i < nm; i++) {
+        double k2 = 4.0 * M_PI * M_PI * (double)(m[3 * i] * m[3 * i] + m[3 * i + 1] * m[3 * i + 1] + m[3 * i + 2] * m[3 * i + 2]);
+        wk[i] = 2.0 * (4.0 * M_PI) * exp(-k2 / (4.0 * xi * xi)) / k2;
+    }
+    int nr = rc > 0.5 ? (int)ceil(rc - 0.5) : 0;
+    double rc2 = rc * rc, g0 = 2.0 * xi / sqrt(M_PI);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long t = 0; t < T; t++) {
+        acc_t a[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (long s = 0; s < S; s++) {
+            double r[3];
+            for (int c = 0; c < 3; c++) { r[c] = (x[3 * t + c] - y[3 * s + c]) / L; r[c] -= floor(r[c] + 0.5); }
+            for (int n0 = -nr; n0 <= nr; n0++)
+                for (int n1 = -nr; n1 <= nr; n1++)
+                    for (int n2 = -nr; n2 <= nr; n2++) {
+                        double d[3] = {r[0] + n0, r[1] + n1, r[2] + n2};
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (r2 == 0.0 || r2 >= rc2) continue;
+                        double rr = sqrt(r2);
+                        double cf = -(erfc(xi * rr) + g0 * rr * exp(-xi * xi * r2)) / (r2 * rr);
+                        for (int c = 0; c < 3; c++) acc_add(&a[c], cf * d[c] * phi[s]);
+                    }
+        }
+        for (long i = 0; i < nm; i++) {
+            double th = 2.0 * M_PI * (m[3 * i] * x[3 * t] + m[3 * i + 1] * x[3 * t + 1] + m[3 * i + 2] * x[3 * t + 2]) / L;
+            double v = -wk[i] * (re[i] * sin(th) + im[i] * cos(th));
+            for (int c = 0; c < 3; c++) acc_add(&a[c], v * 2.0 * M_PI * m[3 * i + c]);
+        }
+        for (int c = 0; c < 3; c++) g[3 * t + c] = acc_get(&a[c]) / (L * L);
+    }
+    free(m); free(re); free(im); free(wk);
+}
+
+void orc_laplace_dp_grad(long S, const double *y, const double *phi, long T, const double *x,
+                         double L, double xi, double rc, double kc, double H, double *g) {
+    int mm[3] = {(int)ceil(kc / (2.0 * M_PI)), (int)ceil(kc / (2.0 * M_PI)), (int)ceil(kc * H / (2.0 * M_PI))};
+    double P[3] = {1.0, 1.0, H};
+    long cap = (long)(2 * mm[0] + 1) * (2 * mm[1] + 1) * (mm[2] + 1), nm = 0;
+    int *m = (int *)malloc(sizeof(int) * 3 * cap);
+    for (int mz = 0; mz <= mm[2]; mz++)
+        for (int my = -mm[1]; my <= mm[1]; my++)
+            for (int mx = -mm[0]; mx <= mm[0]; mx++) {
+                if (mx == 0 && my == 0) continue;
+                if (mz == 0 && (my < 0 || (my == 0 && mx <= 0))) continue;
+                double kx = 2.0 * M_PI * mx, ky = 2.0 * M_PI * my, kz = 2.0 * M_PI * mz / H;
+                if (kx * kx + ky * ky + kz * kz >= kc * kc) continue;
+                m[3 * nm] = mx; m[3 * nm + 1] = my; m[3 * nm + 2] = mz; nm++;
+            }
+    double *re = (double *)malloc(sizeof(double) * (nm ? nm : 1));
+    double *im = (double *)malloc(sizeof(double) * (nm ? nm : 1));
+    structure_factors_box(S, y, phi, 1, L, mm, P, nm, m, re, im);
+    int nr = rc > 0.5 ? (int)ceil(rc - 0.5) : 0;
+    double rc2 = rc * rc, g0 = 2.0 * xi / sqrt(M_PI);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long t = 0; t < T; t++) {
+        acc_t a[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (long s = 0; s < S; s++) {
+            double r[3];
+            for (int c = 0; c < 3; c++) r[c] = (x[3 * t + c] - y[3 * s + c]) / L;
+            for (int c = 0; c < 2; c++) r[c] -= floor(r[c] + 0.5);
+            for (int n0 = -nr; n0 <= nr; n0++)
+                for (int n1 = -nr; n1 <= nr; n1++) {
+                    double d[3] = {r[0] + n0, r[1] + n1, r[2]};
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 == 0.0 || r2 >= rc2) continue;
+                    double rr = sqrt(r2);
+                    double cf = -(erfc(xi * rr) + g0 * rr * exp(-xi * xi * r2)) / (r2 * rr);
+                    for (int c = 0; c < 3; c++) acc_add(&a[c], cf * d[c] * phi[s]);
+                }
+            acc_add(&a[2], -2.0 * M_PI * erf(xi * r[2]) * phi[s]); /* k_par = 0 term */
+        }
+        for (long i = 0; i < nm; i++) {
+            double k[3] = {2.0 * M_PI * m[3 * i], 2.0 * M_PI * m[3 * i + 1], 2.0 * M_PI * m[3 * i + 2] / H};
+            double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+            double th = (k[0] * x[3 * t] + k[1] * x[3 * t + 1] + k[2] * x[3 * t + 2]) / L;
+            double wk = 2.0 * 4.0 * M_PI / H * exp(-k2 / (4.0 * xi * xi)) / k2;
+            double v = -wk * (re[i] * sin(th) + im[i] * cos(th));
+            for (int c = 0; c < 3; c++) acc_add(&a[c], v * k[c]);
+        }
+        for (int c = 0; c < 3; c++) g[3 * t + c] = acc_get(&a[c]) / (L * L);
+    }
+    free(m); free(re); free(im);
+}
+
+/* gradient of the regularised 1D image sum of one pair (see sp_pair):
+ * out[0] = d/da, out[1 + c] = d/d rho_c for the perpendicular offsets */
+static void sp_pair_grad(double a, const double rho[2], long M, double out[3]) {
+    acc_t s[3] = {{0, 0}, {0, 0}, {0, 0}};
+    double rho2 = rho[0] * rho[0] + rho[1] * rho[1];
+    for (long n = -M; n <= M; n++) {
+        double z = a + (double)n, r2 = z * z + rho2;
+        if (r2 == 0.0) continue;
+        double ir3 = 1.0 / (r2 * sqrt(r2));
+        acc_add(&s[0], -z * ir3);
+        acc_add(&s[1], -rho[0] * ir3);
+        acc_add(&s[2], -rho[1] * ir3);
+    }
+    double n0 = (double)(M + 1);
+    double zp = n0 + a, zm = n0 - a;
+    double Rp = sqrt(zp * zp + rho2), Rm = sqrt(zm * zm + rho2);
+    double Rp3 = Rp * Rp * Rp, Rm3 = Rm * Rm * Rm, Rp5 = Rp3 * Rp * Rp, Rm5 = Rm3 * Rm * Rm;
+    /* integral I = -ln((zp+Rp)/2n0) - ln((zm+Rm)/2n0) */
+    double dI_a = -1.0 / Rp + 1.0 / Rm;
+    double bI = 1.0 / (Rp * (zp + Rp)) + 1.0 / (Rm * (zm + Rm));
+    /* g = 1/Rp + 1/Rm - 2/n0 */
+    double dg_a = -zp / Rp3 + zm / Rm3;
+    double bg = 1.0 / Rp3 + 1.0 / Rm3;
+    /* g' = -zp/Rp^3 - zm/Rm^3 + 2/n0^2 */
+    double dgp_a = -1.0 / Rp3 + 3.0 * zp * zp / Rp5 + 1.0 / Rm3 - 3.0 * zm * zm / Rm5;
+    double bgp = 3.0 * zp / Rp5 + 3.0 * zm / Rm5;
+    acc_add(&s[0], dI_a + 0.5 * dg_a - dgp_a / 12.0);
+    for (int c = 0; c < 2; c++) acc_add(&s[1 + c], rho[c] * (-bI - 0.5 * bg - bgp / 12.0));
+    for (int c = 0; c < 3; c++) out[c] = acc_get(&s[c]);
+}
+
+void orc_laplace_sp_grad(long S, const double *y, const double *phi, long T, const double *x,
+                         int axis, double L, long M, double *g) {
+    int p0 = axis == 0 ? 1 : 0, p1 = axis == 2 ? 1 : 2;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long t = 0; t < T; t++) {
+        acc_t a[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (long s = 0; s < S; s++) {
+            double r[3];
+            for (int c = 0; c < 3; c++) r[c] = (x[3 * t + c] - y[3 * s + c]) / L;
+            double ax = r[axis] - floor(r[axis] + 0.5), rho[2] = {r[p0], r[p1]}, d[3];
+            sp_pair_grad(ax, rho, M, d);
+            acc_add(&a[axis], phi[s] * d[0]);
+            acc_add(&a[p0], phi[s] * d[1]);
+            acc_add(&a[p1], phi[s] * d[2]);
+        }
+        for (int c = 0; c < 3; c++) g[3 * t + c] = acc_get(&a[c]) / (L * L);
     }
 }
