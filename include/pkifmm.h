@@ -48,8 +48,26 @@ extern "C" {
 
 typedef struct pkifmm_plan_s *pkifmm_plan;
 
-/* Kernels, Eq. (kexamples): source/target dimension k = 1 and 3 (Sec. 2.3). */
-enum { PKIFMM_LAPLACE = 0, PKIFMM_STOKES = 1 };
+/* Kernels, Eq. (kexamples): source/target dimension k = 1 and 3 (Sec. 2.3).
+ * Two more target quantities (Sec. 2.3 names kernels whose source and target
+ * dimensions differ, e.g. the Stokes pressure kernel R^3 -> R):
+ *   PKIFMM_LAPLACE_FIELD   Laplace charges (k_s = 1); each target receives
+ *                          k_t = 4 values: the potential and its gradient
+ *                          (d/dx, d/dy, d/dz) with respect to the target.  The
+ *                          translations are those of the Laplace kernel; only
+ *                          the target evaluations differ.
+ *   PKIFMM_STOKES_PRESSURE Stokes forces (k_s = 3); each target receives
+ *                          k_t = 4 values: the velocity and the pressure
+ *                          p = sum f.r/(4 pi r^3) (viscosity 1), the pressure
+ *                          summed as -(1/4 pi) div of the Laplace potentials
+ *                          of the three force components (a second, Laplace
+ *                          field evaluation on 3 nrhs charge vectors inside the
+ *                          same call).  Needs zero net force for every
+ *                          periodicity (each force component is a neutral
+ *                          charge distribution); TP pressure has zero mean.
+ * Densities are [nrhs][S][k_s], potentials [nrhs][T][k_t]; k_s = k_t = k for
+ * PKIFMM_LAPLACE and PKIFMM_STOKES. */
+enum { PKIFMM_LAPLACE = 0, PKIFMM_STOKES = 1, PKIFMM_LAPLACE_FIELD = 2, PKIFMM_STOKES_PRESSURE = 3 };
 
 /* Arithmetic of the evaluation:
  * FP64  — every stage in binary64 (accuracy reference path);
@@ -106,9 +124,9 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes,
 /* Evaluate potentials (Algorithm 2, Stage 2) on `cuda_stream` (a
  * cudaStream_t, NULL = legacy default stream).  Device pointers:
  *   src_xyz [S][3]            source positions
- *   dens    [nrhs][S][k]      source densities phi
+ *   dens    [nrhs][S][k_s]    source densities phi
  *   trg_xyz [T][3]            target positions (may equal src_xyz)
- *   pot     [nrhs][T][k]      output potentials q, overwritten
+ *   pot     [nrhs][T][k_t]    output potentials q, overwritten
  * Positions along periodic axes may lie anywhere (they are wrapped); along
  * free axes they must lie in [lo, lo+L).  S, T >= 0 (S = 0 or T = 0 gives
  * zeros).  The call synchronises with the stream a few times while it sizes
@@ -133,7 +151,7 @@ int pkifmm_evaluate_host(pkifmm_plan plan, int64_t S, const double *src_xyz,
  *                     T = trg_off[nprob]
  *   src_xyz, dens, trg_xyz, pot  DEVICE arrays laid out as in
  *                     pkifmm_evaluate for S sources and T targets
- *                     (dens [nrhs][S][k], pot [nrhs][T][k]).
+ *                     (dens [nrhs][S][k_s], pot [nrhs][T][k_t]).
  * All problems are evaluated together: one forest with one root per
  * problem (problem index above the Morton key), every stage one pass over
  * all problems' boxes; no interaction crosses problems.  The compatibility

@@ -7,6 +7,7 @@ if it is missing.
 """
 
 LAPLACE, STOKES = 0, 1
+LAPLACE_FIELD, STOKES_PRESSURE = 2, 3  # targets get (potential, gradient) / (velocity, pressure)
 FP64, MIXED = 0, 1
 FAR_L2L, FAR_DIRECT = 0, 1
 

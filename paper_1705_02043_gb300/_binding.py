@@ -237,7 +237,10 @@ class PeriodicKIFMM:
         """precompute: "device" (Stage 1 in CUDA kernels) or "host" (OpenMP)."""
         if precompute not in ("device", "host"):
             raise ValueError("precompute must be 'device' or 'host'")
-        self.kernel, self.k, self.nrhs = kernel, (1 if kernel == 0 else 3), nrhs
+        # k: source density components; kt: target components
+        self.kernel, self.nrhs = kernel, nrhs
+        self.k = 1 if kernel in (0, 2) else 3
+        self.kt = {0: 1, 1: 3, 2: 4, 3: 4}.get(kernel, 1)
         self.n = 6 * (p - 1) ** 2 + 2
         self.kn = self.n * self.k
         flags = PKIFMM_PRECOMPUTE_HOST if precompute == "host" else 0
@@ -252,7 +255,7 @@ class PeriodicKIFMM:
             if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
                 raise ValueError("inputs must be contiguous float64 CUDA tensors")
         if pot is None:
-            pot = torch.empty((self.nrhs, T, self.k), dtype=torch.float64, device=src.device)
+            pot = torch.empty((self.nrhs, T, self.kt), dtype=torch.float64, device=src.device)
         if stream is None:
             stream = torch.cuda.current_stream(src.device).cuda_stream
         pkifmm_evaluate(self.handle, S, src, dens, T, trg, pot, ctypes.c_void_p(stream))
@@ -268,7 +271,7 @@ class PeriodicKIFMM:
                 raise ValueError("inputs must be contiguous float64 CUDA tensors")
         nprob = len(src_off) - 1
         if pot is None:
-            pot = torch.empty((self.nrhs, trg.shape[0], self.k), dtype=torch.float64, device=src.device)
+            pot = torch.empty((self.nrhs, trg.shape[0], self.kt), dtype=torch.float64, device=src.device)
         if stream is None:
             stream = torch.cuda.current_stream(src.device).cuda_stream
         pkifmm_evaluate_batched(self.handle, nprob, src_off, trg_off, src, dens, trg, pot, ctypes.c_void_p(stream))
@@ -281,7 +284,7 @@ class PeriodicKIFMM:
         import torch
         if stream is None:
             stream = torch.cuda.current_stream(src.device).cuda_stream
-        pot = torch.empty((self.nrhs, trg.shape[0], self.k), dtype=torch.float64, device=src.device)
+        pot = torch.empty((self.nrhs, trg.shape[0], self.kt), dtype=torch.float64, device=src.device)
         best, ms = pkifmm_autotune_leaf(self.handle, len(src_off) - 1, src_off, trg_off, src, dens, trg, pot,
                                         candidates, reps, ctypes.c_void_p(stream))
         self.leaf_max = best
@@ -293,7 +296,7 @@ class PeriodicKIFMM:
         if isinstance(src, np.ndarray):
             src, dens, trg = (np.ascontiguousarray(a, dtype=np.float64) for a in (src, dens, trg))
         if pot is None:
-            pot = np.zeros((self.nrhs, trg.shape[0], self.k))
+            pot = np.zeros((self.nrhs, trg.shape[0], self.kt))
         pkifmm_evaluate_host(self.handle, src.shape[0], src, dens, trg.shape[0], trg, pot,
                              ctypes.c_void_p(stream) if stream else None)
         return pot

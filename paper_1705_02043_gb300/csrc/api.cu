@@ -13,6 +13,11 @@ using namespace pk;
 
 struct pkifmm_plan_s {
     Plan P;
+    int kernel_id = 0;                   // the public kernel (PKIFMM_*)
+    pkifmm_plan_s *pressure = nullptr;   // PKIFMM_STOKES_PRESSURE: Laplace field plan on 3 nrhs charge vectors
+    pk::DBuf<double> cbuf;               // its scratch: velocities, charges, fields
+    int ks() const { return P.k; }       // source density components
+    int kt() const { return pressure ? 4 : P.kt; }
 };
 
 namespace pk {
@@ -44,16 +49,42 @@ int guarded(F &&f) {
 }
 
 // corr [nprob][nrhs] (nullable); the problem of sorted target t is the prefix of its key
+// Sorted-target results back to the caller's order, [nrhs][T][k], in box
+// units: potentials scale as 1/L (K homogeneous of degree -1); the gradient
+// components of the Laplace field (field: components 1..3) as 1/L^2.  corr:
+// the Laplace TP constant per (problem, vector), added to the potential only.
 __global__ void k_unpermute(const double *__restrict__ pot_s, const int *__restrict__ idx, long long T, int nrhs,
-                            int k, double invL, const double *__restrict__ corr,
+                            int k, int field, double invL, const double *__restrict__ corr,
                             const unsigned long long *__restrict__ keyT, int key_shift, double *__restrict__ pot) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= T * nrhs * k) return;
     long long t = i / (nrhs * k);
     int rem = (int)(i % (nrhs * k)), r = rem / k, a = rem % k;
     double v = pot_s[i];
-    if (corr) v += corr[(long long)(keyT[t] >> key_shift) * nrhs + r];
-    pot[((long long)r * T + idx[t]) * k + a] = v * invL;
+    if (corr && a == 0) v += corr[(long long)(keyT[t] >> key_shift) * nrhs + r];
+    pot[((long long)r * T + idx[t]) * k + a] = (field && a > 0) ? v * invL * invL : v * invL;
+}
+
+// Stokes forces [nrhs][S][3] -> Laplace charges [3 nrhs][S] (vector 3r + a = f_a of vector r)
+__global__ void k_forces_to_charges(const double *__restrict__ f, long long S, int nrhs, double *__restrict__ q) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= S * nrhs * 3) return;
+    const int a = (int)(i % 3);
+    const long long rs = i / 3, s = rs % S, r = rs / S;
+    q[((long long)(3 * r + a)) * S + s] = f[i];
+}
+
+// velocity [nrhs][T][3] and Laplace fields [3 nrhs][T][4] -> [nrhs][T][4] =
+// (u, p), p = -(1/4 pi) sum_a d/dx_a (potential of the charges f_a)
+__global__ void k_velocity_pressure(const double *__restrict__ vel, const double *__restrict__ fld, long long T,
+                                    int nrhs, double *__restrict__ pot) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= T * nrhs) return;
+    const long long t = i % T, r = i / T;
+    for (int a = 0; a < 3; a++) pot[i * 4 + a] = vel[i * 3 + a];
+    double div = 0.0;
+    for (int a = 0; a < 3; a++) div += fld[((3 * r + a) * T + t) * 4 + 1 + a];
+    pot[i * 4 + 3] = -div * 0.079577471545947668;  // 1/(4 pi)
 }
 
 // sums[2*(j*nk+c)] += phi, sums[2*(j*nk+c)+1] += |phi| per problem j (blockIdx.z,
@@ -174,7 +205,7 @@ int evaluate_impl(Plan &P, int nprob, const int64_t *soff, const int64_t *toff, 
     std::fill(P.stage_ms, P.stage_ms + 9, 0.0);
     if (T == 0) return PKIFMM_OK;
     if (S == 0) {
-        PK_CUDA(cudaMemsetAsync(pot, 0, sizeof(double) * T * P.nrhs * P.k, s));
+        PK_CUDA(cudaMemsetAsync(pot, 0, sizeof(double) * T * P.nrhs * P.kt, s));
         return PKIFMM_OK;
     }
     record(P, 0, s);
@@ -226,11 +257,38 @@ int evaluate_impl(Plan &P, int nprob, const int64_t *soff, const int64_t *toff, 
     run_downward(P, s);
     record(P, 6, s);
     run_leaves(P, s);
-    long long n = T * P.nrhs * P.k;
+    long long n = T * P.nrhs * P.kt;
     const double *corr = laplace_tp_constant(P, s);
-    count_launch(), k_unpermute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P.pot_s.p, P.idxT.p, T, P.nrhs, P.k, 1.0 / P.L, corr,
-                                                             P.keyT.p, 3 * P.depth_max, pot);
+    count_launch(), k_unpermute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        P.pot_s.p, P.idxT.p, T, P.nrhs, P.kt, P.kt == 4 ? 1 : 0, 1.0 / P.L, corr, P.keyT.p, 3 * P.depth_max, pot);
     record(P, 7, s);
+    PK_CUDA(cudaGetLastError());
+    return PKIFMM_OK;
+}
+
+// Any plan: the Stokes velocity-pressure plan runs the velocity evaluation,
+// then the Laplace field evaluation on the force components as charges, and
+// combines them; the others evaluate directly.
+int evaluate_any(pkifmm_plan_s *h, int nprob, const int64_t *soff, const int64_t *toff, const double *src,
+                 const double *dens, const double *trg, double *pot, cudaStream_t s) {
+    if (!h->pressure) return evaluate_impl(h->P, nprob, soff, toff, src, dens, trg, pot, s);
+    if (nprob < 1 || !soff || !toff) return fail(PKIFMM_ERR_INVALID_ARG, "nprob < 1 or NULL offsets");
+    Plan &P = h->P;
+    const int nr = P.nrhs;
+    const int64_t S = soff[nprob], T = toff[nprob];
+    if (S < 0 || T < 0 || S > (1LL << 30) || T > (1LL << 30)) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
+    PK_CUDA(cudaSetDevice(P.device));
+    const size_t nv = (size_t)nr * T * 3, nq = (size_t)3 * nr * S, nf = (size_t)3 * nr * T * 4;
+    h->cbuf.reserve(nv + nq + nf + 8);
+    double *vel = h->cbuf.p, *q = vel + nv, *fld = q + nq;
+    int rc = evaluate_impl(P, nprob, soff, toff, src, dens, trg, vel, s);
+    if (rc != PKIFMM_OK) return rc;
+    if (S > 0)
+        count_launch(), k_forces_to_charges<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(dens, S, nr, q);
+    rc = evaluate_impl(h->pressure->P, nprob, soff, toff, src, q, trg, fld, s);
+    if (rc != PKIFMM_OK) return rc;
+    if (T > 0)
+        count_launch(), k_velocity_pressure<<<(unsigned)((nr * T + 255) / 256), 256, 0, s>>>(vel, fld, T, nr, pot);
     PK_CUDA(cudaGetLastError());
     return PKIFMM_OK;
 }
@@ -243,6 +301,104 @@ int set_last_error(int code, const std::string &msg) { return fail(code, msg); }
 
 extern "C" {
 
+static void destroy_plan(pkifmm_plan_s *plan) {
+    if (!plan) return;
+    destroy_plan(plan->pressure);
+    plan->pressure = nullptr;
+    plan->cbuf.release();
+    Plan &P = plan->P;
+    cudaSetDevice(P.device);
+    cudaDeviceSynchronize();
+    m2l_tc_release(P);
+    for (auto &e : P.ev)
+        if (P.events && e) cudaEventDestroy(e);
+    DBuf<double> *d64[] = {&P.g64, &P.uc2e_a, &P.uc2e_b, &P.dc2e_a, &P.dc2e_b, &P.m2m, &P.l2l, &P.m2l, &P.root,
+                           &P.xs, &P.xt, &P.dens_s, &P.pot_s, &P.ysrel64, &P.xtrel64, &P.sums, &P.up64, &P.chk64,
+                           &P.dn64, &P.tmp64};
+    for (auto *b : d64) b->release();
+    DBuf<float> *d32[] = {&P.g32, &P.uc2e_a32, &P.uc2e_b32, &P.dc2e_a32, &P.dc2e_b32, &P.m2m32, &P.l2l32, &P.m2l32,
+                          &P.ysrel32, &P.xtrel32, &P.dens32, &P.pot32, &P.up32, &P.chk32, &P.dn32, &P.tmp32};
+    for (auto *b : d32) b->release();
+    DBuf<int> *di[] = {&P.class_slot_op, &P.idxS, &P.idxT, &P.idxS2, &P.idxT2, &P.hist, &P.err, &P.cnt, &P.off,
+                       &P.gather_idx, &P.leaves_src, &P.leaves_trg, &P.xboxes, &P.tree.parent, &P.tree.child,
+                       &P.tree.lvl_begin_d, &P.tree.u_ptr, &P.tree.u_box, &P.tree.w_ptr, &P.tree.w_box,
+                       &P.tree.x_ptr, &P.tree.x_box, &P.tree.v_slot};
+    for (auto *b : di) b->release();
+    P.keyS.release();
+    P.keyT.release();
+    P.keyS2.release();
+    P.keyT2.release();
+    P.tree.key.release();
+    P.tree.bpos.release();
+    P.tree.srange.release();
+    P.tree.trange.release();
+    P.tree.u_sh.release();
+    P.tree.w_sh.release();
+    P.tree.x_sh.release();
+    P.slot_of.release();
+    P.csr.release();
+    P.ctr.release();
+    P.soff.release();
+    P.toff.release();
+    P.far64.release();
+    if (P.stage_h) cudaFreeHost(P.stage_h);
+    if (P.down_h) cudaFreeHost(P.down_h);
+    if (P.stage_ev) cudaEventDestroy(P.stage_ev);
+    Task *ts[] = {&P.t_uc2e, &P.t_m2l, &P.t_dc2e, &P.t_root};
+    for (auto *t : ts) {
+        t->boxes.release();
+        t->tiles.release();
+        t->class_ops.release();
+    }
+    for (auto *v : {&P.t_m2m, &P.t_l2l})
+        for (auto &t : *v) {
+            t.boxes.release();
+            t.tiles.release();
+            t.class_ops.release();
+        }
+    delete plan;
+}
+
+// One plan of an internal kernel (0 Laplace, 1 Stokes) with kt target components.
+static pkifmm_plan_s *make_plan(int kernel, int kt, unsigned periodic_axes, const double box_lo[3], double box_len,
+                                int p, int ell, int leaf_max, int depth_max, int precision, int nrhs,
+                                const char *cache_dir, bool host_stage1) {
+    auto *h = new pkifmm_plan_s;
+    Plan &P = h->P;
+    P.kernel = kernel;
+    P.k = kernel == 0 ? 1 : 3;
+    P.kt = kt;
+    P.p = p;
+    P.n = surface_count(p);
+    P.kn = P.n * P.k;
+    P.ell = ell;
+    P.leaf_max = leaf_max;
+    P.depth_max = depth_max;
+    P.precision = precision;
+    P.nrhs = nrhs;
+    P.periodic = periodic_axes;
+    for (int a = 0; a < 3; a++) P.lo[a] = box_lo[a];
+    P.L = box_len;
+    try {
+        PK_CUDA(cudaGetDevice(&P.device));
+        // Singular values <= eps * s_max are dropped.  FP64: eps = 2^-52 dim(A),
+        // the numerical rank threshold of Table 1 (the MATLAB / numpy pinv
+        // default).  MIXED: eps = 1e-7, chosen by measured error against
+        // the oracle (binary32 operators; see the tests).
+        double eps = precision == PKIFMM_FP64 ? std::ldexp(1.0, -52) * P.kn : 1e-7;
+        if (const char *e = std::getenv("PKIFMM_EPS_MIXED"); e && precision == PKIFMM_MIXED) eps = std::atof(e);
+        if (host_stage1) build_host_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
+        else build_device_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
+        upload_operators(P);
+        for (auto &e : P.ev) PK_CUDA(cudaEventCreate(&e));
+        P.events = true;
+    } catch (...) {
+        destroy_plan(h);
+        throw;
+    }
+    return h;
+}
+
 int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, const double box_lo[3],
                        double box_len, int p, int ell, int leaf_max, int depth_max, int precision, int nrhs,
                        const char *cache_dir) {
@@ -250,47 +406,32 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, con
     *out = nullptr;
     const bool host_stage1 = (precision & PKIFMM_PRECOMPUTE_HOST) != 0;
     precision &= ~PKIFMM_PRECOMPUTE_HOST;
-    if (kernel != PKIFMM_LAPLACE && kernel != PKIFMM_STOKES) return fail(PKIFMM_ERR_INVALID_ARG, "kernel");
+    if (kernel < PKIFMM_LAPLACE || kernel > PKIFMM_STOKES_PRESSURE) return fail(PKIFMM_ERR_INVALID_ARG, "kernel");
     if (periodic_axes > 7) return fail(PKIFMM_ERR_INVALID_ARG, "periodic_axes");
     if (!box_lo || !(box_len > 0) || !std::isfinite(box_len)) return fail(PKIFMM_ERR_INVALID_ARG, "box");
     if (p < 4 || p > 16 || ell < 1 || ell > 8 || leaf_max < 1 || depth_max < 1 || depth_max > kMaxLevel - 1 ||
         nrhs < 1 || nrhs > 64 || (precision != PKIFMM_FP64 && precision != PKIFMM_MIXED))
         return fail(PKIFMM_ERR_INVALID_ARG, "p / ell / leaf_max / depth_max / nrhs / precision out of range");
+    if (kernel == PKIFMM_STOKES_PRESSURE && nrhs > 21)
+        return fail(PKIFMM_ERR_INVALID_ARG, "nrhs > 21 for the velocity-pressure kernel (3 nrhs charge vectors)");
     bool sp = periodic_axes == 1 || periodic_axes == 2 || periodic_axes == 4;
     if (!(periodic_axes == 0 || periodic_axes == 7 || periodic_axes == 3 || sp))
         return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built (doubly periodic: x and y only)");
     return guarded([&]() {
-        auto *h = new pkifmm_plan_s;
-        Plan &P = h->P;
-        P.kernel = kernel;
-        P.k = kernel == 0 ? 1 : 3;
-        P.p = p;
-        P.n = surface_count(p);
-        P.kn = P.n * P.k;
-        P.ell = ell;
-        P.leaf_max = leaf_max;
-        P.depth_max = depth_max;
-        P.precision = precision;
-        P.nrhs = nrhs;
-        P.periodic = periodic_axes;
-        for (int a = 0; a < 3; a++) P.lo[a] = box_lo[a];
-        P.L = box_len;
-        try {
-            PK_CUDA(cudaGetDevice(&P.device));
-            // Singular values <= eps * s_max are dropped.  FP64: eps = 2^-52 dim(A),
-            // the numerical rank threshold of Table 1 (the MATLAB / numpy pinv
-            // default).  MIXED: eps = 1e-7, chosen by measured error against
-            // the oracle (binary32 operators; see the tests).
-            double eps = precision == PKIFMM_FP64 ? std::ldexp(1.0, -52) * P.kn : 1e-7;
-            if (const char *e = std::getenv("PKIFMM_EPS_MIXED"); e && precision == PKIFMM_MIXED) eps = std::atof(e);
-            if (host_stage1) build_host_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
-            else build_device_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
-            upload_operators(P);
-            for (auto &e : P.ev) PK_CUDA(cudaEventCreate(&e));
-            P.events = true;
-        } catch (...) {
-            delete h;
-            throw;
+        const int internal = (kernel == PKIFMM_LAPLACE || kernel == PKIFMM_LAPLACE_FIELD) ? 0 : 1;
+        const int kt = kernel == PKIFMM_LAPLACE ? 1 : kernel == PKIFMM_LAPLACE_FIELD ? 4 : 3;
+        pkifmm_plan_s *h = make_plan(internal, kt, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max,
+                                     precision, nrhs, cache_dir, host_stage1);
+        h->kernel_id = kernel;
+        if (kernel == PKIFMM_STOKES_PRESSURE) {
+            try {
+                h->pressure = make_plan(0, 4, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max, precision,
+                                        3 * nrhs, cache_dir, host_stage1);
+                h->pressure->kernel_id = PKIFMM_LAPLACE_FIELD;
+            } catch (...) {
+                destroy_plan(h);
+                throw;
+            }
         }
         *out = h;
         return PKIFMM_OK;
@@ -303,7 +444,7 @@ int pkifmm_evaluate(pkifmm_plan plan, int64_t S, const double *src_xyz, const do
     return guarded([&]() {
         if (S < 0 || T < 0) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
         int64_t so[2] = {0, S}, to[2] = {0, T};
-        return evaluate_impl(plan->P, 1, so, to, src_xyz, dens, trg_xyz, pot, (cudaStream_t)cuda_stream);
+        return evaluate_any(plan, 1, so, to, src_xyz, dens, trg_xyz, pot, (cudaStream_t)cuda_stream);
     });
 }
 
@@ -312,8 +453,7 @@ int pkifmm_evaluate_batched(pkifmm_plan plan, int nprob, const int64_t *src_off,
                             void *cuda_stream) {
     if (!plan) return fail(PKIFMM_ERR_INVALID_ARG, "plan is NULL");
     return guarded([&]() {
-        return evaluate_impl(plan->P, nprob, src_off, trg_off, src_xyz, dens, trg_xyz, pot,
-                             (cudaStream_t)cuda_stream);
+        return evaluate_any(plan, nprob, src_off, trg_off, src_xyz, dens, trg_xyz, pot, (cudaStream_t)cuda_stream);
     });
 }
 
@@ -325,8 +465,8 @@ int pkifmm_evaluate_host(pkifmm_plan plan, int64_t S, const double *src_xyz, con
         cudaStream_t s = (cudaStream_t)cuda_stream;
         if (S < 0 || T < 0 || S > (1LL << 30) || T > (1LL << 30)) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
         PK_CUDA(cudaSetDevice(P.device));
-        size_t bs = sizeof(double) * 3 * S, bd = sizeof(double) * S * P.nrhs * P.k;
-        size_t bt = sizeof(double) * 3 * T, bp = sizeof(double) * T * P.nrhs * P.k;
+        size_t bs = sizeof(double) * 3 * S, bd = sizeof(double) * S * P.nrhs * plan->ks();
+        size_t bt = sizeof(double) * 3 * T, bp = sizeof(double) * T * P.nrhs * plan->kt();
         DBuf<char> buf;
         buf.reserve(bs + bd + bt + bp + 64);
         double *ds = (double *)buf.p, *dd = (double *)(buf.p + bs), *dt = (double *)(buf.p + bs + bd),
@@ -338,7 +478,7 @@ int pkifmm_evaluate_host(pkifmm_plan plan, int64_t S, const double *src_xyz, con
         if (T) PK_CUDA(cudaMemcpyAsync(dt, trg_xyz, bt, cudaMemcpyHostToDevice, s));
         if (S < 0 || T < 0) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
         int64_t so[2] = {0, S}, to[2] = {0, T};
-        int rc = evaluate_impl(P, 1, so, to, ds, dd, dt, dp, s);
+        int rc = evaluate_any(plan, 1, so, to, ds, dd, dt, dp, s);
         if (rc == PKIFMM_OK && T) PK_CUDA(cudaMemcpyAsync(pot, dp, bp, cudaMemcpyDeviceToHost, s));
         PK_CUDA(cudaStreamSynchronize(s));
         buf.release();
@@ -349,21 +489,26 @@ int pkifmm_evaluate_host(pkifmm_plan plan, int64_t S, const double *src_xyz, con
 int pkifmm_last_stage_times(pkifmm_plan plan, double *ms, int max) {
     if (!plan || !ms || max < 0) return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
     return guarded([&]() {
-        Plan &P = plan->P;
-        if (P.events && P.T > 0 && P.S > 0) {
-            PK_CUDA(cudaEventSynchronize(P.ev[7]));
-            for (int i = 0; i < 7; i++) {
+        double tot[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        // the velocity-pressure kernel: both evaluations, stage by stage
+        for (pkifmm_plan_s *h = plan; h; h = h->pressure) {
+            Plan &P = h->P;
+            if (P.events && P.T > 0 && P.S > 0) {
+                PK_CUDA(cudaEventSynchronize(P.ev[7]));
+                for (int i = 0; i < 7; i++) {
+                    float t = 0;
+                    PK_CUDA(cudaEventElapsedTime(&t, P.ev[i], P.ev[i + 1]));
+                    P.stage_ms[i] = t;
+                }
                 float t = 0;
-                PK_CUDA(cudaEventElapsedTime(&t, P.ev[i], P.ev[i + 1]));
-                P.stage_ms[i] = t;
+                PK_CUDA(cudaEventElapsedTime(&t, P.ev[0], P.ev[7]));
+                P.stage_ms[7] = t;
             }
-            float t = 0;
-            PK_CUDA(cudaEventElapsedTime(&t, P.ev[0], P.ev[7]));
-            P.stage_ms[7] = t;
+            P.stage_ms[8] = m2l_tc_last_ms(P);
+            for (int i = 0; i < 9; i++) tot[i] += P.stage_ms[i];
         }
-        P.stage_ms[8] = m2l_tc_last_ms(P);
         int m = std::min(max, 9);
-        for (int i = 0; i < m; i++) ms[i] = P.stage_ms[i];
+        for (int i = 0; i < m; i++) ms[i] = tot[i];
         return m;
     });
 }
@@ -380,24 +525,27 @@ int pkifmm_autotune_leaf(pkifmm_plan plan, int nprob, const int64_t *src_off, co
         Plan &P = plan->P;
         cudaStream_t s = (cudaStream_t)cuda_stream;
         const int keep = P.leaf_max;
+        auto set_leaf = [&](int v) {
+            for (pkifmm_plan_s *h = plan; h; h = h->pressure) h->P.leaf_max = v;
+        };
         int best = keep;
         double best_ms = 1e300;
         for (int c = 0; c < ncand; c++) {
-            P.leaf_max = candidates[c];
-            int rc = evaluate_impl(P, nprob, src_off, trg_off, src_xyz, dens, trg_xyz, pot, s);  // warm-up
+            set_leaf(candidates[c]);
+            int rc = evaluate_any(plan, nprob, src_off, trg_off, src_xyz, dens, trg_xyz, pot, s);  // warm-up
             if (rc != PKIFMM_OK) {
-                P.leaf_max = keep;
+                set_leaf(keep);
                 return rc;
             }
             PK_CUDA(cudaStreamSynchronize(s));
             double t_min = 1e300;
             for (int r = 0; r < reps; r++) {
                 auto t0 = std::chrono::steady_clock::now();
-                rc = evaluate_impl(P, nprob, src_off, trg_off, src_xyz, dens, trg_xyz, pot, s);
+                rc = evaluate_any(plan, nprob, src_off, trg_off, src_xyz, dens, trg_xyz, pot, s);
                 PK_CUDA(cudaStreamSynchronize(s));
                 auto t1 = std::chrono::steady_clock::now();
                 if (rc != PKIFMM_OK) {
-                    P.leaf_max = keep;
+                    set_leaf(keep);
                     return rc;
                 }
                 t_min = std::min(t_min, std::chrono::duration<double, std::milli>(t1 - t0).count());
@@ -408,7 +556,7 @@ int pkifmm_autotune_leaf(pkifmm_plan plan, int nprob, const int64_t *src_off, co
                 best = candidates[c];
             }
         }
-        P.leaf_max = best;
+        set_leaf(best);
         *best_out = best;
         return (int)PKIFMM_OK;
     });
@@ -416,7 +564,7 @@ int pkifmm_autotune_leaf(pkifmm_plan plan, int nprob, const int64_t *src_off, co
 
 int pkifmm_plan_set_far_field(pkifmm_plan plan, int mode) {
     if (!plan || (mode != PKIFMM_FAR_L2L && mode != PKIFMM_FAR_DIRECT)) return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
-    plan->P.far_direct = mode == PKIFMM_FAR_DIRECT;
+    for (pkifmm_plan_s *h = plan; h; h = h->pressure) h->P.far_direct = mode == PKIFMM_FAR_DIRECT;
     return PKIFMM_OK;
 }
 
@@ -643,60 +791,7 @@ int pkifmm_precompute_operators(int kernel, unsigned periodic_axes, int p, int e
     });
 }
 
-void pkifmm_plan_destroy(pkifmm_plan plan) {
-    if (!plan) return;
-    Plan &P = plan->P;
-    cudaSetDevice(P.device);
-    cudaDeviceSynchronize();
-    m2l_tc_release(P);
-    for (auto &e : P.ev)
-        if (P.events && e) cudaEventDestroy(e);
-    DBuf<double> *d64[] = {&P.g64, &P.uc2e_a, &P.uc2e_b, &P.dc2e_a, &P.dc2e_b, &P.m2m, &P.l2l, &P.m2l, &P.root,
-                           &P.xs, &P.xt, &P.dens_s, &P.pot_s, &P.ysrel64, &P.xtrel64, &P.sums, &P.up64, &P.chk64,
-                           &P.dn64, &P.tmp64};
-    for (auto *b : d64) b->release();
-    DBuf<float> *d32[] = {&P.g32, &P.uc2e_a32, &P.uc2e_b32, &P.dc2e_a32, &P.dc2e_b32, &P.m2m32, &P.l2l32, &P.m2l32,
-                          &P.ysrel32, &P.xtrel32, &P.dens32, &P.pot32, &P.up32, &P.chk32, &P.dn32, &P.tmp32};
-    for (auto *b : d32) b->release();
-    DBuf<int> *di[] = {&P.class_slot_op, &P.idxS, &P.idxT, &P.idxS2, &P.idxT2, &P.hist, &P.err, &P.cnt, &P.off,
-                       &P.gather_idx, &P.leaves_src, &P.leaves_trg, &P.xboxes, &P.tree.parent, &P.tree.child,
-                       &P.tree.lvl_begin_d, &P.tree.u_ptr, &P.tree.u_box, &P.tree.w_ptr, &P.tree.w_box,
-                       &P.tree.x_ptr, &P.tree.x_box, &P.tree.v_slot};
-    for (auto *b : di) b->release();
-    P.keyS.release();
-    P.keyT.release();
-    P.keyS2.release();
-    P.keyT2.release();
-    P.tree.key.release();
-    P.tree.bpos.release();
-    P.tree.srange.release();
-    P.tree.trange.release();
-    P.tree.u_sh.release();
-    P.tree.w_sh.release();
-    P.tree.x_sh.release();
-    P.slot_of.release();
-    P.csr.release();
-    P.ctr.release();
-    P.soff.release();
-    P.toff.release();
-    P.far64.release();
-    if (P.stage_h) cudaFreeHost(P.stage_h);
-    if (P.down_h) cudaFreeHost(P.down_h);
-    if (P.stage_ev) cudaEventDestroy(P.stage_ev);
-    Task *ts[] = {&P.t_uc2e, &P.t_m2l, &P.t_dc2e, &P.t_root};
-    for (auto *t : ts) {
-        t->boxes.release();
-        t->tiles.release();
-        t->class_ops.release();
-    }
-    for (auto *v : {&P.t_m2m, &P.t_l2l})
-        for (auto &t : *v) {
-            t.boxes.release();
-            t.tiles.release();
-            t.class_ops.release();
-        }
-    delete plan;
-}
+void pkifmm_plan_destroy(pkifmm_plan plan) { destroy_plan(plan); }
 
 const char *pkifmm_strerror(int code) {
     switch (code) {

@@ -664,23 +664,26 @@ __global__ void k_cast(const double *__restrict__ a, T *__restrict__ b, long lon
 
 constexpr int KS_T = 128;  // threads of the kernel-sum blocks
 
-template <typename T, int K, int R>
+template <typename T, int K, int R, int KT = K>
 struct LeafAcc {
     // Sums without the kernel's constant factor (1 for Laplace, 1/8pi for
-    // Stokes), applied once to each result (scale()).
-    T acc[R][K], tot[R][K], cmp[R][K];
+    // Stokes), applied once to each result (scale()).  KT target components:
+    // K for the kernel itself; 4 for the Laplace field (K = 1): the potential
+    // and its gradient at the target, grad(1/r) = -d/r^3.
+    static_assert(KT == K || (K == 1 && KT == 4), "target components");
+    T acc[R][KT], tot[R][KT], cmp[R][KT];
     static constexpr double kScale = K == 1 ? 1.0 : 0.039788735772973836;  // 1/(8 pi)
     __device__ void init() {
 #pragma unroll
         for (int r = 0; r < R; r++)
 #pragma unroll
-            for (int a = 0; a < K; a++) acc[r][a] = tot[r][a] = cmp[r][a] = 0;
+            for (int a = 0; a < KT; a++) acc[r][a] = tot[r][a] = cmp[r][a] = 0;
     }
     __device__ void flush() {
 #pragma unroll
         for (int r = 0; r < R; r++)
 #pragma unroll
-            for (int a = 0; a < K; a++) {
+            for (int a = 0; a < KT; a++) {
                 T y = acc[r][a] - cmp[r][a], s = tot[r][a] + y;
                 cmp[r][a] = (s - tot[r][a]) - y;
                 tot[r][a] = s;
@@ -695,7 +698,17 @@ struct LeafAcc {
         T ir;
         if constexpr (SELF) ir = inv_sqrt(r2);
         else ir = rsqrt_nz(r2);
-        if constexpr (K == 1) {
+        if constexpr (KT == 4) {
+            const T ir3 = ir * ir * ir;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const T q = f[r][0], qi3 = q * ir3;
+                acc[r][0] += ir * q;
+                acc[r][1] -= dx * qi3;
+                acc[r][2] -= dy * qi3;
+                acc[r][3] -= dz * qi3;
+            }
+        } else if constexpr (K == 1) {
 #pragma unroll
             for (int r = 0; r < R; r++) acc[r][0] += ir * f[r][0];
         } else {
@@ -845,7 +858,7 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
 // (x, y, z) and R x K densities; the image offset of a source box is added to
 // the target once.  Each staged tile is summed in registers and added to the
 // running total with Kahan compensation.
-template <typename T, int K, int NT, int R, int TPT>
+template <typename T, int K, int NT, int R, int TPT, int KT>
 __global__ void __launch_bounds__(NT) k_leaf(
     const int *__restrict__ leaves, const int4 *__restrict__ bpos, const int2 *__restrict__ srange,
     const int2 *__restrict__ trange, const int *__restrict__ uptr, const int *__restrict__ ubox,
@@ -894,7 +907,7 @@ __global__ void __launch_bounds__(NT) k_leaf(
                 xs[q][2] = v.z;
             }
         }
-        LeafAcc<T, K, R> L[Q];
+        LeafAcc<T, K, R, KT> L[Q];
 #pragma unroll
         for (int q = 0; q < Q; q++) L[q].init();
         // L2T from the downward equivalent surface (edge 2.95 h)
@@ -999,9 +1012,9 @@ __global__ void __launch_bounds__(NT) k_leaf(
                 for (int r = 0; r < R; r++)
                     if (r < nv)
 #pragma unroll
-                        for (int a = 0; a < K; a++)
-                            pot[(long long)t * nrhs * K + (rhs0 + r) * K + a] =
-                                ((double)L[q].tot[r][a] - (double)L[q].cmp[r][a]) * LeafAcc<T, K, R>::kScale;
+                        for (int a = 0; a < KT; a++)
+                            pot[(long long)t * nrhs * KT + (rhs0 + r) * KT + a] =
+                                ((double)L[q].tot[r][a] - (double)L[q].cmp[r][a]) * LeafAcc<T, K, R, KT>::kScale;
             }
         }
     };
@@ -1206,11 +1219,11 @@ void run_downward(Plan &P, cudaStream_t s) {
     }
 }
 
-template <typename T, int K>
+template <typename T, int K, int KT>
 static void leaves_t(Plan &P, cudaStream_t s) {
     using B = Bufs<T>;
     const int nr = P.nrhs;
-    P.pot_s.reserve((size_t)P.T * nr * K + 1);
+    P.pot_s.reserve((size_t)P.T * nr * KT + 1);
     auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
     auto *xr = reinterpret_cast<const V4<T> *>(B::xrel(P).p);
     // one block per target leaf; block size near the leaf size (most leaves
@@ -1222,7 +1235,7 @@ static void leaves_t(Plan &P, cudaStream_t s) {
         // targets per thread for up to two vectors, so a leaf of up to 2 NT
         // targets takes one pass over its sources
         constexpr int TPT = R <= 2 ? 2 : 1;
-        count_launch(), k_leaf<T, K, NT, R, TPT><<<P.n_leaves_trg, NT, 0, s>>>(
+        count_launch(), k_leaf<T, K, NT, R, TPT, KT><<<P.n_leaves_trg, NT, 0, s>>>(
                 P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
                 P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
                 B::dn(P).p, nr, r0, B::g(P).p, P.n, P.pot_s.p);
@@ -1244,7 +1257,8 @@ static void leaves_t(Plan &P, cudaStream_t s) {
 // all images beyond the near layers evaluated directly from the root's
 // downward equivalent density (surface of half-width 1.475 around the
 // centre of the unit box), in binary64.  Problem of target t: its key prefix.
-template <int K>
+// KT = 4 (Laplace field): the potential and its gradient.
+template <int K, int KT>
 __global__ void k_far_direct(const double *__restrict__ xt, long long T, const unsigned long long *__restrict__ keyT,
                              int key_shift, const double *__restrict__ far, const double *__restrict__ g, int n,
                              int nrhs, double *__restrict__ pot_s) {
@@ -1255,32 +1269,47 @@ __global__ void k_far_direct(const double *__restrict__ xt, long long T, const u
     const int kn = n * K;
     for (int r = 0; r < nrhs; r++) {
         const double *phi = far + (j * nrhs + r) * kn;
-        double acc[K];
-        for (int a = 0; a < K; a++) acc[a] = 0.0;
-        for (int i = 0; i < n; i++)
-            Kern<double, K>::add(acc, x0 - 1.475 * g[3 * i], x1 - 1.475 * g[3 * i + 1], x2 - 1.475 * g[3 * i + 2],
-                                 phi + i * K);
-        for (int a = 0; a < K; a++) pot_s[(t * nrhs + r) * K + a] += acc[a];
+        double acc[KT];
+        for (int a = 0; a < KT; a++) acc[a] = 0.0;
+        for (int i = 0; i < n; i++) {
+            const double d0 = x0 - 1.475 * g[3 * i], d1 = x1 - 1.475 * g[3 * i + 1], d2 = x2 - 1.475 * g[3 * i + 2];
+            if constexpr (KT == 4) {
+                const double ir = 1.0 / sqrt(d0 * d0 + d1 * d1 + d2 * d2), qi3 = phi[i] * ir * ir * ir;
+                acc[0] += phi[i] * ir;
+                acc[1] -= d0 * qi3;
+                acc[2] -= d1 * qi3;
+                acc[3] -= d2 * qi3;
+            } else {
+                Kern<double, K>::add(acc, d0, d1, d2, phi + i * K);
+            }
+        }
+        for (int a = 0; a < KT; a++) pot_s[(t * nrhs + r) * KT + a] += acc[a];
     }
 }
 
 void run_leaves(Plan &P, cudaStream_t s) {
+    const bool field = P.kt == 4;
     if (P.precision == PKIFMM_FP64) {
-        if (P.k == 1) leaves_t<double, 1>(P, s);
-        else leaves_t<double, 3>(P, s);
+        if (field) leaves_t<double, 1, 4>(P, s);
+        else if (P.k == 1) leaves_t<double, 1, 1>(P, s);
+        else leaves_t<double, 3, 3>(P, s);
     } else {
-        if (P.k == 1) leaves_t<float, 1>(P, s);
-        else leaves_t<float, 3>(P, s);
+        if (field) leaves_t<float, 1, 4>(P, s);
+        else if (P.k == 1) leaves_t<float, 1, 1>(P, s);
+        else leaves_t<float, 3, 3>(P, s);
     }
     if (P.far_direct && P.periodic && P.T > 0) {
         const int shift = P.nprob > 1 ? 3 * P.depth_max : 63;  // one problem: index 0
         const unsigned nb = (unsigned)((P.T + 127) / 128);
-        if (P.k == 1)
-            count_launch(), k_far_direct<1><<<nb, 128, 0, s>>>(P.xt.p, P.T, P.keyT.p, shift, P.far64.p, P.g64.p, P.n,
-                                                                P.nrhs, P.pot_s.p);
+        if (field)
+            count_launch(), k_far_direct<1, 4><<<nb, 128, 0, s>>>(P.xt.p, P.T, P.keyT.p, shift, P.far64.p, P.g64.p,
+                                                                   P.n, P.nrhs, P.pot_s.p);
+        else if (P.k == 1)
+            count_launch(), k_far_direct<1, 1><<<nb, 128, 0, s>>>(P.xt.p, P.T, P.keyT.p, shift, P.far64.p, P.g64.p,
+                                                                   P.n, P.nrhs, P.pot_s.p);
         else
-            count_launch(), k_far_direct<3><<<nb, 128, 0, s>>>(P.xt.p, P.T, P.keyT.p, shift, P.far64.p, P.g64.p, P.n,
-                                                                P.nrhs, P.pot_s.p);
+            count_launch(), k_far_direct<3, 3><<<nb, 128, 0, s>>>(P.xt.p, P.T, P.keyT.p, shift, P.far64.p, P.g64.p,
+                                                                   P.n, P.nrhs, P.pot_s.p);
     }
 }
 
