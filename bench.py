@@ -15,6 +15,12 @@ Workloads (``--workload``; the default is the first):
 * ``laplace_tp_multi``: 256 independent triply periodic Laplace problems,
   N log-uniform in [1024, 65536], neutral charges U[-1,1], p = 6, one batched
   evaluation; the leaf size is picked by the library's autotuner first.
+* ``stokes_chebyshev`` / ``stokes_lognormal``: the paper's Stokes timing point
+  sets (97^3 Chebyshev grid; 912,673 lognormal(0.2, 0.5) points), any
+  periodicity (``--periodic``).
+* ``stokes_tp_pressure``: the ``stokes_tp`` problem with velocity and pressure
+  at every target (the Stokes evaluation plus a Laplace field evaluation of
+  the three force components).
 
 All run the MIXED path (binary32 kernel sums, M2L on the tensor cores,
 binary64 root operator).  A step is one evaluation: Morton sort, octree,
@@ -95,13 +101,16 @@ WORKLOADS = {
     "laplace_tp_multi": dict(kernel=0, periodic=7, n=256, p=6, leaf=32, depth=10, nrhs=1, sample=32),
     "stokes_chebyshev": dict(kernel=1, periodic=7, n=97, p=8, leaf=64, depth=12, nrhs=1, sample=128),
     "stokes_lognormal": dict(kernel=1, periodic=7, n=97 ** 3, p=8, leaf=64, depth=12, nrhs=1, sample=128),
+    # velocity and pressure (kernel 3): the Stokes evaluation plus a Laplace field
+    # evaluation on the three force components
+    "stokes_tp_pressure": dict(kernel=3, periodic=7, n=1 << 20, p=8, leaf=64, depth=10, nrhs=1, sample=128),
 }
 
 
 def workload(name, n, seed):
     """(points, densities [nrhs][N][k], problem offsets or None, description)."""
     from paper_1705_02043_gb300 import workloads as w
-    if name == "stokes_tp":
+    if name in ("stokes_tp", "stokes_tp_pressure"):
         x, f = w.stokes_uniform(n, seed=seed, nrhs=1)
         return x, f, None, "seeded uniform points, N(0,1) forces, net force removed"
     if name == "stokes_dp_slab":
@@ -133,6 +142,9 @@ PERIODIC_OVERRIDE = None  # --periodic for the paper-shaped workloads
 
 def oracle_sum(kernel, periodic, x, d, xt):
     import oracle
+    if kernel == 3:  # velocity and pressure
+        return np.concatenate([oracle.periodic_sum(1, periodic, x, d, xt),
+                               oracle.stokes_pressure(periodic, x, d, xt)[:, None]], axis=1)
     out = oracle.periodic_sum(kernel, periodic, x, d, xt)
     return out if kernel == 1 else out[:, None]
 
@@ -195,10 +207,11 @@ def run_precompute(args, wl, pk):
     from paper_1705_02043_gb300 import _binding as pkb
     import torch
     kernel, periodic = wl["kernel"], wl["periodic"]
+    kop = 0 if kernel in (0, 2) else 1  # the translation kernel
     torch.cuda.init()
-    dev = pkb.pkifmm_precompute_operators(kernel, periodic, args.p, args.ell, pk.MIXED, 1, want_ops=False)
+    dev = pkb.pkifmm_precompute_operators(kop, periodic, args.p, args.ell, pk.MIXED, 1, want_ops=False)
     dev_s, ph = dev[4], dev[5]
-    host_s = (pkb.pkifmm_precompute_operators(kernel, periodic, args.p, args.ell, pk.MIXED, 0, want_ops=False)[4]
+    host_s = (pkb.pkifmm_precompute_operators(kop, periodic, args.p, args.ell, pk.MIXED, 0, want_ops=False)[4]
               if args.precompute_host else None)
     t0 = time.perf_counter()
     plan = pk.PeriodicKIFMM(kernel, periodic, p=args.p, ell=args.ell, leaf_max=args.leaf, depth_max=wl["depth"],
@@ -206,7 +219,7 @@ def run_precompute(args, wl, pk):
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
     plan.close()
-    kn = (6 * (args.p - 1) ** 2 + 2) * (1 if kernel == 0 else 3)
+    kn = (6 * (args.p - 1) ** 2 + 2) * (1 if kop == 0 else 3)
     print(json.dumps({
         "metric": "Stage 1 precompute time (surface SVD, M2M/L2L, root far-field table), device build",
         "value": dev_s, "unit": "s", "n_gpus": 1, "higher_is_better": False, "dtype": "f64",
@@ -253,7 +266,9 @@ def main():
     args.p = args.p or wl["p"]
     args.leaf = args.leaf or wl["leaf"]
     args.sample = args.sample or wl["sample"]
-    kernel, periodic, nrhs, k = wl["kernel"], wl["periodic"], wl["nrhs"], (1 if wl["kernel"] == 0 else 3)
+    kernel, periodic, nrhs = wl["kernel"], wl["periodic"], wl["nrhs"]
+    ks = 1 if kernel in (0, 2) else 3  # source density components
+    k = {0: 1, 1: 3, 2: 4, 3: 4}[kernel]  # target components
 
     rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
@@ -349,7 +364,7 @@ def main():
         e2e_step()
         e2e_t.append(time.perf_counter() - t0)
     e2e_v = world * ntrg * nrhs / multi.max_over_ranks(float(np.mean(e2e_t)), dist, dev)
-    h2d = 8 * (3 * ntrg + nrhs * ntrg * k) if off is not None else 8 * (3 * ntrg + nrhs * ntrg * k + 3 * ntrg)
+    h2d = 8 * (3 * ntrg + nrhs * ntrg * ks) if off is not None else 8 * (3 * ntrg + nrhs * ntrg * ks + 3 * ntrg)
     d2h = 8 * nrhs * ntrg * k
 
     result = None
@@ -357,8 +372,11 @@ def main():
         u = out.cpu().numpy()
         pk_, src = peaks()
         nV = stats[4]
-        kn = k * (6 * (args.p - 1) ** 2 + 2)
+        nsurf = 6 * (args.p - 1) ** 2 + 2
+        kn = ks * nsurf
         flops = 2.0 * kn * kn * nV * nrhs  # per M2L (all launches of one evaluation)
+        if kernel == 3:  # plus the Laplace field evaluation's M2L on 3 nrhs charge vectors
+            flops += 2.0 * nsurf * nsurf * nV * 3 * nrhs
         m2l_avg = float(np.mean(m2l_ms))
         achieved = flops / (m2l_avg / 1e3) / 1e12
         peak = pk_.get("bf16_tflops_sustained", 1700.0)
@@ -401,11 +419,12 @@ def main():
             p64.close()
         # Stage 1 (precompute) timed on its own, device build and optionally host build
         from paper_1705_02043_gb300 import _binding as pkb
-        dev_pre = pkb.pkifmm_precompute_operators(kernel, periodic, args.p, args.ell, pk.MIXED, 1, want_ops=False)
+        kop = 0 if kernel in (0, 2) else 1  # the translation kernel
+        dev_pre = pkb.pkifmm_precompute_operators(kop, periodic, args.p, args.ell, pk.MIXED, 1, want_ops=False)
         pre = {"device_s": dev_pre[4],
                "device_phases_s": {"svd": dev_pre[5][0], "m2m_l2l": dev_pre[5][1], "root_table": dev_pre[5][2]},
                "jacobi_sweeps": int(dev_pre[5][3]),
-               "host_s": (pkb.pkifmm_precompute_operators(kernel, periodic, args.p, args.ell, pk.MIXED, 0,
+               "host_s": (pkb.pkifmm_precompute_operators(kop, periodic, args.p, args.ell, pk.MIXED, 0,
                                                           want_ops=False)[4] if args.precompute_host else None),
                "host_threads": os.cpu_count() if args.precompute_host else None,
                "covers": "surface SVD, M2M/L2L, root far-field table (the M2L operators are formed on the "
@@ -416,7 +435,7 @@ def main():
             "vs_baseline": None, "dtype": "mixed: f32 sums, fp16x3 tensor M2L, f64 root",
             "data": f"synthetic ({desc})",
             "config": {"workload": workload_name(args.workload, wl, args.n, args.p, args.leaf),
-                       "kernel": "stokes" if kernel == 1 else "laplace",
+                       "kernel": {0: "laplace", 1: "stokes", 2: "laplace_field", 3: "stokes_velocity_pressure"}[kernel],
                        "periodic": {7: "xyz", 3: "xy", 0: "none"}.get(periodic, str(periodic)),
                        "N": ntrg, "p": args.p, "ell": args.ell, "leaf_max": args.leaf, "depth_max": wl["depth"], "nrhs": nrhs,
                        "problems": 1 if off is None else len(off) - 1,
@@ -437,7 +456,7 @@ def main():
                                  stages)),
             "tree": dict(zip(["boxes", "leaves", "depth", "U", "V", "W", "X", "p2p_pairs"], stats)),
             "autotune": tuned,
-            "p2p": p2p_block(kernel, args.p, ntrg, nrhs, stats, stages[6], clocks, pk_),
+            "p2p": p2p_block(kernel, args.p, ntrg, nrhs, stats, stages[6], clocks, pk_) if kernel in (0, 1) else None,
             "clocks": clocks,
         }
     plan.close()
