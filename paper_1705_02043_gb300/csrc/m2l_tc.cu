@@ -73,6 +73,7 @@ struct TcState {
     int *lmap = nullptr;                 // position -> box maps of the partial grid levels (-1: no box)
     size_t lmap_cap = 0;
     int stages = 3;                      // pipeline depth of the launched instantiation
+    int wide = 1;                        // grid levels with two column tiles per CTA (k_m2l_tcw)
     cudaStream_t side[3] = {};           // the per-level launches run concurrently (disjoint outputs)
     cudaEvent_t fork = nullptr, join[3] = {};
 };
@@ -516,6 +517,206 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// ---------------- grid mode, two column tiles per CTA ----------------
+//
+// The same contraction for two column tiles of one octant class and row block
+// (256 (box, rhs) columns): each K_o tile staged once serves both, so the
+// operator stream a CTA reads is halved per output column.  Per 16-wide K
+// step three N = 256 MMAs: A_hi [B_hi0 | B_hi1] into the hi*hi accumulator,
+// A_hi [B_lo0 | B_lo1] and A_lo [B_hi0 | B_hi1] into the cross accumulator;
+// together they fill tensor memory (512 columns), so there is one work
+// accumulator and the next slot's MMAs wait for the drain of the last.
+// Warp 0 issues the TMA loads (one thread), warp 1 the MMAs (one thread) and
+// owns the tensor memory, warps 4-11 drain (warp w: lanes 32 (w % 4) .. + 31 of
+// tile (w - 4) / 4); warps 2-3 idle.  Two stages of 96 KB.  A pair whose
+// second tile carries bit 30 in .x repeats the first tile and writes nothing
+// for it (odd tile counts).
+constexpr int TCW_THREADS = 384;
+constexpr int TCW_STAGE_BYTES = 2 * TC_A_BYTES + 4 * TC_B_BYTES;  // 96 KB
+constexpr int tcw_smem(int stages) { return TC_CTRL_BYTES + stages * TCW_STAGE_BYTES + TC_SLACK + 1024; }
+constexpr int TCW_SKIP = 1 << 30;
+
+template <int STAGES>
+__global__ void __launch_bounds__(TCW_THREADS, 1)
+    k_m2l_tcw(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+              const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, TcArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)smem;                 // [STAGES]
+    uint64_t *empty = full + STAGES;                   // [STAGES]
+    uint64_t *wfull = empty + STAGES;                  // work accumulator ready
+    uint64_t *wfree = wfull + 1;                       // work accumulator drained
+    uint32_t *tmem_slot = (uint32_t *)(wfree + 1);
+    int *nact_s = (int *)(tmem_slot + 1);
+    short *act = (short *)(nact_s + 1);                // [189]
+    long long *drow = (long long *)(smem + 1024);      // [256]
+    uint8_t *stages = smem + TC_CTRL_BYTES;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mtiles = a.KM / TC_M;
+    const int pair = blockIdx.x / mtiles;
+    const int m0 = (blockIdx.x % mtiles) * TC_M;
+    int4 tl[2] = {a.tiles[2 * pair], a.tiles[2 * pair + 1]};
+    const bool skip1 = (tl[1].x & TCW_SKIP) != 0;
+    tl[1].x &= ~TCW_SKIP;
+    const int cls = tl[0].x & 7, rblk = tl[0].x >> 3;
+    const int kchunks = a.KK / TC_K;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(wfull, 1);
+        mbar_init(wfree, 256);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int n = tid; n < 2 * TC_N; n += TCW_THREADS) {
+        // column n: tile n / 128; within it rhs + rb (x + bx (y + by z)) as in the one-tile kernel
+        const int h = n / TC_N, nn = n % TC_N;
+        const int4 tile = tl[h];
+        const int rl = nn % a.rb, b = nn / a.rb;
+        const int x = b % a.bx, y = (b / a.bx) % a.by, z = b / (a.bx * a.by);
+        const int px = (cls & 1) + 2 * (tile.y + x), py = (cls >> 1 & 1) + 2 * (tile.z + y),
+                  pz = (cls >> 2 & 1) + 2 * (tile.w + z);
+        const int m = (int)morton3_dev(px, py, pz);
+        const int box = a.lmap ? a.lmap[m] : a.lvl_begin + m;
+        drow[n] = (box >= 0 && !(h == 1 && skip1)) ? (long long)box * a.nrhs + rblk * a.rb + rl : -1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    for (int s = tid; s < kVSlots; s += TCW_THREADS) act[s] = (short)(a.class_ops[cls * kVSlots + s] >= 0);
+    __syncthreads();
+    if (tid == 0) {
+        int c = 0;
+        for (int s = 0; s < kVSlots; s++)
+            if (act[s]) act[c++] = (short)s;
+        *nact_s = c;
+    }
+    __syncthreads();
+    const int nact = *nact_s;
+    const uint32_t tmem = *tmem_slot;
+    const int total = nact * kchunks;
+
+    if (warp == 0) {
+        // ---- producer: TMA of the K_o tiles and of both column tiles' sources ----
+        if (lane == 0) {
+            int cur_si = -1, op = 0, cx[2] = {0, 0}, cy[2] = {0, 0}, cz[2] = {0, 0};
+            for (int it = 0; it < total; it++) {
+                const int st = it % STAGES;
+                const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                if (!mbar_wait(&empty[st], ph ^ 1u, a.err)) break;
+                const int si = it / kchunks, k0 = (it % kchunks) * TC_K;
+                if (si != cur_si) {
+                    cur_si = si;
+                    const int s = act[si];
+                    op = a.class_ops[cls * kVSlots + s];
+                    const int *o = a.slot_off + (cls * kVSlots + s) * 3;
+                    const int qx = (cls & 1) + o[0], qy = (cls >> 1 & 1) + o[1], qz = (cls >> 2 & 1) + o[2];
+                    const int par = (qx & 1) | (qy & 1) << 1 | (qz & 1) << 2;
+                    for (int h = 0; h < 2; h++) {
+                        cx[h] = ((qx - (qx & 1)) >> 1) + tl[h].y + 2;
+                        cy[h] = ((qy - (qy & 1)) >> 1) + tl[h].z + 2;
+                        cz[h] = par * a.zd + ((qz - (qz & 1)) >> 1) + tl[h].w + 2;
+                    }
+                }
+                uint8_t *sb = stages + (size_t)st * TCW_STAGE_BYTES;
+                mbar_expect_tx(&full[st], (uint32_t)TCW_STAGE_BYTES);
+                tma_load_2d(sb, &tA_hi, k0, op * a.KM + m0, &full[st]);
+                tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KM + m0, &full[st]);
+                const int r0 = rblk * a.rb;
+                uint8_t *b = sb + 2 * TC_A_BYTES;  // B_hi0, B_hi1, B_lo0, B_lo1
+                for (int h = 0; h < 2; h++) {
+                    tma_load_5d(b + h * TC_B_BYTES, &tB_hi, k0, r0, cx[h], cy[h], cz[h], &full[st]);
+                    tma_load_5d(b + (2 + h) * TC_B_BYTES, &tB_lo, k0, r0, cx[h], cy[h], cz[h], &full[st]);
+                }
+                mbar_arrive(&full[st]);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer: the single work accumulator, one slot at a time ----
+        if (lane == 0) {
+            int it = 0;
+            bool okm = true;
+            const uint32_t dhh = tmem, dx = tmem + 2 * TC_N;  // columns [0, 256) hi*hi, [256, 512) cross
+            for (int si = 0; si < nact && okm; si++) {
+                if (!mbar_wait(wfree, ((uint32_t)si & 1u) ^ 1u, a.err)) break;
+                tc_fence_after();
+                for (int kc = 0; kc < kchunks; kc++, it++) {
+                    const int st = it % STAGES;
+                    if (!mbar_wait(&full[st], (uint32_t)(it / STAGES) & 1u, a.err)) {
+                        okm = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sb = smem_u32(stages + (size_t)st * TCW_STAGE_BYTES);
+#pragma unroll
+                    for (int k16 = 0; k16 < TC_K / 16; k16++) {
+                        const uint64_t a_hi = smem_desc_sw128(sb + k16 * 32);
+                        const uint64_t a_lo = smem_desc_sw128(sb + TC_A_BYTES + k16 * 32);
+                        const uint64_t b_hi = smem_desc_sw128(sb + 2 * TC_A_BYTES + k16 * 32);  // B_hi0 | B_hi1
+                        const uint64_t b_lo = smem_desc_sw128(sb + 2 * TC_A_BYTES + 2 * TC_B_BYTES + k16 * 32);
+                        const uint32_t first = (kc | k16) ? 1u : 0u;
+                        tc_mma(dhh, a_hi, b_hi, first, kIdesc2);
+                        tc_mma(dx, a_hi, b_lo, first, kIdesc2);
+                        tc_mma(dx, a_lo, b_hi, 1u, kIdesc2);
+                    }
+                    tc_commit(&empty[st]);
+                }
+                tc_commit(wfull);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4) {
+        // ---- epilogue: tile h of the pair, lanes of this warp's sub-partition ----
+        const int sp = warp & 3, h = (warp - 4) >> 2;
+        float acc[TC_N];
+#pragma unroll
+        for (int c = 0; c < TC_N; c++) acc[c] = 0.f;
+        bool oke = true;
+        for (int si = 0; si < nact && oke; si++) {
+            bool w = mbar_wait(wfull, (uint32_t)si & 1u, a.err);
+            oke = __all_sync(0xffffffffu, w);
+            if (!oke) break;
+            tc_fence_after();
+#pragma unroll
+            for (int c0 = 0; c0 < TC_N; c0 += 16) {
+                uint32_t v[16], u[16];
+                const uint32_t ta = tmem + ((uint32_t)(sp * 32) << 16) + h * TC_N + c0;
+                tc_ld16_nowait(ta, v);
+                tc_ld16_nowait(ta + 2 * TC_N, u);
+                tc_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; j++) acc[c0 + j] += __uint_as_float(v[j]) + __uint_as_float(u[j]);
+            }
+            tc_fence_before();
+            mbar_arrive(wfree);
+        }
+        const float unscale = ldexpf(1.0f, -(phi_exp(a.amax) + a.kexp));
+        const int krow = m0 + sp * 32 + lane;
+        if (krow < a.kn) {
+#pragma unroll
+            for (int c = 0; c < TC_N; c++) {
+                long long d = drow[h * TC_N + c];
+                if (d >= 0) a.chk[d * a.kn + krow] = acc[c] * unscale;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
 // ---------------- set-up and launch ----------------
 
 // K_o * 2^kexp split into fp16 hi/lo, padded to KM x KK: out[h][op][i][j]
@@ -732,6 +933,11 @@ void m2l_tc_prepare(Plan &P) {
     t->stages = 3;
     if (const char *e = std::getenv("PKIFMM_M2L_STAGES"))
         if (std::atoi(e) == 2) t->stages = 2;
+    // two column tiles per CTA on the grid levels; PKIFMM_M2L_WIDE=0 launches one
+    // tile per CTA there (timing comparisons; the results are the same)
+    PK_CUDA(cudaFuncSetAttribute(k_m2l_tcw<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcw_smem(2)));
+    if (const char *e = std::getenv("PKIFMM_M2L_WIDE"))
+        if (std::atoi(e) == 0) t->wide = 0;
 }
 
 namespace {
@@ -863,6 +1069,27 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
                         }
     }
     gt_begin.push_back((int)gtiles.size());
+    // the same grid tiles in pairs of one (class, row block) for k_m2l_tcw,
+    // appended after them; an odd tile is paired with itself (flagged)
+    const size_t wbase = gtiles.size();
+    std::vector<int> wt_begin;
+    for (size_t gi = 0; gi < gp.size(); gi++) {
+        wt_begin.push_back((int)(gtiles.size() - wbase));
+        for (int i = gt_begin[gi]; i < gt_begin[gi + 1];) {
+            const int4 t0 = gtiles[i];
+            if (i + 1 < gt_begin[gi + 1] && gtiles[i + 1].x == t0.x) {
+                const int4 t1 = gtiles[i + 1];
+                gtiles.push_back(t0);
+                gtiles.push_back(t1);
+                i += 2;
+            } else {
+                gtiles.push_back(t0);
+                gtiles.push_back(make_int4(t0.x | TCW_SKIP, t0.y, t0.z, t0.w));
+                i += 1;
+            }
+        }
+    }
+    wt_begin.push_back((int)(gtiles.size() - wbase));
     grow(t->gtiles, t->gtiles_cap, gtiles.size() + 1);
     grow(t->gboxes, t->gboxes_cap, gbox.size() + 1);
     if (!gtiles.empty())
@@ -981,7 +1208,12 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         const int ntl = gt_begin[gi + 1] - gt_begin[gi];
         if (ntl == 0) continue;
         cudaStream_t ls = t->side[nlaunch++ % 3];
-        if (t->stages == 2)
+        if (t->wide) {
+            a.tiles = t->gtiles + wbase + wt_begin[gi];
+            const int npair = (wt_begin[gi + 1] - wt_begin[gi]) / 2;
+            count_launch(), k_m2l_tcw<2><<<npair * mtiles, TCW_THREADS, tcw_smem(2), ls>>>(t->tmap[0], t->tmap[1],
+                                                                                         mb[0], mb[1], a);
+        } else if (t->stages == 2)
             count_launch(), k_m2l_tc<2><<<ntl * mtiles, TC_THREADS, tc_smem(2), ls>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);
         else
             count_launch(), k_m2l_tc<3><<<ntl * mtiles, TC_THREADS, tc_smem(3), ls>>>(t->tmap[0], t->tmap[1], mb[0], mb[1], a);

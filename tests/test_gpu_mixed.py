@@ -130,3 +130,19 @@ def test_mixed_box_gather_eight_vectors(cache):
     e = rel_l2(u8[0][idx], ref)
     print(f"box gather nrhs=8: rel_l2 {e:.3e}")
     assert e < 3e-4  # p = 6
+
+
+@pytest.mark.parametrize("n,nrhs", [(1 << 18, 1), (1 << 17, 4)])
+def test_mixed_grid_two_tiles_per_cta_match_one(n, nrhs, cache, monkeypatch):
+    """The grid-mode M2L with two column tiles per CTA (one operator tile
+    staged for both, N = 256 MMAs) gives the one-tile kernel's results: the
+    same products accumulated in the same order per output column."""
+    x, f = w.stokes_uniform(n, seed=30, nrhs=nrhs)
+    d = f if nrhs > 1 else f[0]
+    monkeypatch.setenv("PKIFMM_M2L_WIDE", "0")
+    u1 = run(1, 7, x, d, x, p=8, leaf=64, precision=1, cache_dir=cache)
+    monkeypatch.setenv("PKIFMM_M2L_WIDE", "1")
+    u2 = run(1, 7, x, d, x, p=8, leaf=64, precision=1, cache_dir=cache)
+    diff = np.abs(u1 - u2).max() / np.abs(u1).max()
+    print(f"two tiles vs one, n={n} nrhs={nrhs}: max rel diff {diff:.2e}")
+    assert diff <= 1e-7
