@@ -58,13 +58,13 @@ typedef struct pkifmm_plan_s *pkifmm_plan;
  *                          the target evaluations differ.
  *   PKIFMM_STOKES_PRESSURE Stokes forces (k_s = 3); each target receives
  *                          k_t = 4 values: the velocity and the pressure
- *                          p = sum f.r/(4 pi r^3) (viscosity 1), the pressure
- *                          summed as -(1/4 pi) div of the Laplace potentials
- *                          of the three force components (a second, Laplace
- *                          field evaluation on 3 nrhs charge vectors inside the
- *                          same call).  Needs zero net force for every
- *                          periodicity (each force component is a neutral
- *                          charge distribution); TP pressure has zero mean.
+ *                          p = sum f.r/(4 pi r^3) (viscosity 1).  The pressure
+ *                          is the Laplace potential of dipoles f at the
+ *                          sources, summed in the same call by a second KIFMM
+ *                          with Laplace translations (dipole kernel at the
+ *                          sources, monopole equivalent densities).  Needs zero
+ *                          net force for every periodicity (each force
+ *                          component neutral); TP pressure has zero mean.
  * Densities are [nrhs][S][k_s], potentials [nrhs][T][k_t]; k_s = k_t = k for
  * PKIFMM_LAPLACE and PKIFMM_STOKES. */
 enum { PKIFMM_LAPLACE = 0, PKIFMM_STOKES = 1, PKIFMM_LAPLACE_FIELD = 2, PKIFMM_STOKES_PRESSURE = 3 };

@@ -14,9 +14,9 @@ using namespace pk;
 struct pkifmm_plan_s {
     Plan P;
     int kernel_id = 0;                   // the public kernel (PKIFMM_*)
-    pkifmm_plan_s *pressure = nullptr;   // PKIFMM_STOKES_PRESSURE: Laplace field plan on 3 nrhs charge vectors
-    pk::DBuf<double> cbuf;               // its scratch: velocities, charges, fields
-    int ks() const { return P.k; }       // source density components
+    pkifmm_plan_s *pressure = nullptr;   // PKIFMM_STOKES_PRESSURE: the Laplace plan with dipole sources
+    pk::DBuf<double> cbuf;               // its scratch: velocities, pressures
+    int ks() const { return P.ks; }      // source density components
     int kt() const { return pressure ? 4 : P.kt; }
 };
 
@@ -50,11 +50,13 @@ int guarded(F &&f) {
 
 // corr [nprob][nrhs] (nullable); the problem of sorted target t is the prefix of its key
 // Sorted-target results back to the caller's order, [nrhs][T][k], in box
-// units: potentials scale as 1/L (K homogeneous of degree -1); the gradient
-// components of the Laplace field (field: components 1..3) as 1/L^2.  corr:
-// the Laplace TP constant per (problem, vector), added to the potential only.
+// units: potentials scale as 1/L (K homogeneous of degree -1); mode 1 (the
+// Laplace field): components 1..3, the gradient, as 1/L^2; mode 2 (Laplace
+// dipole sources, the Stokes pressure): f.r/(4 pi r^3), degree -2, as
+// 1/(4 pi L^2).  corr: the Laplace TP constant per (problem, vector), added to
+// component 0 in the units of the sums.
 __global__ void k_unpermute(const double *__restrict__ pot_s, const int *__restrict__ idx, long long T, int nrhs,
-                            int k, int field, double invL, const double *__restrict__ corr,
+                            int k, int mode, double invL, const double *__restrict__ corr,
                             const unsigned long long *__restrict__ keyT, int key_shift, double *__restrict__ pot) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= T * nrhs * k) return;
@@ -62,29 +64,18 @@ __global__ void k_unpermute(const double *__restrict__ pot_s, const int *__restr
     int rem = (int)(i % (nrhs * k)), r = rem / k, a = rem % k;
     double v = pot_s[i];
     if (corr && a == 0) v += corr[(long long)(keyT[t] >> key_shift) * nrhs + r];
-    pot[((long long)r * T + idx[t]) * k + a] = (field && a > 0) ? v * invL * invL : v * invL;
+    const double sc = mode == 2 ? invL * invL * 0.079577471545947668  // 1/(4 pi)
+                      : (mode == 1 && a > 0) ? invL * invL : invL;
+    pot[((long long)r * T + idx[t]) * k + a] = v * sc;
 }
 
-// Stokes forces [nrhs][S][3] -> Laplace charges [3 nrhs][S] (vector 3r + a = f_a of vector r)
-__global__ void k_forces_to_charges(const double *__restrict__ f, long long S, int nrhs, double *__restrict__ q) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= S * nrhs * 3) return;
-    const int a = (int)(i % 3);
-    const long long rs = i / 3, s = rs % S, r = rs / S;
-    q[((long long)(3 * r + a)) * S + s] = f[i];
-}
-
-// velocity [nrhs][T][3] and Laplace fields [3 nrhs][T][4] -> [nrhs][T][4] =
-// (u, p), p = -(1/4 pi) sum_a d/dx_a (potential of the charges f_a)
-__global__ void k_velocity_pressure(const double *__restrict__ vel, const double *__restrict__ fld, long long T,
+// velocity [nrhs][T][3] and pressure [nrhs][T] -> [nrhs][T][4] = (u, p)
+__global__ void k_velocity_pressure(const double *__restrict__ vel, const double *__restrict__ pres, long long T,
                                     int nrhs, double *__restrict__ pot) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= T * nrhs) return;
-    const long long t = i % T, r = i / T;
     for (int a = 0; a < 3; a++) pot[i * 4 + a] = vel[i * 3 + a];
-    double div = 0.0;
-    for (int a = 0; a < 3; a++) div += fld[((3 * r + a) * T + t) * 4 + 1 + a];
-    pot[i * 4 + 3] = -div * 0.079577471545947668;  // 1/(4 pi)
+    pot[i * 4 + 3] = pres[i];
 }
 
 // sums[2*(j*nk+c)] += phi, sums[2*(j*nk+c)+1] += |phi| per problem j (blockIdx.z,
@@ -125,14 +116,21 @@ __global__ void k_dens_sums(const double *__restrict__ dens, const long long *__
 // constant (2 pi / 3V) (sum q |y - c|^2 - sum phi^u |y^u - c|^2).  That
 // constant is restored here so the result is the zero-mean Ewald potential.
 // m2[j*nrhs + r]: problem j (blockIdx.z), sorted sources soff[j]..soff[j+1]
+// Dipole sources (ks = 3): the second moment of a dipole f at y is the limit
+// of a charge pair, f.grad_y |y - c|^2 = 2 f.(y - c).
 __global__ void k_second_moment_src(const double *__restrict__ xs, const double *__restrict__ dens,
-                                    const long long *__restrict__ soff, int nrhs, double *__restrict__ m2) {
+                                    const long long *__restrict__ soff, int nrhs, int ks, double *__restrict__ m2) {
     int r = blockIdx.y, j = blockIdx.z;
     double acc = 0;
     for (long long i = soff[j] + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < soff[j + 1];
          i += (long long)gridDim.x * blockDim.x) {
         double dx = xs[3 * i] - 0.5, dy = xs[3 * i + 1] - 0.5, dz = xs[3 * i + 2] - 0.5;
-        acc += dens[i * nrhs + r] * (dx * dx + dy * dy + dz * dz);
+        if (ks == 3) {
+            const double *f = dens + (i * nrhs + r) * 3;
+            acc += 2.0 * (f[0] * dx + f[1] * dy + f[2] * dz);
+        } else {
+            acc += dens[i * nrhs + r] * (dx * dx + dy * dy + dz * dz);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(&m2[(long long)j * nrhs + r], acc);
@@ -164,7 +162,7 @@ const double *laplace_tp_constant(Plan &P, cudaStream_t s) {
     double *m2 = P.sums.p, *corr = P.sums.p + 2 * rows;
     PK_CUDA(cudaMemsetAsync(m2, 0, sizeof(double) * 2 * rows, s));
     dim3 grid((unsigned)std::min<long long>(64, (P.S / P.nprob + 255) / 256 + 1), nr, P.nprob);
-    count_launch(), k_second_moment_src<<<grid, 256, 0, s>>>(P.xs.p, P.dens_s.p, P.soff.p, nr, m2);
+    count_launch(), k_second_moment_src<<<grid, 256, 0, s>>>(P.xs.p, P.dens_s.p, P.soff.p, nr, P.ks, m2);
     if (P.precision == PKIFMM_FP64)
         count_launch(), k_second_moment_root<double><<<rows, 256, 0, s>>>(P.up64.p, P.g64.p, P.n, rows, m2);
     else
@@ -230,7 +228,7 @@ int evaluate_impl(Plan &P, int nprob, const int64_t *soff, const int64_t *toff, 
     if (err[0]) return fail(PKIFMM_ERR_INVALID_ARG, "non-finite coordinate");
     if (err[1]) return fail(PKIFMM_ERR_OUT_OF_BOX, "point outside the box along a free axis");
     if (needs_neutral(P)) {
-        const int nk = P.nrhs * P.k;
+        const int nk = P.nrhs * P.ks;
         const size_t nsum = 2 * (size_t)nk * nprob;
         P.sums.reserve(nsum);
         PK_CUDA(cudaMemsetAsync(P.sums.p, 0, sizeof(double) * nsum, s));
@@ -259,16 +257,17 @@ int evaluate_impl(Plan &P, int nprob, const int64_t *soff, const int64_t *toff, 
     run_leaves(P, s);
     long long n = T * P.nrhs * P.kt;
     const double *corr = laplace_tp_constant(P, s);
+    const int mode = P.kt == 4 ? 1 : P.ks == 3 && P.k == 1 ? 2 : 0;
     count_launch(), k_unpermute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-        P.pot_s.p, P.idxT.p, T, P.nrhs, P.kt, P.kt == 4 ? 1 : 0, 1.0 / P.L, corr, P.keyT.p, 3 * P.depth_max, pot);
+        P.pot_s.p, P.idxT.p, T, P.nrhs, P.kt, mode, 1.0 / P.L, corr, P.keyT.p, 3 * P.depth_max, pot);
     record(P, 7, s);
     PK_CUDA(cudaGetLastError());
     return PKIFMM_OK;
 }
 
 // Any plan: the Stokes velocity-pressure plan runs the velocity evaluation,
-// then the Laplace field evaluation on the force components as charges, and
-// combines them; the others evaluate directly.
+// then the pressure as the Laplace potential of dipoles f at the sources
+// (p = sum f.r/(4 pi r^3)), and interleaves them; the others evaluate directly.
 int evaluate_any(pkifmm_plan_s *h, int nprob, const int64_t *soff, const int64_t *toff, const double *src,
                  const double *dens, const double *trg, double *pot, cudaStream_t s) {
     if (!h->pressure) return evaluate_impl(h->P, nprob, soff, toff, src, dens, trg, pot, s);
@@ -278,17 +277,15 @@ int evaluate_any(pkifmm_plan_s *h, int nprob, const int64_t *soff, const int64_t
     const int64_t S = soff[nprob], T = toff[nprob];
     if (S < 0 || T < 0 || S > (1LL << 30) || T > (1LL << 30)) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
     PK_CUDA(cudaSetDevice(P.device));
-    const size_t nv = (size_t)nr * T * 3, nq = (size_t)3 * nr * S, nf = (size_t)3 * nr * T * 4;
-    h->cbuf.reserve(nv + nq + nf + 8);
-    double *vel = h->cbuf.p, *q = vel + nv, *fld = q + nq;
+    const size_t nv = (size_t)nr * T * 3, np = (size_t)nr * T;
+    h->cbuf.reserve(nv + np + 8);
+    double *vel = h->cbuf.p, *pres = vel + nv;
     int rc = evaluate_impl(P, nprob, soff, toff, src, dens, trg, vel, s);
     if (rc != PKIFMM_OK) return rc;
-    if (S > 0)
-        count_launch(), k_forces_to_charges<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(dens, S, nr, q);
-    rc = evaluate_impl(h->pressure->P, nprob, soff, toff, src, q, trg, fld, s);
+    rc = evaluate_impl(h->pressure->P, nprob, soff, toff, src, dens, trg, pres, s);
     if (rc != PKIFMM_OK) return rc;
     if (T > 0)
-        count_launch(), k_velocity_pressure<<<(unsigned)((nr * T + 255) / 256), 256, 0, s>>>(vel, fld, T, nr, pot);
+        count_launch(), k_velocity_pressure<<<(unsigned)((nr * T + 255) / 256), 256, 0, s>>>(vel, pres, T, nr, pot);
     PK_CUDA(cudaGetLastError());
     return PKIFMM_OK;
 }
@@ -362,12 +359,13 @@ static void destroy_plan(pkifmm_plan_s *plan) {
 // One plan of an internal kernel (0 Laplace, 1 Stokes) with kt target components.
 static pkifmm_plan_s *make_plan(int kernel, int kt, unsigned periodic_axes, const double box_lo[3], double box_len,
                                 int p, int ell, int leaf_max, int depth_max, int precision, int nrhs,
-                                const char *cache_dir, bool host_stage1) {
+                                const char *cache_dir, bool host_stage1, int ks = 0) {
     auto *h = new pkifmm_plan_s;
     Plan &P = h->P;
     P.kernel = kernel;
     P.k = kernel == 0 ? 1 : 3;
     P.kt = kt;
+    P.ks = ks ? ks : P.k;
     P.p = p;
     P.n = surface_count(p);
     P.kn = P.n * P.k;
@@ -412,8 +410,6 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, con
     if (p < 4 || p > 16 || ell < 1 || ell > 8 || leaf_max < 1 || depth_max < 1 || depth_max > kMaxLevel - 1 ||
         nrhs < 1 || nrhs > 64 || (precision != PKIFMM_FP64 && precision != PKIFMM_MIXED))
         return fail(PKIFMM_ERR_INVALID_ARG, "p / ell / leaf_max / depth_max / nrhs / precision out of range");
-    if (kernel == PKIFMM_STOKES_PRESSURE && nrhs > 21)
-        return fail(PKIFMM_ERR_INVALID_ARG, "nrhs > 21 for the velocity-pressure kernel (3 nrhs charge vectors)");
     bool sp = periodic_axes == 1 || periodic_axes == 2 || periodic_axes == 4;
     if (!(periodic_axes == 0 || periodic_axes == 7 || periodic_axes == 3 || sp))
         return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built (doubly periodic: x and y only)");
@@ -425,9 +421,10 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, con
         h->kernel_id = kernel;
         if (kernel == PKIFMM_STOKES_PRESSURE) {
             try {
-                h->pressure = make_plan(0, 4, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max, precision,
-                                        3 * nrhs, cache_dir, host_stage1);
-                h->pressure->kernel_id = PKIFMM_LAPLACE_FIELD;
+                // the pressure: Laplace translations, dipole sources (the forces), one value per target
+                h->pressure = make_plan(0, 1, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max, precision,
+                                        nrhs, cache_dir, host_stage1, 3);
+                h->pressure->kernel_id = -1;
             } catch (...) {
                 destroy_plan(h);
                 throw;

@@ -664,13 +664,16 @@ __global__ void k_cast(const double *__restrict__ a, T *__restrict__ b, long lon
 
 constexpr int KS_T = 128;  // threads of the kernel-sum blocks
 
-template <typename T, int K, int R, int KT = K>
+template <typename T, int K, int R, int KT = K, int KS = K>
 struct LeafAcc {
     // Sums without the kernel's constant factor (1 for Laplace, 1/8pi for
     // Stokes), applied once to each result (scale()).  KT target components:
     // K for the kernel itself; 4 for the Laplace field (K = 1): the potential
-    // and its gradient at the target, grad(1/r) = -d/r^3.
+    // and its gradient at the target, grad(1/r) = -d/r^3.  KS components of
+    // a source (add_src): K, or 3 for Laplace dipoles (K = 1): f.d/r^3, the
+    // potential f.grad_y(1/|x - y|) of a dipole f at y.
     static_assert(KT == K || (K == 1 && KT == 4), "target components");
+    static_assert(KS == K || (K == 1 && KS == 3 && KT == 1), "source components");
     T acc[R][KT], tot[R][KT], cmp[R][KT];
     static constexpr double kScale = K == 1 ? 1.0 : 0.039788735772973836;  // 1/(8 pi)
     __device__ void init() {
@@ -723,15 +726,30 @@ struct LeafAcc {
             }
         }
     }
+    // one source of the source kernel (KS components) at offset d = x - y
+    template <bool SELF>
+    __device__ __forceinline__ void add_src(T dx, T dy, T dz, const T (*f)[KS]) {
+        if constexpr (KS == K) {
+            add<SELF>(dx, dy, dz, f);
+        } else {
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            T ir;
+            if constexpr (SELF) ir = inv_sqrt(r2);
+            else ir = rsqrt_nz(r2);
+            const T ir3 = ir * ir * ir;
+#pragma unroll
+            for (int r = 0; r < R; r++) acc[r][0] += (f[r][0] * dx + f[r][1] * dy + f[r][2] * dz) * ir3;
+        }
+    }
 };
 
-template <typename T, int K, int R>
+template <typename T, int K, int R, int KS = K>
 __global__ void __launch_bounds__(KS_T) k_s2m(const int *__restrict__ leaves, const int4 *__restrict__ bpos,
                                               const int2 *__restrict__ srange, const V4<T> *__restrict__ yrel,
                                               const T *__restrict__ dens, int nrhs, int rhs0,
                                               const T *__restrict__ g, int n, T *__restrict__ chk) {
     __shared__ V4<T> sy[KS_T];
-    __shared__ T sphi[KS_T][R][K];
+    __shared__ T sphi[KS_T][R][KS];
     const int b = leaves[blockIdx.x];
     const int4 p = bpos[b];
     const T h = (T)exp2i(p.w), sc = (T)1.475 * h;
@@ -745,7 +763,7 @@ __global__ void __launch_bounds__(KS_T) k_s2m(const int *__restrict__ leaves, co
             x1 = sc * g[3 * i + 1];
             x2 = sc * g[3 * i + 2];
         }
-        LeafAcc<T, K, R> L;
+        LeafAcc<T, K, R, K, KS> L;
         L.init();
         for (int s0 = r.x; s0 < r.y; s0 += KS_T) {
             __syncthreads();
@@ -755,14 +773,14 @@ __global__ void __launch_bounds__(KS_T) k_s2m(const int *__restrict__ leaves, co
 #pragma unroll
                 for (int q = 0; q < R; q++)
 #pragma unroll
-                    for (int a = 0; a < K; a++)
-                        sphi[threadIdx.x][q][a] = q < nv ? dens[(long long)sidx * nrhs * K + (rhs0 + q) * K + a] : (T)0;
+                    for (int a = 0; a < KS; a++)
+                        sphi[threadIdx.x][q][a] = q < nv ? dens[(long long)sidx * nrhs * KS + (rhs0 + q) * KS + a] : (T)0;
             }
             __syncthreads();
             int m = min(KS_T, r.y - s0);
             for (int j = 0; j < m; j++) {
                 const V4<T> y = sy[j];
-                L.template add<false>(x0 - y.x, x1 - y.y, x2 - y.z, sphi[j]);
+                L.template add_src<false>(x0 - y.x, x1 - y.y, x2 - y.z, sphi[j]);
             }
         }
         if (i < n) {
@@ -791,14 +809,14 @@ __device__ __forceinline__ void centre_offset(int4 B, int4 A, const int sh[3], d
 }
 
 // X list: q~d[B][rhs][i] += h_B sum_{(A,p) in X(B)} sum_{s in A} K(0.525 h_B g_i - yrel_s + off) phi_s
-template <typename T, int K, int R>
+template <typename T, int K, int R, int KS = K>
 __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, const int4 *__restrict__ bpos,
                                               const int2 *__restrict__ srange, const int *__restrict__ xptr,
                                               const int *__restrict__ xbox, const unsigned char *__restrict__ xsh,
                                               const V4<T> *__restrict__ yrel, const T *__restrict__ dens, int nrhs,
                                               int rhs0, const T *__restrict__ g, int n, T *__restrict__ chk) {
     __shared__ V4<T> sy[KS_T];
-    __shared__ T sphi[KS_T][R][K];
+    __shared__ T sphi[KS_T][R][KS];
     const int b = boxes[blockIdx.x];
     const int4 B = bpos[b];
     const T h = (T)exp2i(B.w), sc = (T)0.525 * h;
@@ -811,7 +829,7 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
             x1 = sc * g[3 * i + 1];
             x2 = sc * g[3 * i + 2];
         }
-        LeafAcc<T, K, R> L;
+        LeafAcc<T, K, R, K, KS> L;
         L.init();
         for (int e = xptr[b]; e < xptr[b + 1]; e++) {
             int A = xbox[e], sh[3];
@@ -828,15 +846,15 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
 #pragma unroll
                     for (int q = 0; q < R; q++)
 #pragma unroll
-                        for (int a = 0; a < K; a++)
+                        for (int a = 0; a < KS; a++)
                             sphi[threadIdx.x][q][a] =
-                                q < nv ? dens[(long long)sidx * nrhs * K + (rhs0 + q) * K + a] : (T)0;
+                                q < nv ? dens[(long long)sidx * nrhs * KS + (rhs0 + q) * KS + a] : (T)0;
                 }
                 __syncthreads();
                 int m = min(KS_T, r.y - s0);
                 for (int j = 0; j < m; j++) {
                     const V4<T> y = sy[j];
-                    L.template add<false>(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
+                    L.template add_src<false>(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
                 }
             }
         }
@@ -858,7 +876,7 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
 // (x, y, z) and R x K densities; the image offset of a source box is added to
 // the target once.  Each staged tile is summed in registers and added to the
 // running total with Kahan compensation.
-template <typename T, int K, int NT, int R, int TPT, int KT>
+template <typename T, int K, int NT, int R, int TPT, int KT, int KS = K>
 __global__ void __launch_bounds__(NT) k_leaf(
     const int *__restrict__ leaves, const int4 *__restrict__ bpos, const int2 *__restrict__ srange,
     const int2 *__restrict__ trange, const int *__restrict__ uptr, const int *__restrict__ ubox,
@@ -870,9 +888,11 @@ __global__ void __launch_bounds__(NT) k_leaf(
     // pass) while more than NT remain, so each staged source serves them all
     __shared__ V4<T> sy[NT];
     __shared__ T sphi[NT][R][K];
+    __shared__ T sphs[KS == K ? 1 : NT][R][KS];  // U-list source densities when they differ from K
     const unsigned tid = threadIdx.x;
     // one density value per source (Laplace, one vector): it rides in the source's fourth lane
     constexpr bool PACK = K == 1 && R == 1;
+    constexpr bool PACK_SRC = PACK && KS == 1;
     const int b = leaves[blockIdx.x];
     const int4 B = bpos[b];
     const T h = (T)exp2i(B.w);
@@ -907,7 +927,7 @@ __global__ void __launch_bounds__(NT) k_leaf(
                 xs[q][2] = v.z;
             }
         }
-        LeafAcc<T, K, R, KT> L[Q];
+        LeafAcc<T, K, R, KT, KS> L[Q];
 #pragma unroll
         for (int q = 0; q < Q; q++) L[q].init();
         // L2T from the downward equivalent surface (edge 2.95 h)
@@ -977,15 +997,18 @@ __global__ void __launch_bounds__(NT) k_leaf(
                 const int sidx = s0 + tid;
                 if (sidx < rg.y) {
                     V4<T> v = yrel[sidx];
-                    if constexpr (PACK) {
+                    if constexpr (PACK_SRC) {
                         v.w = dens[(long long)sidx * nrhs + rhs0];
                     } else {
+                        T(*dst)[KS] = [&]() -> T(*)[KS] {
+                            if constexpr (KS == K) return sphi[tid];
+                            else return sphs[tid];
+                        }();
 #pragma unroll
                         for (int r = 0; r < R; r++)
 #pragma unroll
-                            for (int a = 0; a < K; a++)
-                                sphi[tid][r][a] =
-                                    r < nv ? dens[(long long)sidx * nrhs * K + (rhs0 + r) * K + a] : (T)0;
+                            for (int a = 0; a < KS; a++)
+                                dst[r][a] = r < nv ? dens[(long long)sidx * nrhs * KS + (rhs0 + r) * KS + a] : (T)0;
                     }
                     sy[tid] = v;
                 }
@@ -994,11 +1017,15 @@ __global__ void __launch_bounds__(NT) k_leaf(
 #pragma unroll 4
                 for (int j = 0; j < m; j++) {
                     const V4<T> y = sy[j];
-                    const T fw[1][1] = {{y.w}};
+                    [[maybe_unused]] const T fw[1][1] = {{y.w}};
+                    const T(*src)[KS] = [&]() -> const T(*)[KS] {
+                        if constexpr (PACK_SRC) return (const T(*)[KS])fw;
+                        else if constexpr (KS == K) return sphi[j];
+                        else return sphs[j];
+                    }();
 #pragma unroll
                     for (int q = 0; q < Q; q++)
-                        L[q].template add<true>(xo[q][0] - y.x, xo[q][1] - y.y, xo[q][2] - y.z,
-                                                PACK ? (const T(*)[K])fw : sphi[j]);
+                        L[q].template add_src<true>(xo[q][0] - y.x, xo[q][1] - y.y, xo[q][2] - y.z, src);
                 }
 #pragma unroll
                 for (int q = 0; q < Q; q++) L[q].flush();
@@ -1014,7 +1041,7 @@ __global__ void __launch_bounds__(NT) k_leaf(
 #pragma unroll
                         for (int a = 0; a < KT; a++)
                             pot[(long long)t * nrhs * KT + (rhs0 + r) * KT + a] =
-                                ((double)L[q].tot[r][a] - (double)L[q].cmp[r][a]) * LeafAcc<T, K, R, KT>::kScale;
+                                ((double)L[q].tot[r][a] - (double)L[q].cmp[r][a]) * LeafAcc<T, K, R, KT, KS>::kScale;
             }
         }
     };
@@ -1082,7 +1109,7 @@ static void prepare_points(Plan &P, cudaStream_t s) {
     if (P.n_leaves_trg)
         count_launch(), k_relcoords<T><<<P.n_leaves_trg, 128, 0, s>>>(P.leaves_trg.p, P.tree.bpos.p, P.tree.trange.p, P.xt.p, xr);
     if (sizeof(T) == 4) {
-        long long nd = P.S * P.nrhs * P.k;
+        long long nd = P.S * P.nrhs * P.ks;
         P.dens32.reserve(nd + 1);
         if (nd) count_launch(), k_cast<float><<<nblk(nd, 256), 256, 0, s>>>(P.dens_s.p, P.dens32.p, nd);
     }
@@ -1094,7 +1121,7 @@ static void prepare_points(Plan &P, cudaStream_t s) {
     PK_CUDA(cudaMemsetAsync(B::up(P).p, 0, sizeof(T) * rows, s));
 }
 
-template <typename T, int K>
+template <typename T, int K, int KS = K>
 static void upward_t(Plan &P, cudaStream_t s) {
     using B = Bufs<T>;
     prepare_points<T>(P, s);
@@ -1105,7 +1132,7 @@ static void upward_t(Plan &P, cudaStream_t s) {
         for (int r = 0; r < nr; r += 4) {  // up to 4 density vectors per pass
             auto go = [&](auto rt) {
                 constexpr int R = decltype(rt)::value;
-                count_launch(), k_s2m<T, K, R><<<P.n_leaves_src, KS_T, 0, s>>>(
+                count_launch(), k_s2m<T, K, R, KS><<<P.n_leaves_src, KS_T, 0, s>>>(
                     P.leaves_src.p, P.tree.bpos.p, P.tree.srange.p, yr, B::dens(P), nr, r, B::g(P).p, P.n,
                     B::chk(P).p);
             };
@@ -1122,10 +1149,12 @@ static void upward_t(Plan &P, cudaStream_t s) {
 
 void run_upward(Plan &P, cudaStream_t s) {
     if (P.precision == PKIFMM_FP64) {
-        if (P.k == 1) upward_t<double, 1>(P, s);
+        if (P.ks == 3 && P.k == 1) upward_t<double, 1, 3>(P, s);
+        else if (P.k == 1) upward_t<double, 1>(P, s);
         else upward_t<double, 3>(P, s);
     } else {
-        if (P.k == 1) upward_t<float, 1>(P, s);
+        if (P.ks == 3 && P.k == 1) upward_t<float, 1, 3>(P, s);
+        else if (P.k == 1) upward_t<float, 1>(P, s);
         else upward_t<float, 3>(P, s);
     }
 }
@@ -1177,7 +1206,7 @@ void run_m2l(Plan &P, cudaStream_t s) {
     }
 }
 
-template <typename T, int K>
+template <typename T, int K, int KS = K>
 static void downward_t(Plan &P, cudaStream_t s) {
     using B = Bufs<T>;
     const int kn = P.kn, nr = P.nrhs;
@@ -1187,7 +1216,7 @@ static void downward_t(Plan &P, cudaStream_t s) {
         for (int r = 0; r < nr; r += 4) {
             auto go = [&](auto rt) {
                 constexpr int R = decltype(rt)::value;
-                count_launch(), k_s2l<T, K, R><<<P.n_xboxes, KS_T, 0, s>>>(
+                count_launch(), k_s2l<T, K, R, KS><<<P.n_xboxes, KS_T, 0, s>>>(
                     P.xboxes.p, P.tree.bpos.p, P.tree.srange.p, P.tree.x_ptr.p, P.tree.x_box.p, P.tree.x_sh.p, yr,
                     B::dens(P), nr, r, B::g(P).p, P.n, B::chk(P).p);
             };
@@ -1211,15 +1240,17 @@ static void downward_t(Plan &P, cudaStream_t s) {
 
 void run_downward(Plan &P, cudaStream_t s) {
     if (P.precision == PKIFMM_FP64) {
-        if (P.k == 1) downward_t<double, 1>(P, s);
+        if (P.ks == 3 && P.k == 1) downward_t<double, 1, 3>(P, s);
+        else if (P.k == 1) downward_t<double, 1>(P, s);
         else downward_t<double, 3>(P, s);
     } else {
-        if (P.k == 1) downward_t<float, 1>(P, s);
+        if (P.ks == 3 && P.k == 1) downward_t<float, 1, 3>(P, s);
+        else if (P.k == 1) downward_t<float, 1>(P, s);
         else downward_t<float, 3>(P, s);
     }
 }
 
-template <typename T, int K, int KT>
+template <typename T, int K, int KT, int KS = K>
 static void leaves_t(Plan &P, cudaStream_t s) {
     using B = Bufs<T>;
     const int nr = P.nrhs;
@@ -1235,7 +1266,7 @@ static void leaves_t(Plan &P, cudaStream_t s) {
         // targets per thread for up to two vectors, so a leaf of up to 2 NT
         // targets takes one pass over its sources
         constexpr int TPT = R <= 2 ? 2 : 1;
-        count_launch(), k_leaf<T, K, NT, R, TPT, KT><<<P.n_leaves_trg, NT, 0, s>>>(
+        count_launch(), k_leaf<T, K, NT, R, TPT, KT, KS><<<P.n_leaves_trg, NT, 0, s>>>(
                 P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
                 P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
                 B::dn(P).p, nr, r0, B::g(P).p, P.n, P.pot_s.p);
@@ -1291,10 +1322,12 @@ void run_leaves(Plan &P, cudaStream_t s) {
     const bool field = P.kt == 4;
     if (P.precision == PKIFMM_FP64) {
         if (field) leaves_t<double, 1, 4>(P, s);
+        else if (P.ks == 3 && P.k == 1) leaves_t<double, 1, 1, 3>(P, s);
         else if (P.k == 1) leaves_t<double, 1, 1>(P, s);
         else leaves_t<double, 3, 3>(P, s);
     } else {
         if (field) leaves_t<float, 1, 4>(P, s);
+        else if (P.ks == 3 && P.k == 1) leaves_t<float, 1, 1, 3>(P, s);
         else if (P.k == 1) leaves_t<float, 1, 1>(P, s);
         else leaves_t<float, 3, 3>(P, s);
     }

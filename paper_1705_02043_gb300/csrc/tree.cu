@@ -681,9 +681,9 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
                                               P.nprob);
         radix_sort(P.keyS, P.idxS, P.keyS2, P.idxS2, P.hist, (int)S, key_bits, s);
         count_launch(), k_gather3<<<blocks(S, 256), 256, 0, s>>>(xn.p, P.idxS.p, S, P.xs.p);
-        int nk = P.nrhs * P.k;
+        int nk = P.nrhs * P.ks;
         P.dens_s.reserve((size_t)S * nk);
-        count_launch(), k_gather_dens<<<blocks(S * nk, 256), 256, 0, s>>>(dens, P.idxS.p, S, P.nrhs, P.k, P.dens_s.p);
+        count_launch(), k_gather_dens<<<blocks(S * nk, 256), 256, 0, s>>>(dens, P.idxS.p, S, P.nrhs, P.ks, P.dens_s.p);
     }
     if (T && trg == src && T == S && P.same_offsets) {
         // targets are the sources: same keys, order and coordinates
