@@ -203,7 +203,7 @@ def run_reference(args, rank, world, wl):
 
 
 def run_precompute(args, wl, pk):
-    """Stage 1 timing (the precompute of Algorithm 2; Sec. 3.6 tabulates it on CPUs)."""
+    """Stage 1 timing (the precompute of Algorithm 2; Sec. 3.7 tabulates it on CPUs)."""
     from paper_1705_02043_gb300 import _binding as pkb
     import torch
     kernel, periodic = wl["kernel"], wl["periodic"]

@@ -176,7 +176,7 @@ int pkifmm_evaluate_batched(pkifmm_plan plan, int nprob, const int64_t *src_off,
 enum { PKIFMM_FAR_L2L = 0, PKIFMM_FAR_DIRECT = 1 };
 int pkifmm_plan_set_far_field(pkifmm_plan plan, int mode);
 
-/* Leaf-size autotuner (the paper fixes s by hand, Sec. 3.6; no counterpart).
+/* Leaf-size autotuner (the paper fixes s by hand, Sec. 3.5; no counterpart).
  * For each candidate leaf size s (candidates[0..ncand-1], each >= 1) the
  * plan evaluates the given batch (arguments as pkifmm_evaluate_batched) once
  * to warm up and then `reps` times, timing each call on the host clock

@@ -71,7 +71,7 @@ def test_error_falls_with_p(cache):
 
 
 def test_ell_independence(cache):
-    """Sec. 3.5: results for ell = 1, 2, 3 agree."""
+    """Sec. 3.6: results for ell = 1, 2, 3 agree."""
     x, f = w.stokes_uniform(1200, seed=6, neutral=False)
     us = [run(1, 7, x, f[0], x, p=6, leaf=30, ell=ell, cache_dir=cache) for ell in (1, 2, 3)]
     assert rel_l2(us[1], us[0]) < 1e-11 and rel_l2(us[2], us[0]) < 1e-11

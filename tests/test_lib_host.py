@@ -157,7 +157,7 @@ def test_root_operator_matches_oracle_sp_stokes(axis):
 @pytest.mark.parametrize("kernel,periodic", [(0, 7), (1, 7), (0, 1), (1, 2), (0, 3), (1, 3)])
 def test_root_operator_independent_of_ell(kernel, periodic):
     """Folding layers 2..ell back in makes the operator independent of ell
-    (Sec. 3.5: the results do not depend on ell)."""
+    (Sec. 3.6: the results do not depend on ell)."""
     M1 = pk.pkifmm_root_operator(kernel, periodic, 4, 1)
     for ell in (2, 3):
         M = pk.pkifmm_root_operator(kernel, periodic, 4, ell)
