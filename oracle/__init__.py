@@ -219,6 +219,21 @@ def periodic_sum(kernel: int, periodic_axes: int, src, dens, trg, L: float = 1.0
     raise NotImplementedError(f"oracle: kernel {kernel} periodicity {periodic_axes}")
 
 
+def finite_array(kernel: int, axis: int, nimg: int, src, dens, trg, L: float = 1.0) -> np.ndarray:
+    """A finite array of cells along ``axis`` (the cell and its copies shifted by
+    n L e_axis, |n| <= nimg; the finite-length channel of Sec. 4): the plain sum
+    of the free-space kernel over the 2 nimg + 1 copies of the sources.  No
+    compatibility condition is needed (the sum is finite)."""
+    y = _c(src)
+    out = None
+    for n in range(-nimg, nimg + 1):
+        ys = y.copy()
+        ys[:, axis] += n * L
+        v = free_space(kernel, ys, dens, trg)
+        out = v if out is None else out + v
+    return out
+
+
 def laplace_gradient(periodic_axes: int, src, q, trg, L: float = 1.0, xi=None, rc=None, M: int = 200) -> np.ndarray:
     """Gradient at the targets of the periodic Laplace potential of
     ``periodic_sum(LAPLACE, ...)``: each term of the same sums differentiated
