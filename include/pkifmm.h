@@ -121,6 +121,19 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes,
                        int leaf_max, int depth_max, int precision, int nrhs,
                        const char *cache_dir);
 
+/* A finite array of cells (Sec. 4: the far-field operator can describe other
+ * geometries, e.g. a channel of finite length): B0 and its copies shifted by
+ * n box_len along `axis` (0, 1, 2), |n| <= nimg (nimg >= 1), free in the other
+ * directions.  The adjacent copies are the root's colleagues in the octree
+ * (as for one periodic axis); the root operator is the plain free-space sum
+ * over the copies 2 <= |n| <= nimg (it does not depend on ell).  Every point
+ * must lie inside B0 (OUT_OF_BOX otherwise, no wrapping); no compatibility
+ * condition applies.  Other arguments and errors as pkifmm_plan_create. */
+int pkifmm_plan_create_finite(pkifmm_plan *out, int kernel, int axis, int nimg,
+                              const double box_lo[3], double box_len, int p, int ell,
+                              int leaf_max, int depth_max, int precision, int nrhs,
+                              const char *cache_dir);
+
 /* Evaluate potentials (Algorithm 2, Stage 2) on `cuda_stream` (a
  * cudaStream_t, NULL = legacy default stream).  Device pointers:
  *   src_xyz [S][3]            source positions
@@ -264,6 +277,12 @@ int pkifmm_root_operator(int kernel, unsigned periodic_axes, int p, int ell, dou
  * for a non-finite coordinate). */
 int pkifmm_morton_order_noalloc(int64_t n, const double *xyz, const double box_lo[3], double box_len,
                                 unsigned periodic_axes, int depth, int32_t *perm, void *cuda_stream);
+
+/* Host-only view of the root operator of a finite array of cells (see
+ * pkifmm_plan_create_finite): m_out [kn][kn], the free-space kernel from the
+ * upward equivalent surface of B0 to its downward check surface summed over
+ * the copies 2 <= |n| <= nimg along `axis`. */
+int pkifmm_root_operator_finite(int kernel, int axis, int nimg, int p, double *m_out);
 
 /* Stage 1 alone (Algorithm 2; Sec. 2.2-2.3, 3.1), without a plan, for
  * comparing and timing the host (where = 0) and device (where = 1) builds.

@@ -52,6 +52,9 @@ def load_library():
             lib.pkifmm_surface_singular_values.argtypes = [i, i, P]
             lib.pkifmm_backward_error.argtypes = [i, i, P]
             lib.pkifmm_root_operator.argtypes = [i, u, i, i, P]
+            lib.pkifmm_root_operator_finite.argtypes = [i, i, i, i, P]
+            lib.pkifmm_plan_create_finite.argtypes = [ctypes.POINTER(P), i, i, i, P, d, i, i, i, i, i, i,
+                                                      ctypes.c_char_p]
             lib.pkifmm_precompute_operators.argtypes = [i, u, i, i, i, i, P, P, P, P, P, P]
             lib.pkifmm_plan_destroy.argtypes = [P]
             lib.pkifmm_plan_destroy.restype = None
@@ -95,6 +98,24 @@ def pkifmm_plan_create(kernel, periodic_axes, box_lo, box_len, p, ell, leaf_max,
                                   leaf_max, depth_max, precision, nrhs,
                                   cache_dir.encode() if cache_dir else None))
     return h
+
+
+def pkifmm_plan_create_finite(kernel, axis, nimg, box_lo, box_len, p, ell, leaf_max, depth_max, precision, nrhs,
+                              cache_dir=None):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    lo = np.ascontiguousarray(box_lo, dtype=np.float64)
+    _check(lib.pkifmm_plan_create_finite(ctypes.byref(h), kernel, axis, nimg, _ptr(lo), float(box_len), p, ell,
+                                         leaf_max, depth_max, precision, nrhs,
+                                         cache_dir.encode() if cache_dir else None))
+    return h
+
+
+def pkifmm_root_operator_finite(kernel, axis, nimg, p):
+    kn = (6 * (p - 1) ** 2 + 2) * (1 if kernel == 0 else 3)
+    out = np.zeros((kn, kn))
+    _check(load_library().pkifmm_root_operator_finite(kernel, axis, nimg, p, _ptr(out)))
+    return out
 
 
 def pkifmm_evaluate(plan, S, src, dens, T, trg, pot, stream=None):
@@ -233,8 +254,10 @@ class PeriodicKIFMM:
     """Owns a plan; evaluate() passes torch CUDA tensors' device pointers."""
 
     def __init__(self, kernel, periodic_axes, box_lo=(0.0, 0.0, 0.0), box_len=1.0, p=6, ell=2,
-                 leaf_max=64, depth_max=10, precision=0, nrhs=1, cache_dir=None, precompute="device"):
-        """precompute: "device" (Stage 1 in CUDA kernels) or "host" (OpenMP)."""
+                 leaf_max=64, depth_max=10, precision=0, nrhs=1, cache_dir=None, precompute="device", images=None):
+        """precompute: "device" (Stage 1 in CUDA kernels) or "host" (OpenMP).
+        images: None for the periodic sums; an integer N >= 1 for a finite array
+        of cells along the single axis of periodic_axes (copies |n| <= N)."""
         if precompute not in ("device", "host"):
             raise ValueError("precompute must be 'device' or 'host'")
         # k: source density components; kt: target components
@@ -244,8 +267,15 @@ class PeriodicKIFMM:
         self.n = 6 * (p - 1) ** 2 + 2
         self.kn = self.n * self.k
         flags = PKIFMM_PRECOMPUTE_HOST if precompute == "host" else 0
-        self.handle = pkifmm_plan_create(kernel, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max,
-                                         precision | flags, nrhs, cache_dir)
+        if images is None:
+            self.handle = pkifmm_plan_create(kernel, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max,
+                                             precision | flags, nrhs, cache_dir)
+        else:
+            if periodic_axes not in (1, 2, 4):
+                raise ValueError("a finite array runs along one axis: periodic_axes 1, 2 or 4")
+            self.handle = pkifmm_plan_create_finite(kernel, {1: 0, 2: 1, 4: 2}[periodic_axes], images, box_lo,
+                                                    box_len, p, ell, leaf_max, depth_max, precision | flags, nrhs,
+                                                    cache_dir)
 
     def evaluate(self, src, dens, trg, pot=None, stream=None):
         """src [S,3], dens [nrhs,S,k], trg [T,3] float64 CUDA tensors -> pot [nrhs,T,k]."""

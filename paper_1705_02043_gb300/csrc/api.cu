@@ -172,7 +172,7 @@ const double *laplace_tp_constant(Plan &P, cudaStream_t s) {
 }
 
 bool needs_neutral(const Plan &P) {
-    if (!P.periodic) return false;
+    if (!P.periodic || P.nimg >= 0) return false;  // free space and finite arrays: finite sums
     if (P.kernel == PKIFMM_LAPLACE) return true;
     return P.periodic != 7;  // Stokes SP/DP: zero net force; TP allows a net force
 }
@@ -359,13 +359,14 @@ static void destroy_plan(pkifmm_plan_s *plan) {
 // One plan of an internal kernel (0 Laplace, 1 Stokes) with kt target components.
 static pkifmm_plan_s *make_plan(int kernel, int kt, unsigned periodic_axes, const double box_lo[3], double box_len,
                                 int p, int ell, int leaf_max, int depth_max, int precision, int nrhs,
-                                const char *cache_dir, bool host_stage1, int ks = 0) {
+                                const char *cache_dir, bool host_stage1, int ks = 0, int nimg = -1) {
     auto *h = new pkifmm_plan_s;
     Plan &P = h->P;
     P.kernel = kernel;
     P.k = kernel == 0 ? 1 : 3;
     P.kt = kt;
     P.ks = ks ? ks : P.k;
+    P.nimg = nimg;
     P.p = p;
     P.n = surface_count(p);
     P.kn = P.n * P.k;
@@ -385,8 +386,8 @@ static pkifmm_plan_s *make_plan(int kernel, int kt, unsigned periodic_axes, cons
         // the oracle (binary32 operators; see the tests).
         double eps = precision == PKIFMM_FP64 ? std::ldexp(1.0, -52) * P.kn : 1e-7;
         if (const char *e = std::getenv("PKIFMM_EPS_MIXED"); e && precision == PKIFMM_MIXED) eps = std::atof(e);
-        if (host_stage1) build_host_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
-        else build_device_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "");
+        if (host_stage1) build_host_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "", nimg);
+        else build_device_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "", nullptr, nimg);
         upload_operators(P);
         for (auto &e : P.ev) PK_CUDA(cudaEventCreate(&e));
         P.events = true;
@@ -397,7 +398,8 @@ static pkifmm_plan_s *make_plan(int kernel, int kt, unsigned periodic_axes, cons
     return h;
 }
 
-int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, const double box_lo[3],
+// nimg >= 0: a finite array of cells along the single periodic axis
+static int create_impl(pkifmm_plan *out, int kernel, unsigned periodic_axes, int nimg, const double box_lo[3],
                        double box_len, int p, int ell, int leaf_max, int depth_max, int precision, int nrhs,
                        const char *cache_dir) {
     if (!out) return fail(PKIFMM_ERR_INVALID_ARG, "out is NULL");
@@ -417,13 +419,13 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, con
         const int internal = (kernel == PKIFMM_LAPLACE || kernel == PKIFMM_LAPLACE_FIELD) ? 0 : 1;
         const int kt = kernel == PKIFMM_LAPLACE ? 1 : kernel == PKIFMM_LAPLACE_FIELD ? 4 : 3;
         pkifmm_plan_s *h = make_plan(internal, kt, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max,
-                                     precision, nrhs, cache_dir, host_stage1);
+                                     precision, nrhs, cache_dir, host_stage1, 0, nimg);
         h->kernel_id = kernel;
         if (kernel == PKIFMM_STOKES_PRESSURE) {
             try {
                 // the pressure: Laplace translations, dipole sources (the forces), one value per target
                 h->pressure = make_plan(0, 1, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max, precision,
-                                        nrhs, cache_dir, host_stage1, 3);
+                                        nrhs, cache_dir, host_stage1, 3, nimg);
                 h->pressure->kernel_id = -1;
             } catch (...) {
                 destroy_plan(h);
@@ -433,6 +435,24 @@ int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, con
         *out = h;
         return PKIFMM_OK;
     });
+}
+
+int pkifmm_plan_create(pkifmm_plan *out, int kernel, unsigned periodic_axes, const double box_lo[3],
+                       double box_len, int p, int ell, int leaf_max, int depth_max, int precision, int nrhs,
+                       const char *cache_dir) {
+    return create_impl(out, kernel, periodic_axes, -1, box_lo, box_len, p, ell, leaf_max, depth_max, precision, nrhs,
+                       cache_dir);
+}
+
+int pkifmm_plan_create_finite(pkifmm_plan *out, int kernel, int axis, int nimg, const double box_lo[3],
+                              double box_len, int p, int ell, int leaf_max, int depth_max, int precision, int nrhs,
+                              const char *cache_dir) {
+    if (axis < 0 || axis > 2 || nimg < 1 || nimg > (1 << 20)) {
+        if (out) *out = nullptr;
+        return fail(PKIFMM_ERR_INVALID_ARG, "axis must be 0..2 and the image count 1..2^20");
+    }
+    return create_impl(out, kernel, 1u << axis, nimg, box_lo, box_len, p, ell, leaf_max, depth_max, precision, nrhs,
+                       cache_dir);
 }
 
 int pkifmm_evaluate(pkifmm_plan plan, int64_t S, const double *src_xyz, const double *dens, int64_t T,
@@ -755,6 +775,17 @@ int pkifmm_root_operator(int kernel, unsigned periodic_axes, int p, int ell, dou
     if (!(periodic_axes == 7 || periodic_axes == 3 || sp)) return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built");
     return guarded([&]() {
         auto M = root_operator(kernel, p, periodic_axes, ell, surface_grid(p));
+        std::copy(M.begin(), M.end(), m_out);
+        return PKIFMM_OK;
+    });
+}
+
+int pkifmm_root_operator_finite(int kernel, int axis, int nimg, int p, double *m_out) {
+    if ((kernel != 0 && kernel != 1) || p < 2 || p > 16 || axis < 0 || axis > 2 || nimg < 0 || nimg > (1 << 20) ||
+        !m_out)
+        return fail(PKIFMM_ERR_INVALID_ARG, "bad argument");
+    return guarded([&]() {
+        auto M = root_operator(kernel, p, 1u << axis, 2, surface_grid(p), nimg);
         std::copy(M.begin(), M.end(), m_out);
         return PKIFMM_OK;
     });

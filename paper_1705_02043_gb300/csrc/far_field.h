@@ -335,5 +335,26 @@ PK_HD inline bool root_table_entry(int kernel, unsigned periodic, int ell, int p
     return true;
 }
 
+// Entry t of the root operator's table for a finite array of cells along
+// `axis` (the cell and its copies shifted by n e, |n| <= nimg; the
+// finite-length channel of Sec. 4): the plain free-space sum over the copies
+// that are not the root's colleagues, 2 <= |n| <= nimg.  Same lattice as above.
+PK_HD inline void finite_table_entry(int kernel, int axis, int nimg, int p, double inner_half, int t, double *acc) {
+    const int w = 2 * p - 1, k = kernel == 0 ? 1 : 3;
+    const int di = t / (w * w) - (p - 1), dj = (t / w) % w - (p - 1), dk = t % w - (p - 1);
+    const double step = 2.0 * inner_half / (p - 1);
+    const double r[3] = {di * step, dj * step, dk * step};
+    Neumaier s[9];
+    double blk[9], zero[3] = {0, 0, 0};
+    for (int n = nimg; n >= 2; n--)
+        for (int sg = -1; sg <= 1; sg += 2) {
+            double d[3] = {r[0], r[1], r[2]};
+            d[axis] += sg * n;
+            kernel_block(kernel, d, zero, blk);
+            for (int i = 0; i < k * k; i++) s[i].add(blk[i]);
+        }
+    for (int i = 0; i < k * k; i++) acc[i] = s[i].get();
+}
+
 }  // namespace ff
 }  // namespace pk

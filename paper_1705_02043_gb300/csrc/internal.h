@@ -106,6 +106,7 @@ struct Plan {
     int kernel = 0, k = 1, p = 0, n = 0, kn = 0, ell = 2, leaf_max = 64, depth_max = 10;
     int kt = 1;  // target components: k, or 4 for the Laplace field (potential and gradient)
     int ks = 1;  // source density components: k, or 3 for Laplace dipole sources
+    int nimg = -1;  // >= 0: finite array of cells along the periodic axis (no wrap, no compatibility condition)
     int precision = 0, nrhs = 1, device = 0;
     unsigned periodic = 0;
     double lo[3] = {0, 0, 0}, L = 1;

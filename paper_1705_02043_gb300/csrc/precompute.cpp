@@ -166,16 +166,24 @@ void far_kernel_block(int kernel, unsigned periodic, int ell, const double *r, d
 }
 
 std::vector<double> root_operator(int kernel, int p, unsigned periodic, int ell,
-                                  const std::vector<double> &g) {
+                                  const std::vector<double> &g, int nimg) {
     int k = kernel == 0 ? 1 : 3, n = (int)g.size() / 3, kn = n * k, w = 2 * p - 1;
     // table of K^{P,F} + near-layer images 2..ell on the difference lattice
     std::vector<double> tab((size_t)w * w * w * k * k);
-    double probe[9], r0[3] = {0, 0, 0};
-    if (!ff::far_kernel_block(kernel, periodic, ell, r0, probe))
-        throw std::runtime_error("root operator: periodicity not supported");
+    const int axis = periodic == 1 ? 0 : periodic == 2 ? 1 : 2;
+    if (nimg >= 0) {
+        if (!(periodic == 1 || periodic == 2 || periodic == 4))
+            throw std::runtime_error("root operator: a finite array runs along one axis");
+    } else {
+        double probe[9], r0[3] = {0, 0, 0};
+        if (!ff::far_kernel_block(kernel, periodic, ell, r0, probe))
+            throw std::runtime_error("root operator: periodicity not supported");
+    }
 #pragma omp parallel for schedule(dynamic, 8)
-    for (int t = 0; t < w * w * w; t++)
-        ff::root_table_entry(kernel, periodic, ell, p, kInnerHalf, t, &tab[(size_t)t * k * k]);
+    for (int t = 0; t < w * w * w; t++) {
+        if (nimg >= 0) ff::finite_table_entry(kernel, axis, nimg, p, kInnerHalf, t, &tab[(size_t)t * k * k]);
+        else ff::root_table_entry(kernel, periodic, ell, p, kInnerHalf, t, &tab[(size_t)t * k * k]);
+    }
     std::vector<double> Mr((size_t)kn * kn);
     for (int i = 0; i < n; i++)
         for (int j = 0; j < n; j++) {
@@ -205,7 +213,9 @@ std::string cache_path(const std::string &dir, const HostOps &o) {
     char buf[256];
     std::snprintf(buf, sizeof buf, "/pkifmm_k%d_p%d_per%u_l%d_e%.3e_v%d.bin", o.kernel, o.p, o.periodic,
                   o.ell, o.eps_rel, kVersion);
-    return dir + buf;
+    std::string name = buf;
+    if (o.nimg >= 0) name.insert(name.size() - 4, "_n" + std::to_string(o.nimg));  // finite arrays
+    return dir + name;
 }
 
 std::vector<std::vector<double> *> payload(HostOps &o) {
@@ -260,7 +270,8 @@ void save_cache(const std::string &path, HostOps &o) {
 
 }  // namespace
 
-void init_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell, double eps_rel) {
+void init_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell, double eps_rel, int nimg) {
+    o.nimg = nimg;
     o.kernel = kernel;
     o.k = kernel == 0 ? 1 : 3;
     o.p = p;
@@ -299,8 +310,8 @@ void c2e_factors(HostOps &o) {
 }
 
 void build_host_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell, double eps_rel,
-                    const std::string &cache_dir) {
-    init_ops(o, kernel, p, periodic, ell, eps_rel);
+                    const std::string &cache_dir, int nimg) {
+    init_ops(o, kernel, p, periodic, ell, eps_rel, nimg);
     const int kn = o.kn, n = o.n;
     bool cached = load_cached_ops(o, cache_dir);
     if (!cached) {
@@ -340,7 +351,7 @@ void build_host_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell, d
             matmul(kn, kn, kn, o.dc2e_b.data(), K.data(), tmp.data());
             matmul(kn, kn, kn, o.dc2e_a.data(), tmp.data(), &o.l2l[(size_t)c * kn * kn]);
         }
-        if (periodic) o.root = root_operator(kernel, p, periodic, ell, o.g);
+        if (periodic) o.root = root_operator(kernel, p, periodic, ell, o.g, nimg);
         else o.root.clear();
         save_cached_ops(o, cache_dir);
     }

@@ -32,6 +32,7 @@ struct HostOps {
     int kernel = 0, k = 1, p = 0, n = 0, kn = 0;
     unsigned periodic = 0;
     int ell = 0;
+    int nimg = -1;                  // >= 0: finite array of cells along the periodic axis (copies |n| <= nimg)
     double eps_rel = 0;             // singular values <= eps_rel * s_max are dropped
     std::vector<double> g;          // [n][3] unit surface grid
     std::vector<double> U, S, V;    // SVD of A_up1 = K(1.475 g, 0.525 g)
@@ -46,7 +47,7 @@ struct HostOps {
 // Pieces shared by the host and device builds: field set-up and surface grid;
 // the operator cache (false / no-op for an empty directory); the
 // check-to-equivalent factors (V S+, U^T, U S+, V^T) from U, S, V and eps_rel.
-void init_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell, double eps_rel);
+void init_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell, double eps_rel, int nimg = -1);
 bool load_cached_ops(HostOps &o, const std::string &cache_dir);
 void save_cached_ops(HostOps &o, const std::string &cache_dir);
 void c2e_factors(HostOps &o);
@@ -54,15 +55,16 @@ void c2e_factors(HostOps &o);
 // Build all host operators; throws std::runtime_error on failure.
 // cache_dir may be empty.
 void build_host_ops(HostOps &ops, int kernel, int p, unsigned periodic, int ell,
-                    double eps_rel, const std::string &cache_dir);
+                    double eps_rel, const std::string &cache_dir, int nimg = -1);
 
 // K^{P,F}_ell(r) block for a unit periodic box, r a difference vector with
 // |r_a| <= ~1.1; periodic in the axes of `periodic`.
 void far_kernel_block(int kernel, unsigned periodic, int ell, const double *r, double *out);
 
 // Root operator M[kn][kn] = K^{P,F}_ell(x^d, y^u) + sum_{1<|p|<=ell} K(x^d, y^u + p).
+// nimg >= 0: the finite array of cells along the periodic axis instead.
 std::vector<double> root_operator(int kernel, int p, unsigned periodic, int ell,
-                                  const std::vector<double> &g);
+                                  const std::vector<double> &g, int nimg = -1);
 
 void matmul(int m, int n, int kk, const double *A, const double *B, double *C);  // C = A B
 
@@ -74,6 +76,6 @@ void matmul(int m, int n, int kk, const double *A, const double *B, double *C); 
 // and the root table, then the number of Jacobi sweeps (the last one rotating
 // nothing); left untouched when the operators come from the cache.
 void build_device_ops(HostOps &ops, int kernel, int p, unsigned periodic, int ell,
-                      double eps_rel, const std::string &cache_dir, double *phases = nullptr);
+                      double eps_rel, const std::string &cache_dir, double *phases = nullptr, int nimg = -1);
 
 }  // namespace pk

@@ -17,7 +17,8 @@
 // * M2M and L2L: (V S+) (U^T K) for the 8 octants, two batched binary64
 //   GEMMs per family;
 // * root operator: the K^{P,F}_ell table on the difference lattice of the
-//   surface grid (far_field.h, one thread per entry), then scattered to the
+//   surface grid (far_field.h, one thread per entry; for a finite array of
+//   cells the plain sum over the non-adjacent copies), then scattered to the
 //   kn x kn matrix.
 // The check-to-equivalent factors themselves (O(kn^2) scalings of U, S, V)
 // are formed on the host from the copied-back SVD, as in the host build.
@@ -370,12 +371,14 @@ void dgemm(int m, int n, int kk, const double *A, long long sA, const double *B,
 
 // One thread per table entry, launched in 32-thread blocks so that the few
 // hundred warps spread over all SMs (each runs a long binary64 Ewald sum).
-__global__ void k_root_table(int kernel, unsigned periodic, int ell, int p, int entries, double *__restrict__ tab) {
+__global__ void k_root_table(int kernel, unsigned periodic, int ell, int nimg, int p, int entries,
+                             double *__restrict__ tab) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= entries) return;
     const int k = kernel == 0 ? 1 : 3;
     double acc[9];
-    ff::root_table_entry(kernel, periodic, ell, p, kInnerHalf, t, acc);
+    if (nimg >= 0) ff::finite_table_entry(kernel, periodic == 1 ? 0 : periodic == 2 ? 1 : 2, nimg, p, kInnerHalf, t, acc);
+    else ff::root_table_entry(kernel, periodic, ell, p, kInnerHalf, t, acc);
     for (int i = 0; i < k * k; i++) tab[(size_t)t * k * k + i] = acc[i];
 }
 
@@ -402,8 +405,8 @@ void to_host(std::vector<T> &h, const T *d, size_t n, cudaStream_t s) {
 }  // namespace
 
 void build_device_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell, double eps_rel,
-                      const std::string &cache_dir, double *phases) {
-    init_ops(o, kernel, p, periodic, ell, eps_rel);
+                      const std::string &cache_dir, double *phases, int nimg) {
+    init_ops(o, kernel, p, periodic, ell, eps_rel, nimg);
     using clk = std::chrono::steady_clock;
     auto t_mark = clk::now();
     auto lap = [&](int i) {
@@ -415,7 +418,10 @@ void build_device_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell,
         c2e_factors(o);
         return;
     }
-    if (periodic) {  // validate the mask before any device work
+    if (nimg >= 0) {  // validate the mask before any device work
+        if (!(periodic == 1 || periodic == 2 || periodic == 4))
+            throw Error(PKIFMM_ERR_UNSUPPORTED, "root operator: a finite array runs along one axis");
+    } else if (periodic) {
         double probe[9], r0[3] = {0, 0, 0};
         if (!ff::far_kernel_block(kernel, periodic, ell, r0, probe))
             throw Error(PKIFMM_ERR_UNSUPPORTED, "root operator: periodicity not supported");
@@ -512,7 +518,8 @@ void build_device_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell,
     if (periodic) {
         const int w = 2 * p - 1, entries = w * w * w;
         DevArr<double> tab((size_t)entries * k * k), Mr(kn2);
-        count_launch(), k_root_table<<<nblocks(entries, 32), 32, 0, s>>>(kernel, periodic, ell, p, entries, tab.p);
+        count_launch(), k_root_table<<<nblocks(entries, 32), 32, 0, s>>>(kernel, periodic, ell, nimg, p, entries,
+                                                                         tab.p);
         count_launch(), k_root_scatter<<<nblocks(nn, 256), 256, 0, s>>>(tab.p, g.p, n, p, k, Mr.p);
         PK_CUDA(cudaGetLastError());
         to_host(o.root, Mr.p, kn2, s);

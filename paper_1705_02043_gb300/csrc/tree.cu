@@ -665,6 +665,8 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
     int pbits = 0;
     while ((1LL << pbits) < P.nprob) pbits++;
     const int key_bits = 3 * D + pbits;  // problem index above the Morton bits
+    // periodic axes wrap; a finite array of cells keeps every point inside the cell
+    const unsigned wrap = P.nimg >= 0 ? 0u : P.periodic;
     P.err.reserve(4);
     PK_CUDA(cudaMemsetAsync(P.err.p, 0, sizeof(int) * 4, s));
     P.keyS.reserve(S + 1);
@@ -676,7 +678,7 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
     DBuf<double> xn;
     xn.reserve(3 * std::max(S, T) + 3);
     if (S) {
-        count_launch(), k_keys<<<blocks(S, 256), 256, 0, s>>>(src, S, P.lo[0], P.lo[1], P.lo[2], P.L, P.periodic, D, xn.p,
+        count_launch(), k_keys<<<blocks(S, 256), 256, 0, s>>>(src, S, P.lo[0], P.lo[1], P.lo[2], P.L, wrap, D, xn.p,
                                               P.keyS.p, P.idxS.p, P.err.p, P.nprob > 1 ? P.soff.p : nullptr,
                                               P.nprob);
         radix_sort(P.keyS, P.idxS, P.keyS2, P.idxS2, P.hist, (int)S, key_bits, s);
@@ -691,7 +693,7 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
         PK_CUDA(cudaMemcpyAsync(P.idxT.p, P.idxS.p, sizeof(int) * T, cudaMemcpyDeviceToDevice, s));
         PK_CUDA(cudaMemcpyAsync(P.xt.p, P.xs.p, sizeof(double) * 3 * T, cudaMemcpyDeviceToDevice, s));
     } else if (T) {
-        count_launch(), k_keys<<<blocks(T, 256), 256, 0, s>>>(trg, T, P.lo[0], P.lo[1], P.lo[2], P.L, P.periodic, D, xn.p,
+        count_launch(), k_keys<<<blocks(T, 256), 256, 0, s>>>(trg, T, P.lo[0], P.lo[1], P.lo[2], P.L, wrap, D, xn.p,
                                               P.keyT.p, P.idxT.p, P.err.p, P.nprob > 1 ? P.toff.p : nullptr,
                                               P.nprob);
         radix_sort(P.keyT, P.idxT, P.keyT2, P.idxT2, P.hist, (int)T, key_bits, s);

@@ -191,3 +191,29 @@ def test_precompute_entry_host_build():
         b.pkifmm_precompute_operators(0, 7, 5, 2, pk.FP64, 2)
     with pytest.raises(pk.PKIFMMError):
         b.pkifmm_precompute_operators(0, 5, 5, 2, pk.FP64, 0)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_finite_array_root_operator(kernel):
+    # a finite array of cells: the root operator is the free-space kernel from
+    # the root's upward equivalent surface to its downward check surface (both
+    # 0.525 g in the unit cell) summed over the copies 2 <= |n| <= N
+    from paper_1705_02043_gb300 import _binding as b
+    p, axis, N = 4, 1, 5
+    g = np.array([(-1 + 2 * i / (p - 1), -1 + 2 * j / (p - 1), -1 + 2 * k / (p - 1))
+                  for i in range(p) for j in range(p) for k in range(p)
+                  if not (0 < i < p - 1 and 0 < j < p - 1 and 0 < k < p - 1)])
+    r = 0.525 * (g[:, None, :] - g[None, :, :])
+    ref = 0.0
+    for n in list(range(-N, -1)) + list(range(2, N + 1)):
+        d = r.copy()
+        d[..., axis] += n
+        rr = np.linalg.norm(d, axis=-1)
+        if kernel == 0:
+            ref = ref + 1.0 / rr
+        else:
+            blk = (np.eye(3) / rr[..., None, None] + d[..., :, None] * d[..., None, :] / rr[..., None, None] ** 3)
+            ref = ref + (blk / (8 * np.pi)).transpose(0, 2, 1, 3).reshape(len(g) * 3, len(g) * 3)
+    M = b.pkifmm_root_operator_finite(kernel, axis, N, p)
+    assert np.abs(M - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert not np.any(b.pkifmm_root_operator_finite(kernel, axis, 1, p))  # only adjacent copies: no far field
