@@ -38,7 +38,7 @@ def test_finite_array_fp64(kernel, mask, nimg):
     ref = oracle.finite_array(kernel, {1: 0, 2: 1, 4: 2}[mask], nimg, x, d, x[idx])
     e = rel_l2(u[idx], ref)
     print(f"finite array kernel {kernel} axis mask {mask} N={nimg}: rel_l2 {e:.2e}")
-    assert e < 1e-6
+    assert e < 1e-7  # measured 3e-10..3e-8 at p = 10
 
 
 def test_finite_array_mixed():
@@ -47,7 +47,7 @@ def test_finite_array_mixed():
     idx = np.arange(0, len(x), 401)
     e = rel_l2(u[idx], oracle.finite_array(1, 1, 10, x, f[0], x[idx]))
     print(f"finite array mixed: rel_l2 {e:.2e}")
-    assert e < 3e-5
+    assert e < 2e-5  # measured 5.4e-6
 
 
 def test_finite_array_points_stay_in_the_cell():
