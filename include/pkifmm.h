@@ -92,15 +92,19 @@ enum {
     PKIFMM_ERR_OOM = -5,          /* device or host allocation failed */
     PKIFMM_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
     PKIFMM_ERR_CACHE = -7,        /* operator cache unreadable / unwritable */
-    PKIFMM_ERR_UNSUPPORTED = -8   /* combination not built (DP in x-z or y-z; MIXED without tcgen05) */
+    PKIFMM_ERR_UNSUPPORTED = -8   /* combination not built (MIXED without tcgen05) */
 };
 
 /* Build a plan: Algorithm 2, Stage 1 (precompute), Sec. 2.2-2.3.
  *   kernel         PKIFMM_LAPLACE or PKIFMM_STOKES
  *   periodic_axes  bit 0 = x, bit 1 = y, bit 2 = z; 0 = free space.
- *                  Built for both kernels: 0 (free space), one axis
- *                  (SP: 1, 2 or 4), 3 (DP in x and y), 7 (TP).  The
- *                  other doubly periodic pairs (5, 6) return UNSUPPORTED.
+ *                  Every mask is built: 0 (free space), one axis (SP: 1,
+ *                  2 or 4), two axes (DP: 3, 5, 6), 7 (TP).  DP in (x, z)
+ *                  or (y, z) runs the (x, y) operators in a frame whose
+ *                  axes are permuted so the free axis is last (points,
+ *                  vector densities and vector results are carried into
+ *                  it and back; the tree and list exports are in that
+ *                  frame).
  *   box_lo, box_len  B0 = [box_lo, box_lo + box_len)^3 (host pointer, 3 doubles)
  *   p              points per edge of the equivalent/check surfaces (Sec. 2.2,
  *                  n = 6(p-1)^2 + 2), 4 <= p <= 16

@@ -16,6 +16,11 @@ struct pkifmm_plan_s {
     int kernel_id = 0;                   // the public kernel (PKIFMM_*)
     pkifmm_plan_s *pressure = nullptr;   // PKIFMM_STOKES_PRESSURE: the Laplace plan with dipole sources
     pk::DBuf<double> cbuf;               // its scratch: velocities, pressures
+    // doubly periodic in (x, z) or (y, z): the plans run the (x, y) case on
+    // permuted coordinates, x'_a = x_{perm[a]} (the free axis last)
+    int perm[3] = {0, 1, 2};
+    bool permuted = false;
+    pk::DBuf<double> pbuf;               // permuted points, densities and results
     int ks() const { return P.ks; }      // source density components
     int kt() const { return pressure ? 4 : P.kt; }
 };
@@ -76,6 +81,25 @@ __global__ void k_velocity_pressure(const double *__restrict__ vel, const double
     if (i >= T * nrhs) return;
     for (int a = 0; a < 3; a++) pot[i * 4 + a] = vel[i * 3 + a];
     pot[i * 4 + 3] = pres[i];
+}
+
+// Items of `stride` doubles: components off..off+2 are a vector, permuted
+// out[off + a] = in[off + perm[a]] (forward) or out[off + perm[a]] = in[off + a]
+// (inverse); the others are copied.  Rotating the frame by an axis permutation
+// leaves the Laplace and Stokes kernels' form unchanged (both are isotropic).
+__global__ void k_permute(const double *__restrict__ in, long long n, int stride, int off, int p0, int p1, int p2,
+                          int inverse, double *__restrict__ out) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *a = in + i * stride;
+    double *b = out + i * stride;
+    for (int c = 0; c < stride; c++) b[c] = a[c];
+    if (off < 0) return;
+    const int pm[3] = {p0, p1, p2};
+    for (int c = 0; c < 3; c++) {
+        if (inverse) b[off + pm[c]] = a[off + c];
+        else b[off + c] = a[off + pm[c]];
+    }
 }
 
 // sums[2*(j*nk+c)] += phi, sums[2*(j*nk+c)+1] += |phi| per problem j (blockIdx.z,
@@ -268,8 +292,48 @@ int evaluate_impl(Plan &P, int nprob, const int64_t *soff, const int64_t *toff, 
 // Any plan: the Stokes velocity-pressure plan runs the velocity evaluation,
 // then the pressure as the Laplace potential of dipoles f at the sources
 // (p = sum f.r/(4 pi r^3)), and interleaves them; the others evaluate directly.
+int evaluate_plain(pkifmm_plan_s *h, int nprob, const int64_t *soff, const int64_t *toff, const double *src,
+                   const double *dens, const double *trg, double *pot, cudaStream_t s);
+
+// Doubly periodic in (x, z) or (y, z): points, vector densities and vector
+// results are carried into the frame where the free axis is z, evaluated
+// there, and the results carried back.
 int evaluate_any(pkifmm_plan_s *h, int nprob, const int64_t *soff, const int64_t *toff, const double *src,
                  const double *dens, const double *trg, double *pot, cudaStream_t s) {
+    if (!h->permuted) return evaluate_plain(h, nprob, soff, toff, src, dens, trg, pot, s);
+    if (nprob < 1 || !soff || !toff) return fail(PKIFMM_ERR_INVALID_ARG, "nprob < 1 or NULL offsets");
+    const int64_t S = soff[nprob], T = toff[nprob];
+    if (S < 0 || T < 0 || S > (1LL << 30) || T > (1LL << 30)) return fail(PKIFMM_ERR_INVALID_ARG, "S, T out of range");
+    if ((S && (!src || !dens)) || (T && (!trg || !pot))) return fail(PKIFMM_ERR_INVALID_ARG, "NULL array");
+    Plan &P = h->P;
+    PK_CUDA(cudaSetDevice(P.device));
+    const int nr = P.nrhs, ks = h->ks(), kt = h->kt();
+    const size_t ns = 3 * (size_t)S, nd = (size_t)nr * S * ks, nt = 3 * (size_t)T, np = (size_t)nr * T * kt;
+    h->pbuf.reserve(ns + nd + nt + np + 8);
+    double *ps = h->pbuf.p, *pd = ps + ns, *pt = pd + nd, *pp = pt + nt;
+    const int *m = h->perm;
+    auto launch = [&](const double *in, long long n, int stride, int off, int inv, double *out) {
+        if (n > 0)
+            count_launch(), k_permute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, n, stride, off, m[0], m[1], m[2],
+                                                                                 inv, out);
+    };
+    launch(src, S, 3, 0, 0, ps);
+    launch(dens, (long long)nr * S, ks, ks == 3 ? 0 : -1, 0, pd);
+    launch(trg, T, 3, 0, 0, pt);
+    PK_CUDA(cudaGetLastError());
+    // targets that are the sources stay the sources (one sort)
+    int rc = evaluate_plain(h, nprob, soff, toff, ps, pd, trg == src ? ps : pt, pp, s);
+    if (rc != PKIFMM_OK) return rc;
+    // vector part of the results: velocity (k_t 3, or 0..2 of the pressure kernel),
+    // the gradient of the Laplace field (1..3)
+    const int off = kt == 3 ? 0 : (kt == 4 && h->kernel_id == PKIFMM_LAPLACE_FIELD) ? 1 : kt == 4 ? 0 : -1;
+    launch(pp, (long long)nr * T, kt, off, 1, pot);
+    PK_CUDA(cudaGetLastError());
+    return PKIFMM_OK;
+}
+
+int evaluate_plain(pkifmm_plan_s *h, int nprob, const int64_t *soff, const int64_t *toff, const double *src,
+                   const double *dens, const double *trg, double *pot, cudaStream_t s) {
     if (!h->pressure) return evaluate_impl(h->P, nprob, soff, toff, src, dens, trg, pot, s);
     if (nprob < 1 || !soff || !toff) return fail(PKIFMM_ERR_INVALID_ARG, "nprob < 1 or NULL offsets");
     Plan &P = h->P;
@@ -303,6 +367,7 @@ static void destroy_plan(pkifmm_plan_s *plan) {
     destroy_plan(plan->pressure);
     plan->pressure = nullptr;
     plan->cbuf.release();
+    plan->pbuf.release();
     Plan &P = plan->P;
     cudaSetDevice(P.device);
     cudaDeviceSynchronize();
@@ -412,15 +477,33 @@ static int create_impl(pkifmm_plan *out, int kernel, unsigned periodic_axes, int
     if (p < 4 || p > 16 || ell < 1 || ell > 8 || leaf_max < 1 || depth_max < 1 || depth_max > kMaxLevel - 1 ||
         nrhs < 1 || nrhs > 64 || (precision != PKIFMM_FP64 && precision != PKIFMM_MIXED))
         return fail(PKIFMM_ERR_INVALID_ARG, "p / ell / leaf_max / depth_max / nrhs / precision out of range");
-    bool sp = periodic_axes == 1 || periodic_axes == 2 || periodic_axes == 4;
-    if (!(periodic_axes == 0 || periodic_axes == 7 || periodic_axes == 3 || sp))
-        return fail(PKIFMM_ERR_UNSUPPORTED, "periodicity not built (doubly periodic: x and y only)");
+    // doubly periodic in (x, z) or (y, z): the (x, y) plans in a permuted frame
+    int perm[3] = {0, 1, 2};
+    const bool permuted = periodic_axes == 5 || periodic_axes == 6;
+    if (periodic_axes == 5) {  // x' = x, y' = z, z' = y
+        perm[1] = 2;
+        perm[2] = 1;
+    } else if (periodic_axes == 6) {  // x' = y, y' = z, z' = x
+        perm[0] = 1;
+        perm[1] = 2;
+        perm[2] = 0;
+    }
+    double lo_p[3] = {0, 0, 0};
+    if (box_lo)
+        for (int a = 0; a < 3; a++) lo_p[a] = box_lo[perm[a]];
+    if (permuted) {
+        periodic_axes = 3;
+        if (nimg >= 0) return fail(PKIFMM_ERR_INVALID_ARG, "finite arrays run along one axis");
+    }
+    if (box_lo) box_lo = lo_p;
     return guarded([&]() {
         const int internal = (kernel == PKIFMM_LAPLACE || kernel == PKIFMM_LAPLACE_FIELD) ? 0 : 1;
         const int kt = kernel == PKIFMM_LAPLACE ? 1 : kernel == PKIFMM_LAPLACE_FIELD ? 4 : 3;
         pkifmm_plan_s *h = make_plan(internal, kt, periodic_axes, box_lo, box_len, p, ell, leaf_max, depth_max,
                                      precision, nrhs, cache_dir, host_stage1, 0, nimg);
         h->kernel_id = kernel;
+        h->permuted = permuted;
+        for (int a = 0; a < 3; a++) h->perm[a] = perm[a];
         if (kernel == PKIFMM_STOKES_PRESSURE) {
             try {
                 // the pressure: Laplace translations, dipole sources (the forces), one value per target

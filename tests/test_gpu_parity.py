@@ -155,9 +155,10 @@ def test_error_codes(cache):
     with pytest.raises(pk.PKIFMMError) as e:
         run(1, 7, y, np.ones((300, 3)), y, p=4, cache_dir=cache)
     assert e.value.name == "INVALID_ARG"
+    from paper_1705_02043_gb300 import _binding as b
     with pytest.raises(pk.PKIFMMError) as e:
-        pk.PeriodicKIFMM(1, 6, p=6)  # doubly periodic in y and z is not built
-    assert e.value.name == "UNSUPPORTED"
+        b.pkifmm_plan_create_finite(1, 3, 2, (0.0, 0.0, 0.0), 1.0, 6, 2, 40, 10, 0, 1)  # no axis 3
+    assert e.value.name == "INVALID_ARG"
 
 
 def test_empty_inputs(cache):

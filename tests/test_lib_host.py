@@ -167,7 +167,7 @@ def test_root_operator_independent_of_ell(kernel, periodic):
 
 def test_unsupported_and_invalid_arguments():
     with pytest.raises(pk.PKIFMMError) as e:
-        pk.pkifmm_root_operator(1, 5, 4, 2)  # doubly periodic in x and z: not built
+        pk.pkifmm_root_operator(1, 5, 4, 2)  # built for (x, y); plans run (x, z), (y, z) in a permuted frame
     assert e.value.name == "UNSUPPORTED"
     with pytest.raises(pk.PKIFMMError) as e:
         pk.pkifmm_root_operator(0, 7, 1, 2)
