@@ -251,11 +251,20 @@ def pkifmm_strerror(code):
 
 
 class PeriodicKIFMM:
-    """Owns a plan; evaluate() passes torch CUDA tensors' device pointers."""
+    """Owns a plan; evaluate() passes torch CUDA tensors' device pointers.
+
+    kernel: LAPLACE (charges -> potential), STOKES (forces -> velocity),
+    LAPLACE_FIELD (charges -> potential and gradient), STOKES_PRESSURE (forces
+    -> velocity and pressure).  periodic_axes: bit 0 = x, 1 = y, 2 = z (0 free,
+    7 triply periodic).  Densities [nrhs, S, k], results [nrhs, T, kt]
+    (self.k, self.kt)."""
 
     def __init__(self, kernel, periodic_axes, box_lo=(0.0, 0.0, 0.0), box_len=1.0, p=6, ell=2,
                  leaf_max=64, depth_max=10, precision=0, nrhs=1, cache_dir=None, precompute="device", images=None):
-        """precompute: "device" (Stage 1 in CUDA kernels) or "host" (OpenMP).
+        """p: surface points per edge (accuracy); ell: image layers in the near
+        sum; leaf_max: points per leaf (s); precision: FP64 or MIXED; nrhs:
+        density vectors evaluated together; cache_dir: Stage 1 operator cache.
+        precompute: "device" (Stage 1 in CUDA kernels) or "host" (OpenMP).
         images: None for the periodic sums; an integer N >= 1 for a finite array
         of cells along the single axis of periodic_axes (copies |n| <= N)."""
         if precompute not in ("device", "host"):
