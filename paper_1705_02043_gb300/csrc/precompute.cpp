@@ -82,16 +82,62 @@ void matmul(int m, int n, int kk, const double *A, const double *B, double *C) {
     }
 }
 
-// One-sided (Hestenes) Jacobi: orthogonalise the columns of A by plane
-// rotations, accumulating them in V.  Pairs are scheduled round-robin so the
-// m/2 rotations of one round are independent.  Columns are stored as rows
-// (At = A^T) for contiguous access.
+// One-sided (Hestenes) Jacobi preconditioned by QR with column pivoting
+// (Drmac and Veselic): A P = Q R by Householder reflectors, then the columns of
+// R^T are orthogonalised by plane rotations accumulated in Vt, so that
+// R^T = U_x S V_x^T and A = (Q V_x) S (P U_x)^T; on these matrices the
+// rotations settle in about a third of the sweeps plain Jacobi on A needs.
+// Pairs are scheduled round-robin so the m/2 rotations of one round are
+// independent.  Columns are stored as rows for contiguous access.
 void jacobi_svd(int m, const std::vector<double> &A, std::vector<double> &U,
                 std::vector<double> &S, std::vector<double> &V) {
     int mm = m + (m & 1);  // even player count; index m (if odd) is a bye
-    std::vector<double> At((size_t)m * m), Vt((size_t)m * m, 0.0);
+    // ---- A P = Q R: W holds the columns of A as rows; reflector k in hv[k] ----
+    std::vector<double> W((size_t)m * m), hv((size_t)m * m, 0.0), tau(m, 0.0), c2(m);
+    std::vector<int> perm(m);
+    std::iota(perm.begin(), perm.end(), 0);
     for (int i = 0; i < m; i++)
-        for (int j = 0; j < m; j++) At[(size_t)j * m + i] = A[(size_t)i * m + j];
+        for (int j = 0; j < m; j++) W[(size_t)j * m + i] = A[(size_t)i * m + j];
+    for (int j = 0; j < m; j++) {
+        double v = 0;
+        for (int i = 0; i < m; i++) v += W[(size_t)j * m + i] * W[(size_t)j * m + i];
+        c2[j] = v;
+    }
+    for (int k = 0; k < m; k++) {
+        int js = k;  // largest trailing norm, lowest index on ties
+        for (int j = k + 1; j < m; j++)
+            if (c2[j] > c2[js]) js = j;
+        if (js != k) {
+            std::swap_ranges(W.begin() + (size_t)k * m, W.begin() + (size_t)(k + 1) * m, W.begin() + (size_t)js * m);
+            std::swap(c2[k], c2[js]);
+            std::swap(perm[k], perm[js]);
+        }
+        double *x = &W[(size_t)k * m], ss = 0;
+        for (int i = k; i < m; i++) ss += x[i] * x[i];
+        const double x0 = x[k], nrm = std::sqrt(ss), alpha = x0 >= 0 ? -nrm : nrm, v0 = x0 - alpha;
+        const double vn2 = ss - x0 * x0 + v0 * v0, t = vn2 > 0 ? 2.0 / vn2 : 0.0;
+        double *v = &hv[(size_t)k * m];
+        v[k] = v0;
+        for (int i = k + 1; i < m; i++) v[i] = x[i];
+        tau[k] = t;
+        x[k] = alpha;
+        for (int i = k + 1; i < m; i++) x[i] = 0.0;
+#pragma omp parallel for schedule(static)
+        for (int j = k + 1; j < m; j++) {
+            double *w = &W[(size_t)j * m], d = 0, n2 = 0;
+            for (int i = k; i < m; i++) d += v[i] * w[i];
+            d *= t;
+            for (int i = k; i < m; i++) {
+                w[i] -= d * v[i];
+                if (i > k) n2 += w[i] * w[i];
+            }
+            c2[j] = n2;
+        }
+    }
+    // ---- Jacobi on the columns of R^T (the rows of R) ----
+    std::vector<double> At((size_t)m * m, 0.0), Vt((size_t)m * m, 0.0);
+    for (int i = 0; i < m; i++)
+        for (int j = i; j < m; j++) At[(size_t)i * m + j] = W[(size_t)j * m + i];
     for (int i = 0; i < m; i++) Vt[(size_t)i * m + i] = 1.0;
     std::vector<int> ring(mm);
     std::iota(ring.begin(), ring.end(), 0);
@@ -135,6 +181,19 @@ void jacobi_svd(int m, const std::vector<double> &A, std::vector<double> &U,
         }
         if (rotations == 0) break;
     }
+    // Q V_x: the reflectors applied in reverse order to the rows of Vt
+    for (int k = m - 1; k >= 0; k--) {
+        const double t = tau[k];
+        if (t == 0.0) continue;
+        const double *v = &hv[(size_t)k * m];
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < m; j++) {
+            double *y = &Vt[(size_t)j * m], d = 0;
+            for (int i = k; i < m; i++) d += v[i] * y[i];
+            d *= t;
+            for (int i = k; i < m; i++) y[i] -= d * v[i];
+        }
+    }
     std::vector<double> sig(m);
     for (int j = 0; j < m; j++) {
         double s = 0;
@@ -152,8 +211,8 @@ void jacobi_svd(int m, const std::vector<double> &A, std::vector<double> &U,
         S[jj] = sig[j];
         double inv = sig[j] > 0 ? 1.0 / sig[j] : 0.0;
         for (int i = 0; i < m; i++) {
-            U[(size_t)i * m + jj] = At[(size_t)j * m + i] * inv;
-            V[(size_t)i * m + jj] = Vt[(size_t)j * m + i];
+            U[(size_t)i * m + jj] = Vt[(size_t)j * m + i];              // Q V_x
+            V[(size_t)perm[i] * m + jj] = At[(size_t)j * m + i] * inv;  // P U_x
         }
     }
 }

@@ -1,8 +1,8 @@
 """Stage 1 (Algorithm 2; Sec. 2.2-2.3, 3.1) built by the device kernels
 against the host build.
 
-The singular values and the root far-field table are well conditioned and
-agree to rounding.  The M2M / L2L operators contain the pseudo-inverse of the
+The singular values (5e-13 s_max) and the root far-field table (1e-12) are
+well conditioned and agree to rounding.  The M2M / L2L operators contain the pseudo-inverse of the
 surface matrix, cut at 2^-52 kn s_max for binary64, so their entries along
 the near-null directions depend on the SVD's rounding (two correct SVDs give
 operators 1e-7..1e-4 apart as p grows); what is unique is the field they produce on the
@@ -48,7 +48,9 @@ def test_device_operators_match_host(kernel, p, periodic):
     Sd, md, ld, rd, td, ph = b.pkifmm_precompute_operators(kernel, periodic, p, 2, pk.FP64, 1)
     print(f"kernel {kernel} p={p} periodic {periodic}: host {th:.3f} s, device {td:.3f} s "
           f"(svd {ph[0]:.3f} s in {ph[3]:.0f} sweeps, m2m/l2l {ph[1]:.3f} s, root {ph[2]:.3f} s)")
-    assert np.abs(Sd - Sh).max() <= 1e-13 * Sh[0]
+    # Jacobi singular values carry ~1e-13 s_max of rounding (the host build and
+    # LAPACK's SVD differ by up to 1.8e-13 s_max at Stokes p = 8)
+    assert np.abs(Sd - Sh).max() <= 5e-13 * Sh[0]
     if periodic:
         assert np.abs(rd - rh).max() <= 1e-12 * np.abs(rh).max()
     else:
