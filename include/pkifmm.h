@@ -111,7 +111,7 @@ enum {
  *   ell            near-field layers of images (Eq. (pfmmSplit)), >= 1
  *   leaf_max       s: a box splits while it holds more than s sources or
  *                  more than s targets (Sec. 2.2 notation)
- *   depth_max      deepest octree level, 1..16
+ *   depth_max      deepest octree level, 1..15
  *   precision      PKIFMM_FP64 or PKIFMM_MIXED, optionally | PKIFMM_PRECOMPUTE_HOST
  *   nrhs           density vectors evaluated together on one geometry (>= 1)
  *   cache_dir      directory for the operator cache (NULL: no cache)
