@@ -217,3 +217,25 @@ def test_finite_array_root_operator(kernel):
     M = b.pkifmm_root_operator_finite(kernel, axis, N, p)
     assert np.abs(M - ref).max() <= 1e-13 * np.abs(ref).max()
     assert not np.any(b.pkifmm_root_operator_finite(kernel, axis, 1, p))  # only adjacent copies: no far field
+
+
+def test_argument_checks_without_a_gpu():
+    # the checks that run before any CUDA call: new kernels, finite arrays,
+    # periodicity masks
+    from paper_1705_02043_gb300 import _binding as b
+    lo = (0.0, 0.0, 0.0)
+    for args in [(4, 7), (-1, 7)]:  # kernels 0..3 only
+        with pytest.raises(pk.PKIFMMError) as e:
+            b.pkifmm_plan_create(args[0], args[1], lo, 1.0, 6, 2, 40, 10, 0, 1)
+        assert e.value.name == "INVALID_ARG"
+    with pytest.raises(pk.PKIFMMError) as e:
+        b.pkifmm_plan_create(0, 8, lo, 1.0, 6, 2, 40, 10, 0, 1)  # no such mask
+    assert e.value.name == "INVALID_ARG"
+    for axis, nimg in [(3, 2), (-1, 2), (0, 0), (1, -4)]:
+        with pytest.raises(pk.PKIFMMError) as e:
+            b.pkifmm_plan_create_finite(1, axis, nimg, lo, 1.0, 6, 2, 40, 10, 0, 1)
+        assert e.value.name == "INVALID_ARG"
+    with pytest.raises(pk.PKIFMMError):
+        b.pkifmm_root_operator_finite(0, 3, 2, 4)
+    with pytest.raises(ValueError):
+        pk.PeriodicKIFMM(pk.STOKES, 3, images=2)  # a finite array runs along one axis
