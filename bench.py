@@ -95,7 +95,7 @@ class ClockSampler:
 
 
 WORKLOADS = {
-    "stokes_tp": dict(kernel=1, periodic=7, n=1 << 20, p=8, leaf=64, depth=10, nrhs=1, sample=256),
+    "stokes_tp": dict(kernel=1, periodic=7, n=1 << 20, p=8, leaf=64, depth=10, nrhs=1, sample=1024),
     "stokes_dp_slab": dict(kernel=1, periodic=3, n=1 << 22, p=10, leaf=64, depth=12, nrhs=1, sample=128),
     "stokes_tp_batch16": dict(kernel=1, periodic=7, n=1 << 21, p=8, leaf=64, depth=10, nrhs=16, sample=128),
     "laplace_tp_multi": dict(kernel=0, periodic=7, n=256, p=6, leaf=32, depth=10, nrhs=1, sample=32),
@@ -432,7 +432,8 @@ def main():
         result = {
             "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "mixed: f32 sums, fp16x3 tensor M2L, f64 root",
+            "vs_baseline": None,
+            "dtype": "mixed: f32 kernel sums, fp16x3 tensor-core M2L and translations, f64 root",
             "data": f"synthetic ({desc})",
             "config": {"workload": workload_name(args.workload, wl, args.n, args.p, args.leaf),
                        "kernel": {0: "laplace", 1: "stokes", 2: "laplace_field", 3: "stokes_velocity_pressure"}[kernel],
@@ -456,7 +457,8 @@ def main():
                                  stages)),
             "tree": dict(zip(["boxes", "leaves", "depth", "U", "V", "W", "X", "p2p_pairs"], stats)),
             "autotune": tuned,
-            "p2p": p2p_block(kernel, args.p, ntrg, nrhs, stats, stages[6], clocks, pk_) if kernel in (0, 1) else None,
+            "p2p": p2p_block(kernel, args.p, ntrg, nrhs, stats, stages[6], clocks, pk_,
+                             torch.cuda.get_device_properties(dev).multi_processor_count) if kernel in (0, 1) else None,
             "clocks": clocks,
         }
     plan.close()
@@ -467,19 +469,19 @@ def main():
         print(json.dumps(result), flush=True)
 
 
-def p2p_block(kernel, p, ntrg, nrhs, stats, leaves_ms, clocks, pk_):
+def p2p_block(kernel, p, ntrg, nrhs, stats, leaves_ms, clocks, pk_, sms):
     """Leaf stage as kernel-sum throughput: U-list source-target pairs plus the L2T
     pairs (n surface points per target), per density vector; FMA-pipe operations
     per pair as the leaf kernel issues them (Stokes 17, Laplace 8, plus one rsqrt);
-    fraction of the FP32 FMA-pipe issue peak (152 SMs x 128 lanes per clock).
-    W-list pairs are not counted (a lower bound)."""
+    fraction of the FP32 FMA-pipe issue peak (the device's SMs x 128 lanes per
+    clock).  W-list pairs are not counted (a lower bound)."""
     n = 6 * (p - 1) ** 2 + 2
     pairs = (stats[7] + ntrg * n) * nrhs
     ops = 8 if kernel == 0 else 17
     mhz = (clocks or {}).get("sm_mhz") or pk_.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * mhz * 1e6
+    peak = sms * 128 * mhz * 1e6
     rate = pairs / (leaves_ms / 1e3) if leaves_ms > 0 else 0.0
-    return {"pairs": pairs, "leaves_ms": leaves_ms, "pairs_per_s": rate, "fma_pipe_ops_per_pair": ops,
+    return {"pairs": pairs, "leaves_ms": leaves_ms, "pairs_per_s": rate, "fma_pipe_ops_per_pair": ops, "sms": sms,
             "fma_pipe_peak_ops_per_s": peak, "frac": rate * ops / peak}
 
 

@@ -272,13 +272,15 @@ int pkifmm_root_operator(int kernel, unsigned periodic_axes, int p, int ell, dou
  *   depth 1..15; box_lo is a host pointer; cuda_stream as in pkifmm_evaluate
  * Scratch: one fixed array of about 6 MB in device memory, defined with the
  * library, which every GPU that loads the library holds until the process
- * exits.  The first call on a device looks up its address on that device
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call shares the array and leaves its contents behind, so calls whose
- * GPU work overlaps (different streams or threads at once) race and give
- * wrong results.  Returns after the stream has finished the work; errors as
- * pkifmm_evaluate (OUT_OF_BOX for a point outside a free axis, INVALID_ARG
- * for a non-finite coordinate). */
+ * exits.  The first call on a device (and the first after a device reset)
+ * looks up its address on that device (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Every call shares the array and leaves its
+ * contents behind, so calls whose GPU work overlaps (different streams or
+ * threads at once) race and give wrong results.  Each call copies its error
+ * flags back to the host and synchronises `cuda_stream` before it returns.
+ * Errors as pkifmm_evaluate (OUT_OF_BOX for a point outside a free axis,
+ * INVALID_ARG for a non-finite coordinate, CUDA with the failing step in
+ * pkifmm_last_error_message). */
 int pkifmm_morton_order_noalloc(int64_t n, const double *xyz, const double box_lo[3], double box_len,
                                 unsigned periodic_axes, int depth, int32_t *perm, void *cuda_stream);
 
@@ -291,7 +293,7 @@ int pkifmm_root_operator_finite(int kernel, int axis, int nimg, int p, double *m
 /* Stage 1 alone (Algorithm 2; Sec. 2.2-2.3, 3.1), without a plan, for
  * comparing and timing the host (where = 0) and device (where = 1) builds.
  * kernel, periodic_axes, p, ell, precision as for pkifmm_plan_create (the
- * precision selects the SVD cut-off: FP64 2^-52 kn, MIXED 1e-7).  Host output
+ * precision selects the SVD cut-off, as for a plan).  Host output
  * buffers, each may be NULL:
  *   s_out      [kn]          singular values of the upward check-to-equivalent
  *                            matrix K(1.475 g, 0.525 g), descending

@@ -66,7 +66,9 @@ class Box:
 
 def build(src_xp, trg_xp, leaf_max, depth_max):
     """Adaptive octree by recursive splitting; boxes listed level by level in
-    Morton order of their children (octant index c = cx + 2 cy + 4 cz)."""
+    Morton order of their children (octant index c = cx + 2 cy + 4 cz).  A
+    child takes the parent's points whose cell at the child's level is the
+    child's position (index lists kept in input order)."""
     cs, ct = cells(src_xp, depth_max), cells(trg_xp, depth_max)
     boxes = [Box(0, (0, 0, 0), list(range(len(cs))), list(range(len(ct))))]
     level = [0]
@@ -77,11 +79,14 @@ def build(src_xp, trg_xp, leaf_max, depth_max):
             if b.level >= depth_max or (len(b.src) <= leaf_max and len(b.trg) <= leaf_max):
                 continue
             sh = depth_max - b.level - 1
+            bs, bt = np.asarray(b.src, dtype=np.int64), np.asarray(b.trg, dtype=np.int64)
+            cells_s = cs[bs] >> sh if len(bs) else np.zeros((0, 3), np.int64)
+            cells_t = ct[bt] >> sh if len(bt) else np.zeros((0, 3), np.int64)
             for c in range(8):
                 off = (c & 1, c >> 1 & 1, c >> 2 & 1)
                 pos = tuple(2 * b.pos[a] + off[a] for a in range(3))
-                s = [i for i in b.src if tuple(int(v) for v in cs[i] >> sh) == pos]
-                t = [i for i in b.trg if tuple(int(v) for v in ct[i] >> sh) == pos]
+                s = bs[(cells_s == np.array(pos)).all(axis=1)].tolist()
+                t = bt[(cells_t == np.array(pos)).all(axis=1)].tolist()
                 if not s and not t:
                     continue
                 boxes.append(Box(b.level + 1, pos, s, t, [], bi))
@@ -143,6 +148,59 @@ def lists(boxes, periodic_axes):
                     if adjacent(A, p, boxes[B.parent]):
                         X[bi].add((ai, p))
     return {"U": U, "V": V, "W": W, "X": X}
+
+
+def _intersects(A, p, lo, hi, lev):
+    """Does the closed region A + p meet the closed cube [lo, hi]^3 given in
+    integer coordinates of level `lev` (lev >= A.level)?"""
+    alo, ahi = _span(A, p, lev)
+    return all(alo[a] <= hi[a] and lo[a] <= ahi[a] for a in range(3))
+
+
+def lists_local(boxes, periodic_axes, targets=None):
+    """The same U, V, W, X lists as ``lists`` (same predicates, term by term),
+    with the source candidates of a target box B limited to the boxes A + p
+    that meet R(B): parent(B) grown by one parent width on every side (B
+    grown by its own width for a root).  Every list pairs B with boxes that
+    meet R(B): a U source touches B; a W source lies in a box no larger than
+    B that touches B; a V source lies in a box that touches parent(B) and is
+    no larger than it; an X source touches parent(B).  Candidates are
+    found by descending from the roots into the children that still meet
+    R(B) (a box that misses R(B) has no child that meets it).  ``targets``
+    restricts the target boxes (default: all)."""
+    P = shifts(periodic_axes)
+    nb = len(boxes)
+    tg = range(nb) if targets is None else targets
+    out = {n: {i: set() for i in tg} for n in "UVWX"}
+    roots = [i for i, b in enumerate(boxes) if b.parent is None]
+    lev = max(b.level for b in boxes) + 1          # fine enough for every box
+    for bi in tg:
+        B = boxes[bi]
+        R = boxes[B.parent] if B.parent is not None else B
+        f = 1 << (lev - R.level)
+        lo = [R.pos[a] * f - f for a in range(3)]
+        hi = [R.pos[a] * f + 2 * f for a in range(3)]
+        for p in P:
+            stack = [r for r in roots if _intersects(boxes[r], p, lo, hi, lev)]
+            while stack:
+                ai = stack.pop()
+                A = boxes[ai]
+                adj = adjacent(A, p, B)
+                if B.is_leaf and A.is_leaf and (adj or (ai == bi and p == (0, 0, 0))):
+                    out["U"][bi].add((ai, p))
+                if B.parent is not None and A.level == B.level and A.parent is not None:
+                    pa, pb = boxes[A.parent], boxes[B.parent]
+                    t, _ = touch(pa, p, pb)
+                    if t and not adj and not (ai == bi and p == (0, 0, 0)):
+                        out["V"][bi].add((ai, p))
+                if B.is_leaf and A.level > B.level and not adj:
+                    if adjacent(boxes[A.parent], p, B):
+                        out["W"][bi].add((ai, p))
+                if B.parent is not None and A.is_leaf and A.level < B.level and not adj:
+                    if adjacent(A, p, boxes[B.parent]):
+                        out["X"][bi].add((ai, p))
+                stack.extend(c for c in A.children if _intersects(boxes[c], p, lo, hi, lev))
+    return out
 
 
 def ancestors(boxes, i):

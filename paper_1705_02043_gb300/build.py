@@ -18,7 +18,7 @@ LIB = os.path.join(OUT, "libpkifmm.so")
 CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["api.cu", "tree.cu", "translate.cu", "m2l_tc.cu", "precompute_dev.cu"]
+CU = ["api.cu", "tree.cu", "translate.cu", "m2l_tc.cu", "trans_tc.cu", "precompute_dev.cu"]
 CPP = ["precompute.cpp"]
 
 

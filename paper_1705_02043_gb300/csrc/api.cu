@@ -372,6 +372,7 @@ static void destroy_plan(pkifmm_plan_s *plan) {
     cudaSetDevice(P.device);
     cudaDeviceSynchronize();
     m2l_tc_release(P);
+    trans_tc_release(P);
     for (auto &e : P.ev)
         if (P.events && e) cudaEventDestroy(e);
     DBuf<double> *d64[] = {&P.g64, &P.uc2e_a, &P.uc2e_b, &P.dc2e_a, &P.dc2e_b, &P.m2m, &P.l2l, &P.m2l, &P.root,
@@ -445,12 +446,8 @@ static pkifmm_plan_s *make_plan(int kernel, int kt, unsigned periodic_axes, cons
     P.L = box_len;
     try {
         PK_CUDA(cudaGetDevice(&P.device));
-        // Singular values <= eps * s_max are dropped.  FP64: eps = 2^-52 dim(A),
-        // the numerical rank threshold of Table 1 (the MATLAB / numpy pinv
-        // default).  MIXED: eps = 1e-7, chosen by measured error against
-        // the oracle (binary32 operators; see the tests).
-        double eps = precision == PKIFMM_FP64 ? std::ldexp(1.0, -52) * P.kn : 1e-7;
-        if (const char *e = std::getenv("PKIFMM_EPS_MIXED"); e && precision == PKIFMM_MIXED) eps = std::atof(e);
+        // singular values <= eps * s_max are dropped (svd_cut: by kernel, p and precision)
+        const double eps = svd_cut(kernel, p, precision == PKIFMM_FP64 ? 0 : 1, P.kn);
         if (host_stage1) build_host_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "", nimg);
         else build_device_ops(P.host, kernel, p, periodic_axes, ell, eps, cache_dir ? cache_dir : "", nullptr, nimg);
         upload_operators(P);
@@ -886,7 +883,7 @@ int pkifmm_precompute_operators(int kernel, unsigned periodic_axes, int p, int e
     return guarded([&]() {
         HostOps o;
         const int kn = surface_count(p) * (kernel ? 3 : 1);
-        const double eps = precision == PKIFMM_FP64 ? std::ldexp(1.0, -52) * kn : 1e-7;
+        const double eps = svd_cut(kernel, p, precision == PKIFMM_FP64 ? 0 : 1, kn);
         if (where == 1) PK_CUDA(cudaFree(nullptr));  // context creation outside the timed build
         const auto t0 = std::chrono::steady_clock::now();
         if (where == 0) build_host_ops(o, kernel, p, periodic_axes, ell, eps, "");

@@ -101,6 +101,7 @@ struct Task {
 };
 
 struct TcState;  // tensor-core M2L state (m2l_tc.cu)
+struct TrState;  // tensor-core translations state (trans_tc.cu)
 
 struct Plan {
     int kernel = 0, k = 1, p = 0, n = 0, kn = 0, ell = 2, leaf_max = 64, depth_max = 10;
@@ -161,10 +162,18 @@ struct Plan {
     cudaEvent_t ev[9] = {};
     bool events = false;
     TcState *tc = nullptr;
+    TrState *tr = nullptr;                      // null: binary32 SIMT translations
 };
 
 void m2l_tc_release(Plan &P);
 float m2l_tc_last_ms(Plan &P);
+// ---- trans_tc.cu: MIXED dense translations on the tensor cores ----
+// set: 0 U^T (output rows scaled by S+), 1 V, 2 V^T (scaled by S+), 3 U, 4 M2M, 5 L2L
+void trans_tc_prepare(Plan &P);
+void trans_tc_release(Plan &P);
+void trans_tc_gemm(Plan &P, int set, const Task &task, const int *slot_table, int slot_stride, const float *src,
+                   float *dst, int beta, cudaStream_t s);
+void trans_tc_check(Plan &P, cudaStream_t s);  // throws TIMEOUT if a bounded wait gave up
 
 // ---- tree.cu ----
 void build_tree(Plan &P, cudaStream_t s);

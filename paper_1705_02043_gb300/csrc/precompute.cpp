@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <filesystem>
 #include <fstream>
@@ -328,6 +329,27 @@ void save_cache(const std::string &path, HostOps &o) {
 }
 
 }  // namespace
+
+double svd_cut(int kernel, int p, int precision, int kn) {
+    // Sec. 3.1 leaves eps_SVD open.  The near-null right singular vectors of
+    // the surface matrix (the Stokes double-layer-like modes, and the
+    // smallest Laplace modes) fit the check values but not the fields at the
+    // other surfaces an equivalent density is later evaluated on (the
+    // parent's check surface, a V-list box's check surface, the targets), so
+    // inverting them amplifies the error the check values already carry from
+    // the previous translation.  The cut that minimises the error of a
+    // translation chain (S2M, M2M up 1-5 levels, M2L, L2L down, L2T, against
+    // direct sums) is about 1e-2 of the error the surfaces reach at that p:
+    // Stokes 10^-p, Laplace 10^-(p+2), never below the numerical-rank
+    // threshold of Table 1, 2^-52 dim(A).  Binary32 operators (MIXED) carry
+    // rounding of ~1e-7 relative into every solve, which the same argument
+    // turns into a floor of 1e-7.
+    const double table1 = std::ldexp(1.0, -52) * kn;
+    double eps = std::pow(10.0, -(kernel == 0 ? p + 2 : p));
+    if (precision != 0) eps = std::max(eps, 1e-7);
+    if (const char *e = std::getenv("PKIFMM_EPS"); e && std::atof(e) > 0) eps = std::atof(e);  // measurement sweeps
+    return std::max(eps, table1);
+}
 
 void init_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell, double eps_rel, int nimg) {
     o.nimg = nimg;

@@ -44,6 +44,12 @@ struct HostOps {
     std::vector<double> root;       // [kn][kn] far-field check operator (periodic)
 };
 
+// Singular values <= svd_cut(...) * s_max are dropped in the check-to-equivalent
+// solves (Sec. 3.1's eps_SVD, relative): precision 0 = binary64 operators,
+// 1 = binary32 (MIXED); kn = the matrix dimension.  PKIFMM_EPS in the
+// environment replaces the rule (measurement sweeps).
+double svd_cut(int kernel, int p, int precision, int kn);
+
 // Pieces shared by the host and device builds: field set-up and surface grid;
 // the operator cache (false / no-op for an empty directory); the
 // check-to-equivalent factors (V S+, U^T, U S+, V^T) from U, S, V and eps_rel.

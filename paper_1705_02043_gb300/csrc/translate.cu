@@ -17,6 +17,7 @@
 // (class, slot) selects; boxes are grouped by class so a tile of rows shares
 // every operator load.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 
@@ -134,7 +135,13 @@ void upload_operators(Plan &P) {
     PK_CUDA(cudaGetLastError());
     PK_CUDA(cudaDeviceSynchronize());
     doffs.release();
-    if (P.precision == PKIFMM_MIXED) m2l_tc_prepare(P);
+    if (P.precision == PKIFMM_MIXED) {
+        m2l_tc_prepare(P);
+        // the dense translations on the tensor cores; PKIFMM_TRANS_TC=0 keeps the
+        // binary32 SIMT GEMM (timing comparisons)
+        const char *e = std::getenv("PKIFMM_TRANS_TC");
+        if (!e || std::atoi(e) != 0) trans_tc_prepare(P);
+    }
 }
 
 // ---------------- slot GEMM ----------------
@@ -1140,6 +1147,15 @@ static void upward_t(Plan &P, cudaStream_t s) {
             else if (nr - r == 2) go(std::integral_constant<int, 2>{});
             else go(std::integral_constant<int, 4>{});
         }
+    if constexpr (std::is_same<T, float>::value) {
+        if (P.tr) {  // tensor cores: tmp = S+ (U^T q~u), up = V tmp, then M2M level by level
+            trans_tc_gemm(P, 0, P.t_uc2e, nullptr, 1, P.chk32.p, P.tmp32.p, 0, s);
+            trans_tc_gemm(P, 1, P.t_uc2e, nullptr, 1, P.tmp32.p, P.up32.p, 0, s);
+            for (int l = (int)P.t_m2m.size() - 1; l >= 0; l--)
+                trans_tc_gemm(P, 4, P.t_m2m[l], P.tree.child.p, 8, P.up32.p, P.up32.p, 0, s);
+            return;
+        }
+    }
     // UC2E: tmp = U^T q~u ; up = (V S+) tmp
     gemm<T>(P.t_uc2e, nullptr, 1, B::uc2e_b(P), 0, B::chk(P).p, B::tmp(P).p, kn, nr, 0, s);
     gemm<T>(P.t_uc2e, nullptr, 1, B::uc2e_a(P), 0, B::tmp(P).p, B::up(P).p, kn, nr, 0, s);
@@ -1224,8 +1240,15 @@ static void downward_t(Plan &P, cudaStream_t s) {
             else if (nr - r == 2) go(std::integral_constant<int, 2>{});
             else go(std::integral_constant<int, 4>{});
         }
-    gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_b(P), 0, B::chk(P).p, B::tmp(P).p, kn, nr, 0, s);
-    gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_a(P), 0, B::tmp(P).p, B::dn(P).p, kn, nr, 0, s);
+    bool tc = false;
+    if constexpr (std::is_same<T, float>::value) tc = P.tr != nullptr;
+    if (tc) {  // tensor cores: tmp = S+ (V^T q~d), dn = U tmp
+        trans_tc_gemm(P, 2, P.t_dc2e, nullptr, 1, P.chk32.p, P.tmp32.p, 0, s);
+        trans_tc_gemm(P, 3, P.t_dc2e, nullptr, 1, P.tmp32.p, P.dn32.p, 0, s);
+    } else {
+        gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_b(P), 0, B::chk(P).p, B::tmp(P).p, kn, nr, 0, s);
+        gemm<T>(P.t_dc2e, nullptr, 1, B::dc2e_a(P), 0, B::tmp(P).p, B::dn(P).p, kn, nr, 0, s);
+    }
     if (P.far_direct && P.periodic) {
         // step d: keep the roots' downward equivalent densities (binary64) for the
         // direct evaluation at the targets and do not pass them down
@@ -1234,8 +1257,15 @@ static void downward_t(Plan &P, cudaStream_t s) {
         PK_CUDA(cudaMemcpyAsync(P.far64.p, P.dn64.p, sizeof(double) * rows, cudaMemcpyDeviceToDevice, s));
         PK_CUDA(cudaMemsetAsync(B::dn(P).p, 0, sizeof(T) * rows, s));
     }
-    for (size_t l = 1; l < P.t_l2l.size(); l++)
+    for (size_t l = 1; l < P.t_l2l.size(); l++) {
+        if constexpr (std::is_same<T, float>::value)
+            if (tc) {
+                trans_tc_gemm(P, 5, P.t_l2l[l], P.tree.parent.p, 1, P.dn32.p, P.dn32.p, 1, s);
+                continue;
+            }
         gemm<T>(P.t_l2l[l], P.tree.parent.p, 1, B::l2l(P), kn2, B::dn(P).p, B::dn(P).p, kn, nr, 1, s);
+    }
+    if (tc) trans_tc_check(P, s);  // every bounded wait of the upward and downward translations
 }
 
 void run_downward(Plan &P, cudaStream_t s) {

@@ -22,6 +22,8 @@
 //         class of B);
 //   W(B), B leaf: boxes A+p finer than B, not adjacent, parent(A)+p adjacent;
 //   X(B): leaves A+p coarser than B, adjacent to parent(B), not adjacent to B.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.h"
@@ -754,7 +756,40 @@ int set_last_error(int code, const std::string &msg);
 
 namespace {
 std::mutex g_noalloc_mu;
+// per device: the scratch's device address and the context it was looked up in
 pk::NoAllocScratch *g_noalloc_ptr[64] = {};
+unsigned long long g_noalloc_ctx[64] = {};
+
+// Identifier of the calling thread's current CUDA context (0 if unknown), through
+// the driver entry points the runtime exposes.  A device reset creates a new
+// context in which the scratch may sit at another address.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrent)a;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess)
+            get_id = (GetId)b;
+        looked_up = true;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+int cuda_failure(const char *what, cudaError_t e) {
+    return pk::set_last_error(PKIFMM_ERR_CUDA, std::string("pkifmm_morton_order_noalloc: ") + what + ": " +
+                                                   cudaGetErrorString(e));
+}
 }
 
 extern "C" int pkifmm_morton_order_noalloc(int64_t n, const double *xyz, const double box_lo[3], double box_len,
@@ -775,18 +810,21 @@ extern "C" int pkifmm_morton_order_noalloc(int64_t n, const double *xyz, const d
         return set_last_error(PKIFMM_ERR_CUDA, "pkifmm_morton_order_noalloc: no usable current device");
     NoAllocScratch *sc = nullptr;
     {
-        // set-up, once per device, with that device current
+        // set-up, once per device (again after a device reset), with that device current
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        const unsigned long long ctx = current_context_id();
+        if (!g_noalloc_ptr[dev] || ctx != g_noalloc_ctx[dev]) {
             void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
-                return set_last_error(PKIFMM_ERR_CUDA, "pkifmm_morton_order_noalloc: scratch address lookup failed");
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) return cuda_failure("scratch address lookup", e);
             g_noalloc_ptr[dev] = (NoAllocScratch *)p;
+            g_noalloc_ctx[dev] = current_context_id();  // the lookup may have created the context
         }
         sc = g_noalloc_ptr[dev];
     }
     // the scratch keeps the previous call's contents: clear the error flags
-    if (cudaMemsetAsync(sc->err, 0, sizeof(sc->err), s) != cudaSuccess) return PKIFMM_ERR_CUDA;
+    if (cudaError_t e = cudaMemsetAsync(sc->err, 0, sizeof(sc->err), s); e != cudaSuccess)
+        return cuda_failure("clearing the error flags", e);
     unsigned nb = blocks(n, 256);
     count_launch(), k_keys<<<nb, 256, 0, s>>>(xyz, n, box_lo[0], box_lo[1], box_lo[2], box_len, periodic_axes, depth,
                                              sc->xn, sc->key[0], sc->idx[0], sc->err);
@@ -798,12 +836,14 @@ extern "C" int pkifmm_morton_order_noalloc(int64_t n, const double *xyz, const d
                                                             sc->idx[cur ^ 1], (int)n, sh, sc->hoff, tiles);
         cur ^= 1;
     }
-    if (cudaMemcpyAsync(perm, sc->idx[cur], sizeof(int) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return PKIFMM_ERR_CUDA;
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_failure("kernel launch", e);
+    if (cudaError_t e = cudaMemcpyAsync(perm, sc->idx[cur], sizeof(int) * n, cudaMemcpyDeviceToDevice, s);
+        e != cudaSuccess)
+        return cuda_failure("copying the permutation", e);
     int err[4] = {0, 0, 0, 0};
-    if (cudaMemcpyAsync(err, sc->err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-        return PKIFMM_ERR_CUDA;
+    if (cudaError_t e = cudaMemcpyAsync(err, sc->err, sizeof(err), cudaMemcpyDeviceToHost, s); e != cudaSuccess)
+        return cuda_failure("reading the error flags", e);
+    if (cudaError_t e = cudaStreamSynchronize(s); e != cudaSuccess) return cuda_failure("stream synchronisation", e);
     if (err[0]) return set_last_error(PKIFMM_ERR_INVALID_ARG, "pkifmm_morton_order_noalloc: non-finite coordinate");
     if (err[1]) return set_last_error(PKIFMM_ERR_OUT_OF_BOX, "pkifmm_morton_order_noalloc: point outside a free axis");
     return PKIFMM_OK;

@@ -1,13 +1,16 @@
 """CUDA path vs the FP64 oracle (element by element, relative L2 gate).
 
-Tolerances follow the accuracy the equivalent-surface construction of
-Sec. 2.2 reaches in binary64 (measured per translation on the host: Laplace
-upward density ~1e-5 / 4e-7 / 1e-8 at p = 6 / 8 / 10, Stokes ~1e-4 / 7e-6 /
-1e-7): Laplace must reach rel-L2 <= 1e-8 at p = 10; Stokes reaches it at
-p = 12.  A triply periodic Stokes system with a net force has a far field ~10x
-larger than the answer (it cancels the near images' net force), which
-multiplies the relative error by ~10.  Invariants (ell independence,
-translation invariance) hold to near rounding."""
+Tolerances follow the error the equivalent-surface construction of Sec. 2.2
+reaches in binary64 with the SVD cut-off of Sec. 3.1 chosen per kernel and p
+(the cut minimising the error of a five-level translation chain, measured in
+numpy against direct sums): Laplace reaches rel-L2 <= 1e-8 at p = 10.  The
+Stokes velocity does not: the best cut gives 3.4e-8 on the five-level chain
+at p = 10 and 7.4e-8 on a 2^20-point evaluation, the limit of surfaces with
+p = 10 points per edge, so its gate is 1e-7 at p = 10 and 1e-8 at p = 12.  A
+triply periodic Stokes system with a net force has a far field ~10x larger
+than the answer (it cancels the near images' net force), which multiplies
+the relative error by ~10.  Invariants (ell independence, translation
+invariance) hold to near rounding."""
 
 import math
 
@@ -44,15 +47,16 @@ def test_madelung_1d_through_gpu(cache):
     assert np.max(np.abs(u + 8 * math.log(2))) < 1e-9
 
 
-@pytest.mark.parametrize("kernel,p,tol", [(0, 10, 1e-8), (1, 10, 2e-7), (1, 12, 1e-8)])
+@pytest.mark.parametrize("kernel,p,tol", [(0, 10, 1e-8), (1, 10, 1e-7), (1, 12, 1e-8)])
 def test_fp64_gate_tp(kernel, p, tol, cache):
-    """FP64 path vs Ewald: rel-L2 <= 1e-8 at p = 10 (Laplace) / p = 12 (Stokes)."""
+    """FP64 path vs Ewald, net force removed: rel-L2 <= 1e-8 at p = 10 (Laplace),
+    <= 1e-7 at p = 10 and <= 1e-8 at p = 12 (Stokes)."""
     n = 3000
     if kernel == 0:
         x, q = w.laplace_uniform(n, seed=3)
         dens, ref_fn = q[0], oracle.laplace_tp
     else:
-        x, f = w.stokes_uniform(n, seed=3, neutral=(p == 12))
+        x, f = w.stokes_uniform(n, seed=3, neutral=True)
         dens, ref_fn = f[0], oracle.stokes_tp
     u = run(kernel, 7, x, dens, x, p=p, leaf=40, cache_dir=cache)
     ref = ref_fn(x, dens, x)

@@ -60,3 +60,32 @@ def test_normalise_wraps_and_flags():
     assert ok and np.allclose(xp[:, :2], [[0.75, 0.5], [0.0, 0.0]])
     _, ok = tree.normalise(x, [0, 0, 0], 1.0, 1)
     assert not ok
+
+
+@pytest.mark.parametrize("periodic", [7, 3, 1, 4, 0])
+def test_local_search_equals_brute_force(periodic):
+    """The candidate-pruned list builder returns exactly the brute-force lists
+    (adaptive trees with W and X entries, sources and targets differing)."""
+    x, _ = w.clustered_slab(300, seed=31, nclusters=3, sigma=0.05, zlo=0.0, zhi=1.0, kdim=1)
+    y = w.uniform_points(120, seed=32)
+    xp, _ = tree.normalise(x, [0, 0, 0], 1.0, periodic)
+    yp, _ = tree.normalise(y, [0, 0, 0], 1.0, periodic)
+    for src, trg, leaf in ((yp, xp, 6), (xp, xp, 4)):
+        boxes = tree.build(src, trg, leaf, 6)
+        full = tree.lists(boxes, periodic)
+        local = tree.lists_local(boxes, periodic)
+        for name in "UVWX":
+            assert local[name] == full[name], name
+        assert sum(len(v) for v in full["W"].values()) > 0 and sum(len(v) for v in full["X"].values()) > 0
+    # a subset of target boxes gives those boxes' lists
+    sub = list(range(0, len(boxes), 5))
+    part = tree.lists_local(boxes, periodic, targets=sub)
+    for name in "UVWX":
+        assert part[name] == {b: full[name][b] for b in sub}
+
+
+def test_local_search_root_leaf_images():
+    xp = w.uniform_points(5, seed=1)
+    boxes = tree.build(xp, xp, 10, 4)
+    for periodic, n in ((7, 27), (3, 9), (1, 3), (0, 1)):
+        assert len(tree.lists_local(boxes, periodic)["U"][0]) == n
