@@ -380,7 +380,8 @@ static void destroy_plan(pkifmm_plan_s *plan) {
                            &P.dn64, &P.tmp64};
     for (auto *b : d64) b->release();
     DBuf<float> *d32[] = {&P.g32, &P.uc2e_a32, &P.uc2e_b32, &P.dc2e_a32, &P.dc2e_b32, &P.m2m32, &P.l2l32, &P.m2l32,
-                          &P.ysrel32, &P.xtrel32, &P.dens32, &P.pot32, &P.up32, &P.chk32, &P.dn32, &P.tmp32};
+                          &P.ysrel32, &P.xtrel32, &P.dens32, &P.pot32, &P.up32, &P.chk32, &P.dn32, &P.tmp32,
+                          &P.uphat32, &P.chkhat32};
     for (auto *b : d32) b->release();
     DBuf<int> *di[] = {&P.class_slot_op, &P.idxS, &P.idxT, &P.idxS2, &P.idxT2, &P.hist, &P.err, &P.cnt, &P.off,
                        &P.gather_idx, &P.leaves_src, &P.leaves_trg, &P.xboxes, &P.tree.parent, &P.tree.child,
@@ -407,7 +408,7 @@ static void destroy_plan(pkifmm_plan_s *plan) {
     if (P.stage_h) cudaFreeHost(P.stage_h);
     if (P.down_h) cudaFreeHost(P.down_h);
     if (P.stage_ev) cudaEventDestroy(P.stage_ev);
-    Task *ts[] = {&P.t_uc2e, &P.t_m2l, &P.t_dc2e, &P.t_root};
+    Task *ts[] = {&P.t_uc2e, &P.t_m2l, &P.t_dc2e, &P.t_root, &P.t_dcx};
     for (auto *t : ts) {
         t->boxes.release();
         t->tiles.release();

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -149,12 +150,16 @@ struct Plan {
     // equivalent densities [nbox][nrhs][kn]
     DBuf<double> up64, chk64, dn64, tmp64;
     DBuf<float> up32, chk32, dn32, tmp32;
+    // MIXED with a shared M2L basis Ub (r columns): Ub^T phi_u and the M2L output in that basis, [nbox][nrhs][r]
+    std::shared_ptr<const M2LBasis> basis;
+    DBuf<float> uphat32, chkhat32;
     // tree build scratch
     DBuf<int> cnt, off;
     DBuf<int2> csr, ctr;                        // [nlevel boxes][8] child ranges
     DBuf<int> gather_idx;
     Tree tree;
     Task t_uc2e, t_m2l, t_dc2e, t_root;
+    Task t_dcx;                                 // boxes with targets and an X list (MIXED with a shared M2L basis)
     std::vector<Task> t_m2m, t_l2l;             // per level
     DBuf<int> leaves_src, leaves_trg, xboxes;   // task lists for kernel sums
     int n_leaves_src = 0, n_leaves_trg = 0, n_xboxes = 0;
@@ -171,8 +176,10 @@ float m2l_tc_last_ms(Plan &P);
 // set: 0 U^T (output rows scaled by S+), 1 V, 2 V^T (scaled by S+), 3 U, 4 M2M, 5 L2L
 void trans_tc_prepare(Plan &P);
 void trans_tc_release(Plan &P);
+// sets 6, 7 (with a shared M2L basis): [V; Ub^T V], [M2M; Ub^T M2M] write phi to dst
+// and Ub^T phi to dst2; set 8: V^T Ub (rows scaled by S+) from the M2L output in that basis
 void trans_tc_gemm(Plan &P, int set, const Task &task, const int *slot_table, int slot_stride, const float *src,
-                   float *dst, int beta, cudaStream_t s);
+                   float *dst, int beta, cudaStream_t s, float *dst2 = nullptr);
 void trans_tc_check(Plan &P, cudaStream_t s);  // throws TIMEOUT if a bounded wait gave up
 
 // ---- tree.cu ----

@@ -28,6 +28,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 
@@ -612,6 +613,19 @@ __global__ void k_kop_split(int kernel, int n, int KM, int KK, int kexp, const d
     out[total + i] = lo;
 }
 
+// C_o (r x r, binary32) * 2^kexp split into fp16 hi/lo, padded to KM x KK: out[h][op][i][j]
+__global__ void k_cop_split(const float *__restrict__ C, int r, int KM, int KK, int kexp, __half *__restrict__ out) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = (long long)kM2LOps * KM * KK;
+    if (i >= total) return;
+    int m = (int)(i / ((long long)KM * KK));
+    int rem = (int)(i % ((long long)KM * KK)), a = rem / KK, c = rem % KK;
+    const float v = (a < r && c < r) ? ldexpf(C[((long long)m * r + a) * r + c], kexp) : 0.f;
+    __half hi = __float2half_rn(v);
+    out[i] = hi;
+    out[total + i] = __float2half_rn(v - __half2float(hi));
+}
+
 __global__ void k_amax(const float *__restrict__ x, long long n, float *amax) {
     float m = 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -736,31 +750,49 @@ void m2l_tc_prepare(Plan &P) {
     if (!tc_supported()) throw Error(PKIFMM_ERR_UNSUPPORTED, "MIXED path needs an sm_103 GPU (tcgen05)");
     TcState *t = new TcState;
     P.tc = t;
-    t->KM = (P.kn + TC_M - 1) / TC_M * TC_M;
-    t->KK = (P.kn + TC_K - 1) / TC_K * TC_K;
-    // |K_o| <= 1/0.95 (Laplace) or 2/(8 pi 0.95) (Stokes) over the 316 offsets
-    // (closest points 0.95 box edges apart): scale the largest entry to about 2^12
-    t->kexp = P.kernel == 0 ? 12 : 15;
+    // dense operators (kn x kn) or their images C_o = Ub^T K_o Ub in the shared basis (r x r)
+    const int rk = P.basis ? P.basis->r : P.kn;
+    t->KM = (rk + TC_M - 1) / TC_M * TC_M;
+    t->KK = (rk + TC_K - 1) / TC_K * TC_K;
     const int KM = t->KM, KK = t->KK;
     size_t nk = (size_t)kM2LOps * KM * KK;
     PK_CUDA(cudaMalloc(&t->kop, 2 * nk * sizeof(__half)));
-    std::vector<int> offs;
-    for (int x = -3; x <= 3; x++)
-        for (int y = -3; y <= 3; y++)
-            for (int z = -3; z <= 3; z++) {
-                if (std::max(std::abs(x), std::max(std::abs(y), std::abs(z))) <= 1) continue;
-                offs.push_back(x);
-                offs.push_back(y);
-                offs.push_back(z);
-            }
-    int *doffs = nullptr;
-    PK_CUDA(cudaMalloc(&doffs, sizeof(int) * offs.size()));
-    PK_CUDA(cudaMemcpy(doffs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice));
-    count_launch(), k_kop_split<<<(unsigned)((nk + 255) / 256), 256>>>(P.kernel, P.n, KM, KK, t->kexp, P.g64.p, doffs,
-                                                                        t->kop);
-    PK_CUDA(cudaGetLastError());
-    PK_CUDA(cudaDeviceSynchronize());
-    cudaFree(doffs);
+    if (P.basis) {
+        const std::vector<float> &C = P.basis->C;
+        float mx = 0.f;
+        for (float v : C) mx = std::max(mx, std::fabs(v));
+        int e = 0;
+        if (mx > 0.f) std::frexp(mx, &e);
+        t->kexp = 14 - e;  // largest entry just below 2^14
+        float *dc = nullptr;
+        PK_CUDA(cudaMalloc(&dc, sizeof(float) * C.size()));
+        PK_CUDA(cudaMemcpy(dc, C.data(), sizeof(float) * C.size(), cudaMemcpyHostToDevice));
+        count_launch(), k_cop_split<<<(unsigned)((nk + 255) / 256), 256>>>(dc, rk, KM, KK, t->kexp, t->kop);
+        PK_CUDA(cudaGetLastError());
+        PK_CUDA(cudaDeviceSynchronize());
+        cudaFree(dc);
+    } else {
+        // |K_o| <= 1/0.95 (Laplace) or 2/(8 pi 0.95) (Stokes) over the 316 offsets
+        // (closest points 0.95 box edges apart): scale the largest entry to about 2^12
+        t->kexp = P.kernel == 0 ? 12 : 15;
+        std::vector<int> offs;
+        for (int x = -3; x <= 3; x++)
+            for (int y = -3; y <= 3; y++)
+                for (int z = -3; z <= 3; z++) {
+                    if (std::max(std::abs(x), std::max(std::abs(y), std::abs(z))) <= 1) continue;
+                    offs.push_back(x);
+                    offs.push_back(y);
+                    offs.push_back(z);
+                }
+        int *doffs = nullptr;
+        PK_CUDA(cudaMalloc(&doffs, sizeof(int) * offs.size()));
+        PK_CUDA(cudaMemcpy(doffs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice));
+        count_launch(), k_kop_split<<<(unsigned)((nk + 255) / 256), 256>>>(P.kernel, P.n, KM, KK, t->kexp, P.g64.p,
+                                                                            doffs, t->kop);
+        PK_CUDA(cudaGetLastError());
+        PK_CUDA(cudaDeviceSynchronize());
+        cudaFree(doffs);
+    }
     EncodeTiledFn enc = encode_fn();
     for (int h = 0; h < 2; h++) {
         cuuint64_t dims[2] = {(cuuint64_t)KK, (cuuint64_t)kM2LOps * KM};
@@ -836,6 +868,10 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
     const Task &task = P.t_m2l;
     if (task.nrows == 0) return true;
     const int KK = t->KK, nr = P.nrhs, mtiles = t->KM / TC_M;
+    // sources and results: phi_u and the check rows, or both in the shared basis
+    const int rk = P.basis ? P.basis->r : P.kn;
+    const float *up = P.basis ? P.uphat32.p : P.up32.p;
+    float *chk = P.basis ? P.chkhat32.p : P.chk32.p;
     const std::vector<int> &lb = P.tree.lvl_begin;
     const int nlev = (int)lb.size() - 1;
     long long rows = (long long)P.tree.nbox * nr;
@@ -885,7 +921,7 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
             }
     }
     PK_CUDA(cudaMemsetAsync(t->amax, 0, sizeof(float), s));
-    count_launch(), k_amax<<<1024, 256, 0, s>>>(P.up32.p, rows * P.kn, t->amax);
+    count_launch(), k_amax<<<1024, 256, 0, s>>>(up, rows * rk, t->amax);
 
     // remaining boxes: gather mode, class-major
     std::vector<int> gbox;
@@ -970,9 +1006,9 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
     a.v_slot = P.tree.v_slot.p;
     a.class_ops = P.class_slot_op.p;
     a.slot_off = t->slot_off;
-    a.chk = P.chk32.p;
+    a.chk = chk;
     a.amax = t->amax;
-    a.kn = P.kn;
+    a.kn = rk;
     a.KM = t->KM;
     a.KK = KK;
     a.nrhs = nr;
@@ -991,7 +1027,7 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         }
         long long tot = (rows + 1) * KK;
         count_launch(), k_phi_split<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-            P.up32.p, rows, P.kn, KK, t->amax, t->phi, t->phi + t->phi_rows * KK);
+            up, rows, rk, KK, t->amax, t->phi, t->phi + t->phi_rows * KK);
     }
     // parity grids for grid mode
     if (!gp.empty()) {
@@ -999,7 +1035,7 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         for (auto &g : gp) {
             __half *hi = t->grid + g.off, *lo = hi + (size_t)g.rows * KK;
             count_launch(), k_phi_grid<<<(unsigned)g.rows, 128, 0, s>>>(
-                P.up32.p, lb[g.level], g.map_off >= 0 ? t->lmap + g.map_off : nullptr, g.n, nr, P.kn, KK,
+                up, lb[g.level], g.map_off >= 0 ? t->lmap + g.map_off : nullptr, g.n, nr, rk, KK,
                 P.periodic, t->amax, g.rows, hi, lo);
         }
     }

@@ -84,4 +84,24 @@ void matmul(int m, int n, int kk, const double *A, const double *B, double *C); 
 void build_device_ops(HostOps &ops, int kernel, int p, unsigned periodic, int ell,
                       double eps_rel, const std::string &cache_dir, double *phases = nullptr, int nimg = -1);
 
+// The V-list M2L operators of the 316 offsets o in one shared basis (the
+// MIXED path): G = sum_o K_o K_o^T = U S U^T (K_o = K(0.525 g_i, o + 0.525 g_j),
+// kn x kn), Ub = the first r columns of U, C_o = Ub^T K_o Ub.  r: the smallest
+// multiple of 64 whose next relative singular value sqrt(S_r / S_0) is <= tau,
+// or rank_override if > 0 (r = kn keeps every column).  Built on the device in
+// binary64.  Throws pk::Error on failure.
+struct M2LBasis {
+    int r = 0;                  // 0: no basis (dense operators)
+    std::vector<double> Ub;     // [kn][r] orthonormal columns
+    std::vector<float> C;       // [316][r][r]
+    std::vector<double> sig;    // [kn] singular values of the stacked operators / the largest
+};
+void build_m2l_basis(int kernel, int p, double tau, int rank_override, M2LBasis &B);
+
+// C[b] = A[b] B[b] for b < batch, row-major binary64 host arrays with element
+// strides between the batch's matrices (0: one matrix for all), computed on the
+// current device.
+void matmul_device(int m, int n, int kk, const double *A, long long sA, const double *B, long long sB, double *C,
+                   long long sC, int batch);
+
 }  // namespace pk

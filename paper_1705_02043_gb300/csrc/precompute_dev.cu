@@ -402,6 +402,81 @@ void to_host(std::vector<T> &h, const T *d, size_t n, cudaStream_t s) {
     PK_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost, s));
 }
 
+// K_o for a batch of V-list offsets: out[b][i k + a][j k + c] = K_ac(0.525 g_i - (o_b + 0.525 g_j))
+__global__ void k_m2l_batch(int kernel, const double *__restrict__ g, int n, const int *__restrict__ offs,
+                            double *__restrict__ out) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)n * n) return;
+    const int b = blockIdx.y, i = (int)(t / n), j = (int)(t % n), k = kernel == 0 ? 1 : 3;
+    const int *o = offs + 3 * b;
+    double r[3];
+    for (int a = 0; a < 3; a++) r[a] = kInnerHalf * g[3 * i + a] - (o[a] + kInnerHalf * g[3 * j + a]);
+    double blk[9];
+    const double zero[3] = {0.0, 0.0, 0.0};
+    ff::kernel_block(kernel, r, zero, blk);
+    const size_t kn = (size_t)n * k;
+    double *M = out + (size_t)b * kn * kn;
+    for (int a = 0; a < k; a++)
+        for (int c = 0; c < k; c++) M[(i * k + a) * kn + j * k + c] = blk[a * k + c];
+}
+
+// G += sum_b P[b] (len elements each)
+__global__ void k_sum_batch(const double *__restrict__ P, int nb, long long len, double *__restrict__ G) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= len) return;
+    double acc = G[t];
+    for (int b = 0; b < nb; b++) acc += P[(size_t)b * len + t];
+    G[t] = acc;
+}
+
+// A = U S V^T of a square m x m row-major device matrix (unchanged): QR with
+// column pivoting, then one-sided Jacobi on R^T (see the header of this file);
+// U, S, V copied back to the host (row-major, S descending).  Returns the
+// number of Jacobi sweeps, counting the last one that rotated nothing.
+int device_svd(const double *A, int m, cudaStream_t s, std::vector<double> &Uh, std::vector<double> &Sh,
+               std::vector<double> &Vh) {
+    const int kn = m, mm = kn + (kn & 1);
+    const size_t kn2 = (size_t)kn * kn;
+    DevArr<double> W(kn2), hv(kn2), tau(kn), c2(kn), At(kn2), Vt(kn2), U(kn2), V(kn2), S(kn), sig(kn);
+    DevArr<int> rank(kn), perm(kn);
+    DevArr<unsigned long long> rot(1);
+    // W = A^T (columns of A as rows); Vt of the transpose kernel is scratch here
+    count_launch(), k_transpose_eye<<<nblocks((long long)kn2, 256), 256, 0, s>>>(A, kn, W.p, Vt.p);
+    std::vector<int> iota(kn);
+    for (int i = 0; i < kn; i++) iota[i] = i;
+    PK_CUDA(cudaMemcpyAsync(perm.p, iota.data(), sizeof(int) * kn, cudaMemcpyHostToDevice, s));
+    count_launch(), k_row_norm2<<<kn, kJT, 0, s>>>(W.p, kn, c2.p);
+    for (int k = 0; k < kn; k++) {
+        count_launch(), k_qr_pivot<<<1, kQT, 0, s>>>(W.p, kn, k, c2.p, perm.p, hv.p, tau.p);
+        if (kn - k - 1 > 0) count_launch(), k_qr_apply<<<kn - k - 1, kJT, 0, s>>>(W.p, kn, k, hv.p, tau.p, c2.p);
+    }
+    count_launch(), k_r_rows<<<nblocks((long long)kn2, 256), 256, 0, s>>>(W.p, kn, At.p, Vt.p);
+    PK_CUDA(cudaGetLastError());
+    unsigned long long hrot = 0;
+    int sweeps = 0;
+    for (int sweep = 0; sweep < 80; sweep++, sweeps++) {
+        PK_CUDA(cudaMemsetAsync(rot.p, 0, sizeof(unsigned long long), s));
+        for (int round = 0; round < mm - 1; round++)
+            count_launch(), k_jacobi_round<<<mm / 2, kJT, 0, s>>>(At.p, Vt.p, kn, mm, round, 1e-15, rot.p);
+        PK_CUDA(cudaGetLastError());
+        PK_CUDA(cudaMemcpyAsync(&hrot, rot.p, sizeof hrot, cudaMemcpyDeviceToHost, s));
+        PK_CUDA(cudaStreamSynchronize(s));
+        if (hrot == 0) break;
+    }
+    // Q V_x: reflectors applied in reverse order to the rows of Vt
+    for (int k = kn - 1; k >= 0; k--) count_launch(), k_apply_reflector<<<kn, kJT, 0, s>>>(Vt.p, kn, k, hv.p, tau.p);
+    count_launch(), k_row_norms<<<kn, kJT, 0, s>>>(At.p, kn, sig.p);
+    count_launch(), k_rank<<<nblocks(kn, 256), 256, 0, s>>>(sig.p, kn, rank.p);
+    count_launch(), k_extract_qr<<<nblocks((long long)kn2, 256), 256, 0, s>>>(At.p, Vt.p, sig.p, rank.p, perm.p, kn,
+                                                                            U.p, V.p, S.p);
+    PK_CUDA(cudaGetLastError());
+    to_host(Uh, U.p, kn2, s);
+    to_host(Vh, V.p, kn2, s);
+    to_host(Sh, S.p, (size_t)kn, s);
+    PK_CUDA(cudaStreamSynchronize(s));
+    return sweeps + (hrot == 0 ? 1 : 0);
+}
+
 }  // namespace
 
 void build_device_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell, double eps_rel,
@@ -426,7 +501,7 @@ void build_device_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell,
         if (!ff::far_kernel_block(kernel, periodic, ell, r0, probe))
             throw Error(PKIFMM_ERR_UNSUPPORTED, "root operator: periodicity not supported");
     }
-    const int n = o.n, k = o.k, kn = o.kn, mm = kn + (kn & 1);
+    const int n = o.n, k = o.k, kn = o.kn;
     const size_t kn2 = (size_t)kn * kn;
     cudaStream_t s;
     PK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -441,48 +516,12 @@ void build_device_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell,
     // ---- SVD of A_up1 = K(1.475 g, 0.525 g): QR with column pivoting, then
     // one-sided Jacobi on R^T ----
     {
-        DevArr<double> A(kn2), W(kn2), hv(kn2), tau(kn), c2(kn), At(kn2), Vt(kn2), U(kn2), V(kn2), S(kn), sig(kn);
-        DevArr<int> rank(kn), perm(kn);
-        DevArr<unsigned long long> rot(1);
+        DevArr<double> A(kn2);
         count_launch(), k_kmat<<<dim3(nblocks(nn, 256), 1), 256, 0, s>>>(kernel, g.p, n, kOuterHalf, kInnerHalf, 0.0,
                                                                        1.0, A.p);
-        // W = A^T (columns of A as rows); At and Vt of the transpose kernel are scratch here
-        count_launch(), k_transpose_eye<<<nblocks((long long)kn2, 256), 256, 0, s>>>(A.p, kn, W.p, Vt.p);
-        std::vector<int> iota(kn);
-        for (int i = 0; i < kn; i++) iota[i] = i;
-        PK_CUDA(cudaMemcpyAsync(perm.p, iota.data(), sizeof(int) * kn, cudaMemcpyHostToDevice, s));
-        count_launch(), k_row_norm2<<<kn, kJT, 0, s>>>(W.p, kn, c2.p);
-        for (int k = 0; k < kn; k++) {
-            count_launch(), k_qr_pivot<<<1, kQT, 0, s>>>(W.p, kn, k, c2.p, perm.p, hv.p, tau.p);
-            if (kn - k - 1 > 0)
-                count_launch(), k_qr_apply<<<kn - k - 1, kJT, 0, s>>>(W.p, kn, k, hv.p, tau.p, c2.p);
-        }
-        count_launch(), k_r_rows<<<nblocks((long long)kn2, 256), 256, 0, s>>>(W.p, kn, At.p, Vt.p);
         PK_CUDA(cudaGetLastError());
-        unsigned long long hrot = 0;
-        int sweeps = 0;
-        for (int sweep = 0; sweep < 80; sweep++, sweeps++) {
-            PK_CUDA(cudaMemsetAsync(rot.p, 0, sizeof(unsigned long long), s));
-            for (int round = 0; round < mm - 1; round++)
-                count_launch(), k_jacobi_round<<<mm / 2, kJT, 0, s>>>(At.p, Vt.p, kn, mm, round, 1e-15, rot.p);
-            PK_CUDA(cudaGetLastError());
-            PK_CUDA(cudaMemcpyAsync(&hrot, rot.p, sizeof hrot, cudaMemcpyDeviceToHost, s));
-            PK_CUDA(cudaStreamSynchronize(s));
-            if (hrot == 0) break;
-        }
-        // Q V_x: reflectors applied in reverse order to the rows of Vt
-        for (int k = kn - 1; k >= 0; k--)
-            count_launch(), k_apply_reflector<<<kn, kJT, 0, s>>>(Vt.p, kn, k, hv.p, tau.p);
-        count_launch(), k_row_norms<<<kn, kJT, 0, s>>>(At.p, kn, sig.p);
-        count_launch(), k_rank<<<nblocks(kn, 256), 256, 0, s>>>(sig.p, kn, rank.p);
-        count_launch(), k_extract_qr<<<nblocks((long long)kn2, 256), 256, 0, s>>>(At.p, Vt.p, sig.p, rank.p, perm.p,
-                                                                                kn, U.p, V.p, S.p);
-        PK_CUDA(cudaGetLastError());
-        to_host(o.U, U.p, kn2, s);
-        to_host(o.V, V.p, kn2, s);
-        to_host(o.S, S.p, (size_t)kn, s);
-        PK_CUDA(cudaStreamSynchronize(s));
-        if (phases) phases[3] = sweeps + (hrot == 0 ? 1 : 0);
+        const int sweeps = device_svd(A.p, kn, s, o.U, o.S, o.V);
+        if (phases) phases[3] = sweeps;
     }
     c2e_factors(o);
     lap(0);
@@ -529,6 +568,103 @@ void build_device_ops(HostOps &o, int kernel, int p, unsigned periodic, int ell,
     }
     lap(2);
     save_cached_ops(o, cache_dir);
+}
+
+
+void matmul_device(int m, int n, int kk, const double *A, long long sA, const double *B, long long sB, double *C,
+                   long long sC, int batch) {
+    cudaStream_t s;
+    PK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } sg{s};
+    const size_t na = (size_t)(batch - 1) * sA + (size_t)m * kk, nb = (size_t)(batch - 1) * sB + (size_t)kk * n,
+                 nc = (size_t)(batch - 1) * sC + (size_t)m * n;
+    DevArr<double> dA(na), dB(nb), dC(nc);
+    PK_CUDA(cudaMemcpyAsync(dA.p, A, sizeof(double) * na, cudaMemcpyHostToDevice, s));
+    PK_CUDA(cudaMemcpyAsync(dB.p, B, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    dgemm(m, n, kk, dA.p, sA, dB.p, sB, dC.p, sC, batch, s);
+    PK_CUDA(cudaMemcpyAsync(C, dC.p, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaStreamSynchronize(s));
+}
+
+void build_m2l_basis(int kernel, int p, double tau, int rank_override, M2LBasis &B) {
+    const int n = surface_count(p), k = kernel == 0 ? 1 : 3, kn = n * k;
+    const size_t kn2 = (size_t)kn * kn;
+    // the V-list offsets in the enumeration of the M2L operator tables
+    std::vector<int> offs, neg;
+    for (int x = -3; x <= 3; x++)
+        for (int y = -3; y <= 3; y++)
+            for (int z = -3; z <= 3; z++) {
+                if (std::max(std::abs(x), std::max(std::abs(y), std::abs(z))) <= 1) continue;
+                offs.push_back(x);
+                offs.push_back(y);
+                offs.push_back(z);
+            }
+    const int nops = (int)offs.size() / 3;
+    for (int a = 0; a < nops; a++)
+        neg.insert(neg.end(), {-offs[3 * a], -offs[3 * a + 1], -offs[3 * a + 2]});
+    cudaStream_t s;
+    PK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } sg{s};
+    const std::vector<double> gh = surface_grid(p);
+    DevArr<double> g(3 * (size_t)n);
+    PK_CUDA(cudaMemcpyAsync(g.p, gh.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    DevArr<int> doffs(offs.size()), dneg(neg.size());
+    PK_CUDA(cudaMemcpyAsync(doffs.p, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice, s));
+    PK_CUDA(cudaMemcpyAsync(dneg.p, neg.data(), sizeof(int) * neg.size(), cudaMemcpyHostToDevice, s));
+    const long long nn = (long long)n * n;
+    constexpr int kBatch = 16;
+    // G = sum_o K_o K_o^T = sum_o K_o K_{-o} (the kernel is even in r, so K_{-o} = K_o^T)
+    DevArr<double> G(kn2), A(kBatch * kn2), Bm(kBatch * kn2), P(kBatch * kn2);
+    PK_CUDA(cudaMemsetAsync(G.p, 0, sizeof(double) * kn2, s));
+    for (int b0 = 0; b0 < nops; b0 += kBatch) {
+        const int nb = std::min(kBatch, nops - b0);
+        count_launch(), k_m2l_batch<<<dim3(nblocks(nn, 256), nb), 256, 0, s>>>(kernel, g.p, n, doffs.p + 3 * b0, A.p);
+        count_launch(), k_m2l_batch<<<dim3(nblocks(nn, 256), nb), 256, 0, s>>>(kernel, g.p, n, dneg.p + 3 * b0, Bm.p);
+        dgemm(kn, kn, kn, A.p, (long long)kn2, Bm.p, (long long)kn2, P.p, (long long)kn2, nb, s);
+        count_launch(), k_sum_batch<<<nblocks((long long)kn2, 256), 256, 0, s>>>(P.p, nb, (long long)kn2, G.p);
+    }
+    PK_CUDA(cudaGetLastError());
+    // G = U S U^T: the columns of U ordered by the singular values of the stacked operators
+    std::vector<double> U, S, V;
+    device_svd(G.p, kn, s, U, S, V);
+    B.sig.assign(kn, 0.0);
+    for (int j = 0; j < kn; j++) B.sig[j] = S[0] > 0 ? std::sqrt(std::max(S[j], 0.0) / S[0]) : 0.0;
+    int r = 0;
+    if (rank_override > 0) {
+        r = std::min(rank_override, kn);
+    } else {
+        r = 64;
+        while (r < kn && B.sig[r] > tau) r += 64;
+        r = std::min(r, kn);
+    }
+    B.r = r;
+    B.Ub.assign((size_t)kn * r, 0.0);
+    for (int i = 0; i < kn; i++)
+        for (int j = 0; j < r; j++) B.Ub[(size_t)i * r + j] = U[(size_t)i * kn + j];
+    std::vector<double> Ubt((size_t)r * kn);
+    for (int i = 0; i < kn; i++)
+        for (int j = 0; j < r; j++) Ubt[(size_t)j * kn + i] = B.Ub[(size_t)i * r + j];
+    // C_o = Ub^T K_o Ub
+    DevArr<double> dUb((size_t)kn * r), dUbt((size_t)r * kn), T((size_t)kBatch * kn * r), C((size_t)kBatch * r * r);
+    PK_CUDA(cudaMemcpyAsync(dUb.p, B.Ub.data(), sizeof(double) * kn * r, cudaMemcpyHostToDevice, s));
+    PK_CUDA(cudaMemcpyAsync(dUbt.p, Ubt.data(), sizeof(double) * kn * r, cudaMemcpyHostToDevice, s));
+    B.C.assign((size_t)nops * r * r, 0.f);
+    std::vector<double> ch((size_t)kBatch * r * r);
+    for (int b0 = 0; b0 < nops; b0 += kBatch) {
+        const int nb = std::min(kBatch, nops - b0);
+        count_launch(), k_m2l_batch<<<dim3(nblocks(nn, 256), nb), 256, 0, s>>>(kernel, g.p, n, doffs.p + 3 * b0, A.p);
+        dgemm(kn, r, kn, A.p, (long long)kn2, dUb.p, 0, T.p, (long long)kn * r, nb, s);
+        dgemm(r, r, kn, dUbt.p, 0, T.p, (long long)kn * r, C.p, (long long)r * r, nb, s);
+        PK_CUDA(cudaMemcpyAsync(ch.data(), C.p, sizeof(double) * nb * r * r, cudaMemcpyDeviceToHost, s));
+        PK_CUDA(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < (size_t)nb * r * r; i++) B.C[(size_t)b0 * r * r + i] = (float)ch[i];
+    }
 }
 
 }  // namespace pk

@@ -17,8 +17,10 @@
 // operator cannot keep to 22 bits, while U, V have entries of one size.
 //
 // Precision: the tensor core truncates at every fp32 accumulation step, so the
-// work accumulator is drained into fp32 registers (round to nearest) every
-// `drain` K chunks of 64, and at every slot change.
+// work accumulator is drained into fp32 registers (round to nearest) after
+// every K chunk of 64 (PKIFMM_TRANS_DRAIN chunks; measured on a Laplace p = 8
+// clustered case: 1.1e-6 draining every chunk, 1.9e-6 every two, 8.2e-7 for the
+// binary32 SIMT product).
 //
 // Pipeline as in the M2L kernel: warps 0-3 gather the source rows (fp16,
 // split beforehand) with cp.async into the 128B-swizzled K-major layout and
@@ -43,6 +45,9 @@ namespace {
 struct TrOps {
     __half *op = nullptr;  // [2][nops][KM][KK] (hi, lo), scaled by 2^kexp
     int nops = 0, kexp = 0;
+    int M = 0, K = 0;      // output rows, input length
+    int msplit = 0;        // output rows [0, msplit) to dst, [msplit, M) to dst2
+    int KM = 0, KK = 0;    // M padded to 128 (M tiles), K to 64 (K chunks)
     CUtensorMap tmap[2];
 };
 
@@ -51,11 +56,14 @@ constexpr int kTrMaxSlots = 8;
 }  // namespace
 
 struct TrState {
-    int KM = 0, KK = 0, drain = 2;
-    TrOps ops[6];              // U^T, V, V^T, U, M2M[8], L2L[8]
-    float *sinv = nullptr;     // [KM] 1/s_j above the cut, else 0
-    __half *phi = nullptr;     // [2][phi_rows][KK] split source rows
+    int drain = 1;
+    // U^T, V, V^T, U, M2M[8], L2L[8]; with a shared M2L basis Ub (r columns):
+    // [V; Ub^T V], [M2M; Ub^T M2M][8], V^T Ub
+    TrOps ops[9];
+    float *sinv = nullptr;     // [kn padded to 128] 1/s_j above the cut, else 0
+    __half *phi = nullptr;     // [2][phi_rows][phi_kk] split source rows
     size_t phi_rows = 0;
+    int phi_kk = 0;
     float *amax = nullptr;
     int *err = nullptr;
     int *err_host = nullptr;
@@ -70,11 +78,12 @@ struct TrArgs {
     const int *slot_table;          // [box][slot_stride] source box per slot; null: the box itself
     int slot_stride, nslots;
     const int *class_ops;           // [nclass][nslots] operator of (class, slot), -1 none
-    float *dst;
+    float *dst;                     // rows of msplit values: output components [0, msplit)
+    float *dst2;                    // rows of mrows - msplit values: components [msplit, mrows)
     int beta;                       // 1: add to dst
-    const float *rscale;            // [kn] scale of each output component, nullable
+    const float *rscale;            // [KM] scale of each output component, nullable
     const float *amax;              // max |source| over the rows the task reads
-    int kn, KM, KK, nrhs, kexp, drain;
+    int mrows, msplit, KM, KK, nrhs, kexp, drain;
     int *err;
 };
 
@@ -264,7 +273,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_arrive(&wfree[wb]);
         }
         const int krow = m0 + sp * 32 + lane;
-        if (oke && krow < a.kn) {
+        if (oke && krow >= a.msplit && krow < a.mrows) {
+            const float unscale = ldexpf(a.rscale ? a.rscale[krow] : 1.0f, -(phi_exp(a.amax) + a.kexp));
+            const int w2 = a.mrows - a.msplit, k2 = krow - a.msplit;
+#pragma unroll
+            for (int c = 0; c < TC_N; c++) {
+                const long long d = drow[c];
+                if (d >= 0) a.dst2[d * w2 + k2] = acc[c] * unscale;
+            }
+        } else if (oke && krow < a.msplit) {
             const float unscale = ldexpf(a.rscale ? a.rscale[krow] : 1.0f, -(phi_exp(a.amax) + a.kexp));
             if (a.beta) {
                 // the previous values of 16 columns are loaded together (their rows differ,
@@ -275,19 +292,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 16; j++) {
                         const long long d = drow[c0 + j];
-                        old[j] = d >= 0 ? a.dst[d * a.kn + krow] : 0.f;
+                        old[j] = d >= 0 ? a.dst[d * a.msplit + krow] : 0.f;
                     }
 #pragma unroll
                     for (int j = 0; j < 16; j++) {
                         const long long d = drow[c0 + j];
-                        if (d >= 0) a.dst[d * a.kn + krow] = old[j] + acc[c0 + j] * unscale;
+                        if (d >= 0) a.dst[d * a.msplit + krow] = old[j] + acc[c0 + j] * unscale;
                     }
                 }
             } else {
 #pragma unroll
                 for (int c = 0; c < TC_N; c++) {
                     const long long d = drow[c];
-                    if (d >= 0) a.dst[d * a.kn + krow] = acc[c] * unscale;
+                    if (d >= 0) a.dst[d * a.msplit + krow] = acc[c] * unscale;
                 }
             }
         }
@@ -300,15 +317,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
-// op[o][i][j] * 2^kexp split into fp16 hi/lo, padded to KM x KK: out[h][o][i][j]
-__global__ void k_op_split(const double *__restrict__ op, int nops, int kn, int KM, int KK, int kexp,
+// op[o][i][j] (M x K each) * 2^kexp split into fp16 hi/lo, padded to KM x KK: out[h][o][i][j]
+__global__ void k_op_split(const double *__restrict__ op, int nops, int M, int K, int KM, int KK, int kexp,
                            __half *__restrict__ out) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long total = (long long)nops * KM * KK;
     if (i >= total) return;
     const int o = (int)(i / ((long long)KM * KK));
     const int rem = (int)(i % ((long long)KM * KK)), r = rem / KK, c = rem % KK;
-    double v = (r < kn && c < kn) ? ldexp(op[((long long)o * kn + r) * kn + c], kexp) : 0.0;
+    double v = (r < M && c < K) ? ldexp(op[((long long)o * M + r) * K + c], kexp) : 0.0;
     const __half hi = __float2half_rn((float)v);
     out[i] = hi;
     out[total + i] = __float2half_rn((float)(v - (double)__half2float(hi)));
@@ -394,20 +411,27 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// one operator set: nops row-major kn x kn binary64 matrices
-void make_ops(TrOps &o, const double *h, int nops, int kn, int KM, int KK) {
+// one operator set: nops row-major M x K binary64 matrices; output rows
+// [0, msplit) and [msplit, M) go to two destinations
+void make_ops(TrOps &o, const double *h, int nops, int M, int K, int msplit) {
+    o.M = M;
+    o.K = K;
+    o.msplit = msplit;
+    o.KM = (M + TC_M - 1) / TC_M * TC_M;
+    o.KK = (K + TC_K - 1) / TC_K * TC_K;
+    const int KM = o.KM, KK = o.KK;
     double mx = 0;
-    for (size_t i = 0; i < (size_t)nops * kn * kn; i++) mx = std::max(mx, std::fabs(h[i]));
+    for (size_t i = 0; i < (size_t)nops * M * K; i++) mx = std::max(mx, std::fabs(h[i]));
     int e = 0;
     if (mx > 0) std::frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
     o.kexp = 14 - e;                 // largest entry just below 2^14
     o.nops = nops;
     double *d = nullptr;
-    const size_t n = (size_t)nops * kn * kn, nk = (size_t)nops * KM * KK;
+    const size_t n = (size_t)nops * M * K, nk = (size_t)nops * KM * KK;
     PK_CUDA(cudaMalloc(&d, n * sizeof(double)));
     PK_CUDA(cudaMemcpy(d, h, n * sizeof(double), cudaMemcpyHostToDevice));
     PK_CUDA(cudaMalloc(&o.op, 2 * nk * sizeof(__half)));
-    count_launch(), k_op_split<<<(unsigned)((nk + 255) / 256), 256>>>(d, nops, kn, KM, KK, o.kexp, o.op);
+    count_launch(), k_op_split<<<(unsigned)((nk + 255) / 256), 256>>>(d, nops, M, K, KM, KK, o.kexp, o.op);
     PK_CUDA(cudaGetLastError());
     PK_CUDA(cudaDeviceSynchronize());
     cudaFree(d);
@@ -444,29 +468,54 @@ void trans_tc_prepare(Plan &P) {
     const int kn = P.kn;
     TrState *t = new TrState;
     P.tr = t;
-    t->KM = (kn + TC_M - 1) / TC_M * TC_M;
-    t->KK = (kn + TC_K - 1) / TC_K * TC_K;
     if (const char *e = std::getenv("PKIFMM_TRANS_DRAIN"); e && std::atoi(e) >= 1) t->drain = std::atoi(e);
     const size_t kn2 = (size_t)kn * kn;
-    std::vector<double> Ut(kn2), V(kn2), Vt(kn2), U(kn2);
+    std::vector<double> Ut(kn2), Vt(kn2);
     for (int i = 0; i < kn; i++)
         for (int j = 0; j < kn; j++) {
             Ut[(size_t)i * kn + j] = H.U[(size_t)j * kn + i];
-            V[(size_t)i * kn + j] = H.V[(size_t)i * kn + j];
             Vt[(size_t)i * kn + j] = H.V[(size_t)j * kn + i];
-            U[(size_t)i * kn + j] = H.U[(size_t)i * kn + j];
         }
-    make_ops(t->ops[0], Ut.data(), 1, kn, t->KM, t->KK);
-    make_ops(t->ops[1], V.data(), 1, kn, t->KM, t->KK);
-    make_ops(t->ops[2], Vt.data(), 1, kn, t->KM, t->KK);
-    make_ops(t->ops[3], U.data(), 1, kn, t->KM, t->KK);
-    make_ops(t->ops[4], H.m2m.data(), 8, kn, t->KM, t->KK);
-    make_ops(t->ops[5], H.l2l.data(), 8, kn, t->KM, t->KK);
-    std::vector<float> sinv(t->KM, 0.f);
+    make_ops(t->ops[0], Ut.data(), 1, kn, kn, kn);
+    make_ops(t->ops[1], H.V.data(), 1, kn, kn, kn);
+    make_ops(t->ops[2], Vt.data(), 1, kn, kn, kn);
+    make_ops(t->ops[3], H.U.data(), 1, kn, kn, kn);
+    make_ops(t->ops[4], H.m2m.data(), 8, kn, kn, kn);
+    make_ops(t->ops[5], H.l2l.data(), 8, kn, kn, kn);
+    if (P.basis && P.basis->r > 0) {
+        // the V-list M2L runs in the basis Ub: the upward passes also write
+        // Ub^T phi (stacked below V and below each M2M operator), the downward
+        // solve starts from the M2L output in that basis (V^T Ub)
+        const int r = P.basis->r;
+        const std::vector<double> &Ub = P.basis->Ub;
+        std::vector<double> Ubt((size_t)r * kn);
+        for (int i = 0; i < kn; i++)
+            for (int j = 0; j < r; j++) Ubt[(size_t)j * kn + i] = Ub[(size_t)i * r + j];
+        std::vector<double> UbtV((size_t)r * kn), UbtT((size_t)8 * r * kn), VtUb((size_t)kn * r);
+        matmul_device(r, kn, kn, Ubt.data(), 0, H.V.data(), 0, UbtV.data(), 0, 1);
+        matmul_device(r, kn, kn, Ubt.data(), 0, H.m2m.data(), (long long)kn2, UbtT.data(), (long long)r * kn, 8);
+        matmul_device(kn, r, kn, Vt.data(), 0, Ub.data(), 0, VtUb.data(), 0, 1);
+        const size_t ms = (size_t)(kn + r) * kn;
+        std::vector<double> st((size_t)8 * ms);
+        for (int c = 0; c < 8; c++) {
+            const double *top = H.m2m.data() + (size_t)c * kn2;
+            std::copy(top, top + kn2, st.begin() + (size_t)c * ms);
+            std::copy(UbtT.begin() + (size_t)c * r * kn, UbtT.begin() + (size_t)(c + 1) * r * kn,
+                      st.begin() + (size_t)c * ms + kn2);
+        }
+        make_ops(t->ops[7], st.data(), 8, kn + r, kn, kn);
+        st.resize(ms);
+        std::copy(H.V.begin(), H.V.end(), st.begin());
+        std::copy(UbtV.begin(), UbtV.end(), st.begin() + kn2);
+        make_ops(t->ops[6], st.data(), 1, kn + r, kn, kn);
+        make_ops(t->ops[8], VtUb.data(), 1, kn, r, kn);
+    }
+    const int km = t->ops[0].KM;
+    std::vector<float> sinv(km, 0.f);
     const double cut = H.eps_rel * H.S[0];
     for (int j = 0; j < kn; j++) sinv[j] = H.S[j] > cut ? (float)(1.0 / H.S[j]) : 0.f;
-    PK_CUDA(cudaMalloc(&t->sinv, sizeof(float) * t->KM));
-    PK_CUDA(cudaMemcpy(t->sinv, sinv.data(), sizeof(float) * t->KM, cudaMemcpyHostToDevice));
+    PK_CUDA(cudaMalloc(&t->sinv, sizeof(float) * km));
+    PK_CUDA(cudaMemcpy(t->sinv, sinv.data(), sizeof(float) * km, cudaMemcpyHostToDevice));
     PK_CUDA(cudaMalloc(&t->amax, sizeof(float)));
     PK_CUDA(cudaMalloc(&t->err, sizeof(int)));
     PK_CUDA(cudaMemset(t->err, 0, sizeof(int)));
@@ -475,27 +524,31 @@ void trans_tc_prepare(Plan &P) {
 }
 
 void trans_tc_gemm(Plan &P, int set, const Task &task, const int *slot_table, int slot_stride, const float *src,
-                   float *dst, int beta, cudaStream_t s) {
+                   float *dst, int beta, cudaStream_t s, float *dst2) {
     if (task.ntiles == 0) return;
     TrState *t = P.tr;
     if (!t) throw Error(PKIFMM_ERR_UNSUPPORTED, "tensor-core translations not prepared");
+    const TrOps &o = t->ops[set];
+    if (!o.op) throw Error(PKIFMM_ERR_UNSUPPORTED, "translation operator set not prepared");
     if (task.nslots > kTrMaxSlots) throw Error(PKIFMM_ERR_INVALID_ARG, "translation task with too many slots");
-    const int kn = P.kn, nr = P.nrhs, KK = t->KK;
+    if (o.msplit < o.M && (!dst2 || beta)) throw Error(PKIFMM_ERR_INVALID_ARG, "stacked translation needs dst2");
+    const int nr = P.nrhs, KK = o.KK;
     const size_t rows = (size_t)P.tree.nbox * nr + 1;
-    if (rows > t->phi_rows) {
+    if (rows > t->phi_rows || KK > t->phi_kk) {
         cudaFree(t->phi);
         t->phi = nullptr;
-        t->phi_rows = rows + rows / 4;
-        PK_CUDA(cudaMalloc(&t->phi, 2 * t->phi_rows * KK * sizeof(__half)));
+        t->phi_rows = std::max(t->phi_rows, rows + rows / 4);
+        t->phi_kk = std::max(t->phi_kk, KK);
+        PK_CUDA(cudaMalloc(&t->phi, 2 * t->phi_rows * t->phi_kk * sizeof(__half)));
     }
-    __half *hi = t->phi, *lo = t->phi + t->phi_rows * KK;
+    __half *hi = t->phi, *lo = t->phi + t->phi_rows * t->phi_kk;
     const int nbt = (int)task.h_boxes.size();
     const dim3 g(nbt, task.nslots);
     PK_CUDA(cudaMemsetAsync(t->amax, 0, sizeof(float), s));
     const int nitems = nbt * task.nslots;
     count_launch(), k_task_amax<<<std::min(nitems, 2048), 256, 0, s>>>(src, task.boxes.p, nbt, slot_table, slot_stride,
-                                                                     task.nslots, nr, kn, t->amax);
-    count_launch(), k_task_split<<<g, 256, 0, s>>>(src, task.boxes.p, slot_table, slot_stride, nr, kn, KK, t->amax,
+                                                                     task.nslots, nr, o.K, t->amax);
+    count_launch(), k_task_split<<<g, 256, 0, s>>>(src, task.boxes.p, slot_table, slot_stride, nr, o.K, KK, t->amax,
                                                    hi, lo);
     TrArgs a;
     std::memset(&a, 0, sizeof a);
@@ -508,19 +561,20 @@ void trans_tc_gemm(Plan &P, int set, const Task &task, const int *slot_table, in
     a.nslots = task.nslots;
     a.class_ops = task.class_ops.p;
     a.dst = dst;
+    a.dst2 = dst2;
     a.beta = beta;
-    a.rscale = (set == 0 || set == 2) ? t->sinv : nullptr;
+    a.rscale = (set == 0 || set == 2 || set == 8) ? t->sinv : nullptr;
     a.amax = t->amax;
-    a.kn = kn;
-    a.KM = t->KM;
+    a.mrows = o.M;
+    a.msplit = o.msplit;
+    a.KM = o.KM;
     a.KK = KK;
     a.nrhs = nr;
-    a.kexp = t->ops[set].kexp;
+    a.kexp = o.kexp;
     a.drain = t->drain;
     a.err = t->err;
-    const int mtiles = t->KM / TC_M;
-    count_launch(), k_trans_tc<3><<<task.ntiles * mtiles, TC_THREADS, tc_smem(3), s>>>(t->ops[set].tmap[0],
-                                                                                       t->ops[set].tmap[1], a);
+    const int mtiles = o.KM / TC_M;
+    count_launch(), k_trans_tc<3><<<task.ntiles * mtiles, TC_THREADS, tc_smem(3), s>>>(o.tmap[0], o.tmap[1], a);
     PK_CUDA(cudaGetLastError());
 }
 

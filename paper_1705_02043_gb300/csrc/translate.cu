@@ -19,6 +19,9 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "internal.h"
@@ -63,6 +66,32 @@ static void upload(DBuf<T> &d, const std::vector<double> &h) {
     d.reserve(h.size() + 1);
     std::vector<T> t(h.begin(), h.end());
     PK_CUDA(cudaMemcpy(d.p, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice));
+}
+
+// The V-list M2L of the MIXED path runs in the shared basis of the 316
+// operators (build_m2l_basis) when that cuts the padded tensor-core work by at
+// least 30%: rank r at a relative singular value tau = max(30 eps_SVD(FP64),
+// 5e-7), below the error the surfaces reach at this p.  PKIFMM_M2L_RANK=0
+// keeps the dense operators, a positive value fixes r.  Built once per process
+// for each (kernel, p, tau, r).
+static std::shared_ptr<const M2LBasis> m2l_basis_for(int kernel, int p, int kn) {
+    int over = -1;
+    if (const char *e = std::getenv("PKIFMM_M2L_RANK")) over = std::atoi(e);
+    if (over == 0) return nullptr;
+    const double tau = std::max(30.0 * svd_cut(kernel, p, 0, kn), 5e-7);
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, double, int>, std::shared_ptr<const M2LBasis>> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(kernel, p, tau, over);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    auto b = std::make_shared<M2LBasis>();
+    build_m2l_basis(kernel, p, tau, over > 0 ? over : 0, *b);
+    const auto pad = [](int v, int q) { return (long long)((v + q - 1) / q * q); };
+    const bool worth = b->r < kn && 10 * pad(b->r, 128) * pad(b->r, 64) <= 7 * pad(kn, 128) * pad(kn, 64);
+    std::shared_ptr<const M2LBasis> out = (worth || over > 0) && b->r < kn ? b : nullptr;
+    cache[key] = out;
+    return out;
 }
 
 void upload_operators(Plan &P) {
@@ -136,11 +165,13 @@ void upload_operators(Plan &P) {
     PK_CUDA(cudaDeviceSynchronize());
     doffs.release();
     if (P.precision == PKIFMM_MIXED) {
-        m2l_tc_prepare(P);
         // the dense translations on the tensor cores; PKIFMM_TRANS_TC=0 keeps the
         // binary32 SIMT GEMM (timing comparisons)
         const char *e = std::getenv("PKIFMM_TRANS_TC");
-        if (!e || std::atoi(e) != 0) trans_tc_prepare(P);
+        const bool tc = !e || std::atoi(e) != 0;
+        if (tc) P.basis = m2l_basis_for(P.kernel, P.p, P.kn);
+        m2l_tc_prepare(P);
+        if (tc) trans_tc_prepare(P);
     }
 }
 
@@ -454,6 +485,8 @@ void build_tasks(Plan &P, cudaStream_t s) {
     for (int b = (mixed ? P.nprob : 0); b < nb; b++)
         if (H.has_trg(b)) dc.push_back(b);
     make_task(P.t_dc2e, {dc}, 1, {0}, nr, up, bm);
+    // MIXED with a shared M2L basis: the X-list part of the check potential is solved separately
+    if (P.basis) make_task(P.t_dcx, {xb}, 1, {0}, nr, up, bm);
     // L2L per level >= 1, by octant class
     P.t_l2l.resize(depth);
     for (int l = 1; l < depth; l++) {
@@ -1126,6 +1159,12 @@ static void prepare_points(Plan &P, cudaStream_t s) {
     B::dn(P).reserve(rows);
     B::tmp(P).reserve(rows);
     PK_CUDA(cudaMemsetAsync(B::up(P).p, 0, sizeof(T) * rows, s));
+    if (P.basis) {  // Ub^T phi_u is written for boxes with sources only; the others are V sources of zero density
+        const size_t rr = (size_t)P.tree.nbox * P.nrhs * P.basis->r;
+        P.uphat32.reserve(rr);
+        P.chkhat32.reserve(rr);
+        PK_CUDA(cudaMemsetAsync(P.uphat32.p, 0, sizeof(float) * rr, s));
+    }
 }
 
 template <typename T, int K, int KS = K>
@@ -1150,6 +1189,12 @@ static void upward_t(Plan &P, cudaStream_t s) {
     if constexpr (std::is_same<T, float>::value) {
         if (P.tr) {  // tensor cores: tmp = S+ (U^T q~u), up = V tmp, then M2M level by level
             trans_tc_gemm(P, 0, P.t_uc2e, nullptr, 1, P.chk32.p, P.tmp32.p, 0, s);
+            if (P.basis) {  // with Ub^T phi_u for the M2L in the shared basis
+                trans_tc_gemm(P, 6, P.t_uc2e, nullptr, 1, P.tmp32.p, P.up32.p, 0, s, P.uphat32.p);
+                for (int l = (int)P.t_m2m.size() - 1; l >= 0; l--)
+                    trans_tc_gemm(P, 7, P.t_m2m[l], P.tree.child.p, 8, P.up32.p, P.up32.p, 0, s, P.uphat32.p);
+                return;
+            }
             trans_tc_gemm(P, 1, P.t_uc2e, nullptr, 1, P.tmp32.p, P.up32.p, 0, s);
             for (int l = (int)P.t_m2m.size() - 1; l >= 0; l--)
                 trans_tc_gemm(P, 4, P.t_m2m[l], P.tree.child.p, 8, P.up32.p, P.up32.p, 0, s);
@@ -1228,6 +1273,8 @@ static void downward_t(Plan &P, cudaStream_t s) {
     const int kn = P.kn, nr = P.nrhs;
     const long long kn2 = (long long)kn * kn;
     auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
+    // with a shared M2L basis the M2L output is not in the check rows: the X-list sums start from zero
+    if (P.basis && P.n_xboxes) PK_CUDA(cudaMemsetAsync(P.chk32.p, 0, sizeof(float) * P.tree.nbox * nr * kn, s));
     if (P.n_xboxes)
         for (int r = 0; r < nr; r += 4) {
             auto go = [&](auto rt) {
@@ -1242,7 +1289,11 @@ static void downward_t(Plan &P, cudaStream_t s) {
         }
     bool tc = false;
     if constexpr (std::is_same<T, float>::value) tc = P.tr != nullptr;
-    if (tc) {  // tensor cores: tmp = S+ (V^T q~d), dn = U tmp
+    if (tc && P.basis) {  // tmp = S+ (V^T Ub q^) + S+ (V^T q~x), dn = U tmp
+        trans_tc_gemm(P, 8, P.t_dc2e, nullptr, 1, P.chkhat32.p, P.tmp32.p, 0, s);
+        if (P.n_xboxes) trans_tc_gemm(P, 2, P.t_dcx, nullptr, 1, P.chk32.p, P.tmp32.p, 1, s);
+        trans_tc_gemm(P, 3, P.t_dc2e, nullptr, 1, P.tmp32.p, P.dn32.p, 0, s);
+    } else if (tc) {  // tensor cores: tmp = S+ (V^T q~d), dn = U tmp
         trans_tc_gemm(P, 2, P.t_dc2e, nullptr, 1, P.chk32.p, P.tmp32.p, 0, s);
         trans_tc_gemm(P, 3, P.t_dc2e, nullptr, 1, P.tmp32.p, P.dn32.p, 0, s);
     } else {

@@ -182,3 +182,30 @@ def test_tensor_core_translations_match_binary32(kernel, periodic, nrhs, cluster
     print(f"kernel {kernel} periodic {periodic} nrhs {nrhs}: tensor {et:.3e} simt {es:.3e} tensor-vs-simt {d:.3e}")
     assert d < 2e-5
     assert et < 1e-5 and et < es + 1e-6
+
+
+@pytest.mark.parametrize("kernel,periodic,p,clustered", [(1, 7, 8, False), (0, 7, 6, False), (1, 3, 10, True)])
+def test_shared_basis_m2l_matches_dense(kernel, periodic, p, clustered, cache, monkeypatch):
+    """The V-list M2L run in the shared basis of the 316 offset operators
+    (Ub^T K_o Ub, the rank cut where the stacked operators' singular values
+    fall below max(30 eps_SVD, 5e-7)) is as accurate against the oracle as the
+    dense M2L: its truncation sits below the surfaces' own error at p."""
+    n = 30000
+    k = 1 if kernel == 0 else 3
+    if clustered:
+        x, _ = w.clustered_slab(n, seed=33, nclusters=8, sigma=0.03, zlo=0.0, zhi=0.3, kdim=1)
+    else:
+        x = w.uniform_points(n, seed=33)
+    dens = w.make_neutral(np.random.default_rng(34).standard_normal((n, k)))
+    d = dens if k == 3 else dens[:, 0]
+    idx = _sample(n, 300)
+    ref = oracle.periodic_sum(kernel, periodic, x, d, x[idx])
+    monkeypatch.setenv("PKIFMM_M2L_RANK", "0")
+    ud = run(kernel, periodic, x, d, x, p=p, leaf=48, depth=12, precision=1, cache_dir=cache)
+    monkeypatch.delenv("PKIFMM_M2L_RANK")
+    uc = run(kernel, periodic, x, d, x, p=p, leaf=48, depth=12, precision=1, cache_dir=cache)
+    ed, ec = rel_l2(ud[idx], ref), rel_l2(uc[idx], ref)
+    print(f"kernel {kernel} periodic {periodic} p {p}: shared basis {ec:.3e} dense {ed:.3e} "
+          f"basis-vs-dense {rel_l2(uc, ud):.3e}")
+    tol = 1.5e-5 if (kernel == 0 and p == 6) else 1e-5
+    assert ec < tol and ec < 1.5 * ed + 2e-6
