@@ -336,6 +336,13 @@ def main():
     clocks = clk.stop()
     stages = plan.stage_times().tolist()
     stats = plan.tree_stats().tolist()
+    m2l_rank = plan.m2l_rank()
+    m2l_rank_p = None
+    if kernel == 3:  # the pressure plan's Laplace M2L works in its own dimension
+        lp = pk.PeriodicKIFMM(0, periodic, p=args.p, ell=args.ell, leaf_max=args.leaf, depth_max=wl["depth"],
+                              precision=pk.MIXED, nrhs=nrhs, cache_dir=cache)
+        m2l_rank_p = lp.m2l_rank()
+        lp.close()
     t_step = multi.max_over_ranks(float(np.mean(step_ms)), dist, dev)
     value = world * ntrg * nrhs / (t_step / 1e3)
 
@@ -374,16 +381,20 @@ def main():
         nV = stats[4]
         nsurf = 6 * (args.p - 1) ** 2 + 2
         kn = ks * nsurf
-        flops = 2.0 * kn * kn * nV * nrhs  # per M2L (all launches of one evaluation)
-        if kernel == 3:  # plus the Laplace field evaluation's M2L on 3 nrhs charge vectors
-            flops += 2.0 * nsurf * nsurf * nV * 3 * nrhs
+        rk = m2l_rank  # kn, or r of the shared M2L basis
+        flops = 2.0 * rk * rk * nV * nrhs  # per M2L (all launches of one evaluation)
+        if kernel == 3:  # plus the pressure evaluation's M2L (Laplace translations, one vector)
+            flops += 2.0 * m2l_rank_p * m2l_rank_p * nV * nrhs
         m2l_avg = float(np.mean(m2l_ms))
         achieved = flops / (m2l_avg / 1e3) / 1e12
         peak = pk_.get("bf16_tflops_sustained", 1700.0)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": m2l_traffic(workload_name(args.workload, wl, args.n, args.p, args.leaf)),
-                "kernel": "k_m2l_tc: M2L (V list), split-fp16 x3 tcgen05",
+                "kernel": "k_m2l_tc / k_m2l_tcw: M2L (V list), split-fp16 x3 tcgen05",
+                "m2l_dimension": m2l_rank, "kn": kn,
+                "flops_counted": "2 r^2 per V pair and vector, r the dimension the M2L works in "
+                                 "(the shared basis's rank, or kn for dense operators)",
                 "peak_source": f"bf16_tflops_sustained ({src}), same rate as fp16",
                 "algorithmic_flops_per_launch": flops, "avg_launch_ms": m2l_avg,
                 "issued_tensor_frac": achieved * 3 / peak}

@@ -323,6 +323,14 @@ const char *pkifmm_last_error_message(void);
  * launches inside it. */
 int64_t pkifmm_launch_count(void);
 
+/* Dimension the plan's V-list M2L works in (Sec. 2.2, the M2L translation):
+ * kn = k (6(p-1)^2 + 2) when it applies the 316 dense check-form operators
+ * K_o (FP64 plans, and MIXED plans where a shared basis would not cut the
+ * tensor-core work by 30%), or r < kn when the MIXED path applies
+ * C_o = Ub^T K_o Ub in the shared basis Ub of the stacked operators (r columns;
+ * see include notes of pkifmm_plan_create).  Negative on a NULL plan. */
+int pkifmm_m2l_rank(pkifmm_plan plan);
+
 /* 1 if MIXED plans run their M2L on the tensor cores of the current device
  * (tcgen05, sm_103), else 0 (MIXED plans then fail with UNSUPPORTED). */
 int pkifmm_m2l_tensor_core_enabled(void);

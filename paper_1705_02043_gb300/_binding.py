@@ -62,6 +62,7 @@ def load_library():
             lib.pkifmm_strerror.restype = ctypes.c_char_p
             lib.pkifmm_morton_order_noalloc.argtypes = [i64, P, P, d, u, i, P, P]
             lib.pkifmm_m2l_tensor_core_enabled.argtypes = []
+            lib.pkifmm_m2l_rank.argtypes = [P]
             lib.pkifmm_launch_count.argtypes = []
             lib.pkifmm_launch_count.restype = ctypes.c_int64
             lib.pkifmm_last_error_message.argtypes = []
@@ -233,6 +234,10 @@ def pkifmm_morton_order_noalloc(n, xyz, box_lo, box_len, periodic_axes, depth, p
                                                              depth, _ptr(perm), stream))
 
 
+def pkifmm_m2l_rank(plan):
+    return _check(load_library().pkifmm_m2l_rank(plan))
+
+
 def pkifmm_plan_destroy(plan):
     if plan:
         load_library().pkifmm_plan_destroy(plan)
@@ -346,6 +351,10 @@ class PeriodicKIFMM:
 
     def stage_times(self):
         return pkifmm_last_stage_times(self.handle)
+
+    def m2l_rank(self):
+        """Dimension of the V-list M2L: kn (dense operators) or the shared basis's r."""
+        return pkifmm_m2l_rank(self.handle)
 
     def tree_stats(self):
         return pkifmm_tree_stats(self.handle)

@@ -248,7 +248,8 @@ int evaluate_impl(Plan &P, int nprob, const int64_t *soff, const int64_t *toff, 
     }
     sort_points(P, src, dens, trg, s);
     int err[4] = {0, 0, 0, 0};
-    PK_CUDA(cudaMemcpy(err, P.err.p, sizeof err, cudaMemcpyDeviceToHost));
+    PK_CUDA(cudaMemcpyAsync(err, P.err.p, sizeof err, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaStreamSynchronize(s));
     if (err[0]) return fail(PKIFMM_ERR_INVALID_ARG, "non-finite coordinate");
     if (err[1]) return fail(PKIFMM_ERR_OUT_OF_BOX, "point outside the box along a free axis");
     if (needs_neutral(P)) {
@@ -401,6 +402,9 @@ static void destroy_plan(pkifmm_plan_s *plan) {
     P.tree.x_sh.release();
     P.slot_of.release();
     P.csr.release();
+    P.xn.release();
+    P.lcnt.release();
+    P.lpairs.release();
     P.ctr.release();
     P.soff.release();
     P.toff.release();
@@ -920,6 +924,12 @@ const char *pkifmm_strerror(int code) {
 const char *pkifmm_last_error_message(void) { return g_last_error.c_str(); }
 
 int64_t pkifmm_launch_count(void) { return g_launches.load(); }
+
+int pkifmm_m2l_rank(pkifmm_plan plan) {
+    if (!plan) return fail(PKIFMM_ERR_INVALID_ARG, "plan is NULL");
+    const Plan &P = plan->P;
+    return P.basis ? P.basis->r : P.kn;
+}
 
 int pkifmm_m2l_tensor_core_enabled(void) { return m2l_tc_device_supported() ? 1 : 0; }
 

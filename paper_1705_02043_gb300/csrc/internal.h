@@ -155,6 +155,9 @@ struct Plan {
     DBuf<float> uphat32, chkhat32;
     // tree build scratch
     DBuf<int> cnt, off;
+    DBuf<double> xn;                            // normalised coordinates before the gather
+    DBuf<int> lcnt;                             // [3][nbox] U / W / X list lengths
+    DBuf<unsigned long long> lpairs;            // [2] P2P pairs, V entries
     DBuf<int2> csr, ctr;                        // [nlevel boxes][8] child ranges
     DBuf<int> gather_idx;
     Tree tree;

@@ -296,12 +296,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                              : "memory");
             } else {
                 // absent source: zeros written here, no global read (a shared
-                // zero row read by every CTA would serialise on one L2 line)
+                // zero row read by every CTA would serialise on one L2 line);
+                // rows past the tile feed output columns that are never stored
+                if (r < nr) {
 #pragma unroll
-                for (int h = 0; h < 2; h++)
+                    for (int h = 0; h < 2; h++)
 #pragma unroll
-                    for (int c = 0; c < 8; c++)
-                        *reinterpret_cast<uint4 *>(rowdst + h * TC_B_BYTES + (c << 4)) = make_uint4(0, 0, 0, 0);
+                        for (int c = 0; c < 8; c++)
+                            *reinterpret_cast<uint4 *>(rowdst + h * TC_B_BYTES + (c << 4)) = make_uint4(0, 0, 0, 0);
+                }
                 mbar_arrive(&full[st]);  // release: orders the zero stores before the MMA's acquire
             }
         }

@@ -87,9 +87,16 @@ struct TrArgs {
     int *err;
 };
 
+// Tiles marked regular (tile.w = 1: source rows src0 + i; 8: src0 + 8 i, with
+// one density vector) load their 128 source rows per split by one TMA, through
+// a 2D view of the split rows (tB1) or a 3D view with rows grouped by eight
+// (tB8, coordinates (k, src0 % 8, src0 / 8 + i)); the other tiles gather rows
+// with cp.async.
 template <int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_trans_tc(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo, TrArgs a) {
+    k_trans_tc(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+               const __grid_constant__ CUtensorMap tB1_hi, const __grid_constant__ CUtensorMap tB1_lo,
+               const __grid_constant__ CUtensorMap tB8_hi, const __grid_constant__ CUtensorMap tB8_lo, TrArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)smem;          // [STAGES]
@@ -158,7 +165,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
     const int total = nact * kchunks;
 
-    if (warp < 4) {
+    if (warp < 4 && tile.w) {
+        // ---- producer (regular tile): one thread, TMA for both operands ----
+        const int mode = tile.w;
+        int cur_si = -1, src0 = 0;
+        for (int it = 0; it < total; it++) {
+            const int st = it % STAGES;
+            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+            if (!mbar_wait(&empty[st], ph ^ 1u, a.err)) break;
+            const int si = it / kchunks, k0 = (it % kchunks) * TC_K;
+            uint8_t *sb = stages + (size_t)st * TC_STAGE_BYTES;
+            if (tid == 0) {
+                if (si != cur_si) {
+                    cur_si = si;
+                    const int box0 = sbox[0];
+                    src0 = a.slot_table ? a.slot_table[(long long)box0 * a.slot_stride + act[si]] : box0;
+                }
+                const int op = a.class_ops[cls * a.nslots + act[si]];
+                mbar_expect_tx(&full[st], (uint32_t)(2 * TC_A_BYTES + 2 * TC_B_BYTES));
+                tma_load_2d(sb, &tA_hi, k0, op * a.KM + m0, &full[st]);
+                tma_load_2d(sb + TC_A_BYTES, &tA_lo, k0, op * a.KM + m0, &full[st]);
+                if (mode == 8) {
+                    tma_load_3d(sb + 2 * TC_A_BYTES, &tB8_hi, k0, src0 & 7, src0 >> 3, &full[st]);
+                    tma_load_3d(sb + 2 * TC_A_BYTES + TC_B_BYTES, &tB8_lo, k0, src0 & 7, src0 >> 3, &full[st]);
+                } else {
+                    tma_load_2d(sb + 2 * TC_A_BYTES, &tB1_hi, k0, src0, &full[st]);
+                    tma_load_2d(sb + 2 * TC_A_BYTES + TC_B_BYTES, &tB1_lo, k0, src0, &full[st]);
+                }
+            }
+            mbar_arrive(&full[st]);  // 128 arrivals, as in the gather path
+        }
+    } else if (warp < 4) {
         // ---- producers: gather the source rows (cp.async) and TMA the operator tiles ----
         const int r = tid;
         const int rhs = (row0 + r) % a.nrhs, box = sbox[r];
@@ -196,11 +233,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st]))
                              : "memory");
             } else {
+                // a row of the tile without a source in this slot reads zeros; rows past
+                // the tile feed output columns that are never stored and stay as they are
+                if (r < nr) {
 #pragma unroll
-                for (int h = 0; h < 2; h++)
+                    for (int h = 0; h < 2; h++)
 #pragma unroll
-                    for (int c = 0; c < 8; c++)
-                        *reinterpret_cast<uint4 *>(rowdst + h * TC_B_BYTES + (c << 4)) = make_uint4(0, 0, 0, 0);
+                        for (int c = 0; c < 8; c++)
+                            *reinterpret_cast<uint4 *>(rowdst + h * TC_B_BYTES + (c << 4)) = make_uint4(0, 0, 0, 0);
+                }
                 mbar_arrive(&full[st]);
             }
         }
@@ -523,6 +564,32 @@ void trans_tc_prepare(Plan &P) {
     PK_CUDA(cudaFuncSetAttribute(k_trans_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(3)));
 }
 
+// 2D (rows) and 3D (rows by eight) tensor maps of one split, 64 x 128 boxes, 128-byte swizzle
+static void phi_maps(const __half *base, size_t rows, int KK, CUtensorMap &m1, CUtensorMap &m8) {
+    EncodeTiledFn enc = encode_fn();
+    const cuuint64_t row = (cuuint64_t)KK * 2;
+    {
+        cuuint64_t dims[2] = {(cuuint64_t)KK, (cuuint64_t)rows};
+        cuuint64_t strides[1] = {row};
+        cuuint32_t box[2] = {TC_K, TC_N};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = enc(&m1, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void *)base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) throw Error(PKIFMM_ERR_CUDA, "cuTensorMapEncodeTiled (translation rows) failed");
+    }
+    {
+        cuuint64_t dims[3] = {(cuuint64_t)KK, 8, (cuuint64_t)(rows / 8)};
+        cuuint64_t strides[2] = {row, row * 8};
+        cuuint32_t box[3] = {TC_K, 1, TC_N};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = enc(&m8, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, (void *)base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) throw Error(PKIFMM_ERR_CUDA, "cuTensorMapEncodeTiled (translation rows by 8) failed");
+    }
+}
+
 void trans_tc_gemm(Plan &P, int set, const Task &task, const int *slot_table, int slot_stride, const float *src,
                    float *dst, int beta, cudaStream_t s, float *dst2) {
     if (task.ntiles == 0) return;
@@ -574,7 +641,11 @@ void trans_tc_gemm(Plan &P, int set, const Task &task, const int *slot_table, in
     a.drain = t->drain;
     a.err = t->err;
     const int mtiles = o.KM / TC_M;
-    count_launch(), k_trans_tc<3><<<task.ntiles * mtiles, TC_THREADS, tc_smem(3), s>>>(o.tmap[0], o.tmap[1], a);
+    CUtensorMap b1[2], b8[2];
+    phi_maps(hi, t->phi_rows, KK, b1[0], b8[0]);  // rows as k_task_split writes them: stride KK
+    phi_maps(lo, t->phi_rows, KK, b1[1], b8[1]);
+    count_launch(), k_trans_tc<3><<<task.ntiles * mtiles, TC_THREADS, tc_smem(3), s>>>(o.tmap[0], o.tmap[1], b1[0],
+                                                                                       b1[1], b8[0], b8[1], a);
     PK_CUDA(cudaGetLastError());
 }
 

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -379,18 +380,46 @@ struct Uploads {
     }
 };
 
+// src (nullable): source box of (box, slot).  With one density vector a tile
+// whose source boxes are src0 + i (or src0 + 8 i, the children of consecutive
+// parents of a full level) for every slot of its class is marked in .w (1 or 8):
+// the tensor-core translations then load its source rows by TMA.
 static void make_task(Task &t, const std::vector<std::vector<int>> &by_class, int nslots,
-                      const std::vector<int> &class_ops, int nrhs, Uploads &up, int bm = GB_M) {
+                      const std::vector<int> &class_ops, int nrhs, Uploads &up, int bm = GB_M,
+                      const std::function<int(int, int)> &src = nullptr) {
     t.nclass = (int)by_class.size();
     t.nslots = nslots;
     t.h_boxes.clear();
     t.class_count.clear();
     for (auto &v : by_class) t.class_count.push_back((int)v.size());
     std::vector<int4> tiles;
+    auto regular = [&](const std::vector<int> &bx, int c, int i0, int n) {
+        if (!src || nrhs != 1) return 0;
+        int stride = 0;
+        for (int s = 0; s < nslots; s++) {
+            if (class_ops[c * nslots + s] < 0) continue;
+            const int a0 = src(bx[i0], s);
+            if (a0 < 0) return 0;
+            int st = 0;
+            if (n > 1) {
+                st = src(bx[i0 + 1], s) - a0;
+                if (st != 1 && st != 8) return 0;
+            }
+            for (int i = 2; i < n; i++)
+                if (src(bx[i0 + i], s) != a0 + st * i) return 0;
+            if (n > 1) {
+                if (stride && st != stride) return 0;
+                stride = st;
+            }
+        }
+        return stride ? stride : 1;
+    };
     for (int c = 0; c < t.nclass; c++) {
         int row0 = (int)t.h_boxes.size() * nrhs;
         int nrows = (int)by_class[c].size() * nrhs;
-        for (int r = 0; r < nrows; r += bm) tiles.push_back(make_int4(c, row0 + r, std::min(bm, nrows - r), 0));
+        for (int r = 0; r < nrows; r += bm)
+            tiles.push_back(make_int4(c, row0 + r, std::min(bm, nrows - r),
+                                      regular(by_class[c], c, r / nrhs, std::min(bm, nrows - r) / nrhs)));
         t.h_boxes.insert(t.h_boxes.end(), by_class[c].begin(), by_class[c].end());
     }
     t.nrows = (int)t.h_boxes.size() * nrhs;
@@ -463,7 +492,8 @@ void build_tasks(Plan &P, cudaStream_t s) {
     bool mixed = P.precision == PKIFMM_MIXED;
     const int bm = mixed ? GemmCfg<float>::BM : GemmCfg<double>::BM;
     // UC2E over leaves with sources
-    make_task(P.t_uc2e, {leaves_src}, 1, {0}, nr, up, bm);
+    const auto self = [](int b, int) { return b; };
+    make_task(P.t_uc2e, {leaves_src}, 1, {0}, nr, up, bm, self);
     // M2M per level: non-leaf boxes with sources
     int depth = (int)t.lvl_begin.size() - 1;
     P.t_m2m.resize(depth);
@@ -473,7 +503,7 @@ void build_tasks(Plan &P, cudaStream_t s) {
         std::vector<int> v;
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
             if (!H.leaf(b) && H.has_src(b)) v.push_back(b);
-        make_task(P.t_m2m[l], {v}, 8, ops8, nr, up, bm);
+        make_task(P.t_m2m[l], {v}, 8, ops8, nr, up, bm, [&](int b, int sl) { return H.child[8 * (size_t)b + sl]; });
     }
     // M2L: boxes of level >= 1 with targets, by octant class
     std::vector<std::vector<int>> byc(8);
@@ -484,16 +514,16 @@ void build_tasks(Plan &P, cudaStream_t s) {
     std::vector<int> dc;
     for (int b = (mixed ? P.nprob : 0); b < nb; b++)
         if (H.has_trg(b)) dc.push_back(b);
-    make_task(P.t_dc2e, {dc}, 1, {0}, nr, up, bm);
+    make_task(P.t_dc2e, {dc}, 1, {0}, nr, up, bm, self);
     // MIXED with a shared M2L basis: the X-list part of the check potential is solved separately
-    if (P.basis) make_task(P.t_dcx, {xb}, 1, {0}, nr, up, bm);
+    if (P.basis) make_task(P.t_dcx, {xb}, 1, {0}, nr, up, bm, self);
     // L2L per level >= 1, by octant class
     P.t_l2l.resize(depth);
     for (int l = 1; l < depth; l++) {
         std::vector<std::vector<int>> bc(8);
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
             if (H.has_trg(b)) bc[H.octant(b)].push_back(b);
-        make_task(P.t_l2l[l], bc, 1, ops8, nr, up, bm);
+        make_task(P.t_l2l[l], bc, 1, ops8, nr, up, bm, [&](int b, int) { return H.parent[b]; });
     }
     up.flush(P, s);
 }

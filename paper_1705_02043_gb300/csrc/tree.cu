@@ -614,11 +614,11 @@ void build_lists(Plan &P, cudaStream_t s) {
     t.u_ptr.reserve(nb + 1);
     t.w_ptr.reserve(nb + 1);
     t.x_ptr.reserve(nb + 1);
-    DBuf<int> cnt3;
+    DBuf<int> &cnt3 = P.lcnt;
     cnt3.reserve((size_t)3 * nb);
     t.v_slot.reserve((size_t)nb * kVSlots);
     PK_CUDA(cudaMemsetAsync(t.v_slot.p, 0xff, sizeof(int) * (size_t)nb * kVSlots, s));
-    DBuf<unsigned long long> pairs;
+    DBuf<unsigned long long> &pairs = P.lpairs;
     pairs.reserve(2);
     PK_CUDA(cudaMemsetAsync(pairs.p, 0, sizeof(unsigned long long) * 2, s));
     ListOut o{};
@@ -627,9 +627,20 @@ void build_lists(Plan &P, cudaStream_t s) {
     o.x_cnt = cnt3.p + 2 * nb;
     o.slot_of = P.slot_of.p;
     count_launch(), k_lists<<<blocks(nb, 128), 128, 0, s>>>(tv, nb, 0, o);
-    t.nU = exclusive_scan(o.u_cnt, t.u_ptr.p, nb, s);
-    t.nW = exclusive_scan(o.w_cnt, t.w_ptr.p, nb, s);
-    t.nX = exclusive_scan(o.x_cnt, t.x_ptr.p, nb, s);
+    // the three scans, then one read of their totals
+    exclusive_scan(o.u_cnt, t.u_ptr.p, nb, s, false);
+    exclusive_scan(o.w_cnt, t.w_ptr.p, nb, s, false);
+    exclusive_scan(o.x_cnt, t.x_ptr.p, nb, s, false);
+    {
+        int tot[3] = {0, 0, 0};
+        PK_CUDA(cudaMemcpyAsync(&tot[0], t.u_ptr.p + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PK_CUDA(cudaMemcpyAsync(&tot[1], t.w_ptr.p + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PK_CUDA(cudaMemcpyAsync(&tot[2], t.x_ptr.p + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PK_CUDA(cudaStreamSynchronize(s));
+        t.nU = tot[0];
+        t.nW = tot[1];
+        t.nX = tot[2];
+    }
     t.u_box.reserve(t.nU + 1);
     t.u_sh.reserve(t.nU + 1);
     t.w_box.reserve(t.nW + 1);
@@ -655,8 +666,6 @@ void build_lists(Plan &P, cudaStream_t s) {
     PK_CUDA(cudaStreamSynchronize(s));
     t.p2p_pairs = (long long)h[0];
     t.nV = (long long)h[1];
-    cnt3.release();
-    pairs.release();
 }
 
 // ---------------- entry: keys, sort, gather ----------------
@@ -677,7 +686,7 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
     P.idxT.reserve(T + 1);
     P.xs.reserve(3 * S + 3);
     P.xt.reserve(3 * T + 3);
-    DBuf<double> xn;
+    DBuf<double> &xn = P.xn;
     xn.reserve(3 * std::max(S, T) + 3);
     if (S) {
         count_launch(), k_keys<<<blocks(S, 256), 256, 0, s>>>(src, S, P.lo[0], P.lo[1], P.lo[2], P.L, wrap, D, xn.p,
@@ -701,8 +710,6 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
         radix_sort(P.keyT, P.idxT, P.keyT2, P.idxT2, P.hist, (int)T, key_bits, s);
         count_launch(), k_gather3<<<blocks(T, 256), 256, 0, s>>>(xn.p, P.idxT.p, T, P.xt.p);
     }
-    PK_CUDA(cudaStreamSynchronize(s));
-    xn.release();
 }
 
 // ---------------- Morton order without allocation ----------------

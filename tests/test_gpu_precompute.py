@@ -2,13 +2,14 @@
 against the host build.
 
 The singular values (5e-13 s_max) and the root far-field table (1e-12) are
-well conditioned and agree to rounding.  The M2M / L2L operators contain the pseudo-inverse of the
-surface matrix, cut at 2^-52 kn s_max for binary64, so their entries along
-the near-null directions depend on the SVD's rounding (two correct SVDs give
-operators 1e-7..1e-4 apart as p grows); what is unique is the field they produce on the
-check surface, A M2M and A L2L, compared at 1e-9 (the host build itself
-reproduces the child fields to 1e-13 at p = 6 and 3e-10 at Stokes p = 8).  End to end, plans built
-either way give the same potentials (binary64) and both meet the oracle."""
+well conditioned and agree to rounding.  The M2M / L2L operators contain the
+pseudo-inverse of the surface matrix, cut at eps_SVD s_max (binary64:
+10^-p for Stokes, 10^-(p+2) for Laplace, never below 2^-52 kn), so their
+entries along the near-null directions depend on the SVD's rounding; what is
+unique is the field they produce on the check surface, A M2M and A L2L,
+compared at 1e-9.  A random density's field is reproduced to the order of the
+cut-off.  End to end, plans built either way give the same potentials
+(binary64) and both meet the oracle."""
 
 import numpy as np
 import pytest
@@ -70,8 +71,12 @@ def test_device_operators_reproduce_child_fields():
     # the M2M parent density reproduces, on the parent's upward check surface,
     # the field of the child's equivalent density, and the L2L child density
     # the parent's downward field on the child's check surface (Sec. 2.2): an
-    # identity that does not go through the host build at all
+    # identity that does not go through the host build at all.  It holds to the
+    # SVD cut-off: singular values below eps_SVD s_max (1e-6 for Stokes at p = 6)
+    # are not inverted, so the fit of a random density leaves a residual of that
+    # order (a wrong octant or scale would leave one of order 1)
     kernel, p = 1, 6
+    tol = 2e-5
     _, md, ld, _, _, _ = b.pkifmm_precompute_operators(kernel, 7, p, 2, pk.FP64, 1)
     g = _grid(p)
     rng = np.random.default_rng(3)
@@ -82,11 +87,11 @@ def test_device_operators_reproduce_child_fields():
         # times 2 for q~ = edge x q), and of the parent density in the unit frame
         child = 2.0 * _kmat(kernel, 2 * 1.475 * g, sg + 0.525 * g) @ phi
         parent = _kmat(kernel, 1.475 * g, 0.525 * g) @ (md[c] @ phi)
-        assert np.linalg.norm(parent - child) <= 1e-9 * np.linalg.norm(child)
+        assert np.linalg.norm(parent - child) <= tol * np.linalg.norm(child)
         psi = rng.standard_normal(len(g) * 3)
         pf = _kmat(kernel, 0.525 * g, -sg + 2 * 1.475 * g) @ psi  # parent down-equiv on the child check
         cf = _kmat(kernel, 0.525 * g, 1.475 * g) @ (ld[c] @ psi)
-        assert np.linalg.norm(cf - pf) <= 1e-9 * np.linalg.norm(pf)
+        assert np.linalg.norm(cf - pf) <= tol * np.linalg.norm(pf)
 
 
 @pytest.mark.parametrize("kernel,periodic,precision,tol", [(0, 7, 0, 1e-6), (1, 7, 0, 2e-5), (1, 3, 1, 1e-4),
