@@ -404,6 +404,7 @@ static void destroy_plan(pkifmm_plan_s *plan) {
     P.csr.release();
     P.xn.release();
     P.lcnt.release();
+    P.scan_tmp.release();
     P.lpairs.release();
     P.ctr.release();
     P.soff.release();

@@ -157,6 +157,8 @@ struct Plan {
     DBuf<int> cnt, off;
     DBuf<double> xn;                            // normalised coordinates before the gather
     DBuf<int> lcnt;                             // [3][nbox] U / W / X list lengths
+    DBuf<int> scan_tmp;                         // prefix-sum scratch
+    bool same_points = false;                   // the targets are the sources (one sort)
     DBuf<unsigned long long> lpairs;            // [2] P2P pairs, V entries
     DBuf<int2> csr, ctr;                        // [nlevel boxes][8] child ranges
     DBuf<int> gather_idx;

@@ -174,6 +174,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nact = *nact_s;
     const uint32_t tmem = *tmem_slot;
     const int total = nact * kchunks;
+    // slots summed into one work accumulator before it is drained: about 14 K
+    // chunks (the truncation of the tensor core's fp32 accumulation grows with
+    // the steps summed in tensor memory)
+    const int spd = max(1, 14 / kchunks), nunits = (nact + spd - 1) / spd;
 
     if (warp < 4 && a.grid) {
         // ---- producer (grid mode): one thread, TMA for both operands ----
@@ -310,16 +314,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == 4) {
-        // ---- MMA issuer: one slot per work accumulator ----
+        // ---- MMA issuer: spd slots per work accumulator (one drain unit) ----
         if (lane == 0) {
             int it = 0;
             bool okm = true;
-            for (int si = 0; si < nact && okm; si++) {
-                const int wb = si & 1;
-                if (!mbar_wait(&wfree[wb], ((uint32_t)(si >> 1) & 1u) ^ 1u, a.err)) break;
+            for (int u = 0; u < nunits && okm; u++) {
+                const int wb = u & 1;
+                if (!mbar_wait(&wfree[wb], ((uint32_t)(u >> 1) & 1u) ^ 1u, a.err)) break;
                 tc_fence_after();
                 // buffer wb: columns [256 wb, 256 wb + 128) hold hi*hi, the next 128 the cross terms
                 const uint32_t dbig = tmem + wb * 2 * TC_N, dsmall = dbig + TC_N;
+                const int si0 = u * spd, si1 = min(nact, si0 + spd);
+                for (int si = si0; si < si1 && okm; si++)
                 for (int kc = 0; kc < kchunks; kc++, it++) {
                     const int st = it % STAGES;
                     if (!mbar_wait(&full[st], (uint32_t)(it / STAGES) & 1u, a.err)) {
@@ -336,12 +342,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const uint64_t a_lo = smem_desc_sw128(sb + TC_A_BYTES + k16 * 32);
                         const uint64_t b_hl = smem_desc_sw128(sb + 2 * TC_A_BYTES + k16 * 32);  // B_hi then B_lo
                         // A_hi [B_hi | B_lo] -> [hi*hi | hi*lo] in one N = 256 MMA, then lo*hi onto the cross terms
-                        tc_mma(dbig, a_hi, b_hl, (kc | k16) ? 1u : 0u, kIdesc2);
+                        tc_mma(dbig, a_hi, b_hl, (si != si0 || kc | k16) ? 1u : 0u, kIdesc2);
                         tc_mma(dsmall, a_lo, b_hl, 1u);
                     }
                     tc_commit(&empty[st]);
                 }
-                tc_commit(&wfull[wb]);
+                if (okm) tc_commit(&wfull[wb]);
             }
         }
         __syncwarp();
@@ -352,9 +358,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int c = 0; c < TC_N; c++) acc[c] = 0.f;
         bool oke = true;
-        for (int si = 0; si < nact && oke; si++) {
-            const int wb = si & 1;
-            bool w = mbar_wait(&wfull[wb], (uint32_t)(si >> 1) & 1u, a.err);
+        for (int u = 0; u < nunits && oke; u++) {
+            const int wb = u & 1;
+            bool w = mbar_wait(&wfull[wb], (uint32_t)(u >> 1) & 1u, a.err);
             oke = __all_sync(0xffffffffu, w);  // tcgen05.ld is warp-collective
             if (!oke) break;
             tc_fence_after();
@@ -476,6 +482,7 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
     const int nact = *nact_s;
     const uint32_t tmem = *tmem_slot;
     const int total = nact * kchunks;
+    const int spd = max(1, 14 / kchunks), nunits = (nact + spd - 1) / spd;  // slots per drain, as above
 
     if (warp == 0) {
         // ---- producer: TMA of the K_o tiles and of both column tiles' sources ----
@@ -518,9 +525,11 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
             int it = 0;
             bool okm = true;
             const uint32_t dhh = tmem, dx = tmem + 2 * TC_N;  // columns [0, 256) hi*hi, [256, 512) cross
-            for (int si = 0; si < nact && okm; si++) {
-                if (!mbar_wait(wfree, ((uint32_t)si & 1u) ^ 1u, a.err)) break;
+            for (int u = 0; u < nunits && okm; u++) {
+                if (!mbar_wait(wfree, ((uint32_t)u & 1u) ^ 1u, a.err)) break;
                 tc_fence_after();
+                const int si0 = u * spd, si1 = min(nact, si0 + spd);
+                for (int si = si0; si < si1 && okm; si++)
                 for (int kc = 0; kc < kchunks; kc++, it++) {
                     const int st = it % STAGES;
                     if (!mbar_wait(&full[st], (uint32_t)(it / STAGES) & 1u, a.err)) {
@@ -535,14 +544,14 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
                         const uint64_t a_lo = smem_desc_sw128(sb + TC_A_BYTES + k16 * 32);
                         const uint64_t b_hi = smem_desc_sw128(sb + 2 * TC_A_BYTES + k16 * 32);  // B_hi0 | B_hi1
                         const uint64_t b_lo = smem_desc_sw128(sb + 2 * TC_A_BYTES + 2 * TC_B_BYTES + k16 * 32);
-                        const uint32_t first = (kc | k16) ? 1u : 0u;
+                        const uint32_t first = (si != si0 || kc | k16) ? 1u : 0u;
                         tc_mma(dhh, a_hi, b_hi, first, kIdesc2);
                         tc_mma(dx, a_hi, b_lo, first, kIdesc2);
                         tc_mma(dx, a_lo, b_hi, 1u, kIdesc2);
                     }
                     tc_commit(&empty[st]);
                 }
-                tc_commit(wfull);
+                if (okm) tc_commit(wfull);
             }
         }
         __syncwarp();
@@ -553,8 +562,8 @@ __global__ void __launch_bounds__(TCW_THREADS, 1)
 #pragma unroll
         for (int c = 0; c < TC_N; c++) acc[c] = 0.f;
         bool oke = true;
-        for (int si = 0; si < nact && oke; si++) {
-            bool w = mbar_wait(wfull, (uint32_t)si & 1u, a.err);
+        for (int u = 0; u < nunits && oke; u++) {
+            bool w = mbar_wait(wfull, (uint32_t)u & 1u, a.err);
             oke = __all_sync(0xffffffffu, w);
             if (!oke) break;
             tc_fence_after();

@@ -22,8 +22,9 @@
 // clustered case: 1.1e-6 draining every chunk, 1.9e-6 every two, 8.2e-7 for the
 // binary32 SIMT product).
 //
-// Pipeline as in the M2L kernel: warps 0-3 gather the source rows (fp16,
-// split beforehand) with cp.async into the 128B-swizzled K-major layout and
+// Pipeline as in the M2L kernel: warps 0-3 load the source rows (fp16, split
+// beforehand) into the 128B-swizzled K-major layout, by one TMA per split when
+// the tile's source boxes are regular and by cp.async gathers otherwise, and
 // one thread issues the TMA loads of the operator tiles; warp 4 issues the
 // MMAs; warps 5-8 drain.  Every mbarrier wait is bounded in time; on timeout
 // the kernel raises the error flag and returns.
@@ -74,7 +75,7 @@ namespace {
 struct TrArgs {
     const __half *phi_hi, *phi_lo;  // split source rows [rows][KK]
     const int *tboxes;              // task boxes, class-major
-    const int4 *tiles;              // (class, row0, nrows, 0)
+    const int4 *tiles;              // (class, row0, nrows, source-row mode: 0 gather, 1 or 8 regular)
     const int *slot_table;          // [box][slot_stride] source box per slot; null: the box itself
     int slot_stride, nslots;
     const int *class_ops;           // [nclass][nslots] operator of (class, slot), -1 none

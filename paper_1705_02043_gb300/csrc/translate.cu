@@ -19,7 +19,6 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
-#include <functional>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -384,35 +383,39 @@ struct Uploads {
 // whose source boxes are src0 + i (or src0 + 8 i, the children of consecutive
 // parents of a full level) for every slot of its class is marked in .w (1 or 8):
 // the tensor-core translations then load its source rows by TMA.
+template <typename Src = std::nullptr_t>
 static void make_task(Task &t, const std::vector<std::vector<int>> &by_class, int nslots,
-                      const std::vector<int> &class_ops, int nrhs, Uploads &up, int bm = GB_M,
-                      const std::function<int(int, int)> &src = nullptr) {
+                      const std::vector<int> &class_ops, int nrhs, Uploads &up, int bm = GB_M, Src src = nullptr) {
     t.nclass = (int)by_class.size();
     t.nslots = nslots;
     t.h_boxes.clear();
     t.class_count.clear();
     for (auto &v : by_class) t.class_count.push_back((int)v.size());
     std::vector<int4> tiles;
-    auto regular = [&](const std::vector<int> &bx, int c, int i0, int n) {
-        if (!src || nrhs != 1) return 0;
-        int stride = 0;
-        for (int s = 0; s < nslots; s++) {
-            if (class_ops[c * nslots + s] < 0) continue;
-            const int a0 = src(bx[i0], s);
-            if (a0 < 0) return 0;
-            int st = 0;
-            if (n > 1) {
-                st = src(bx[i0 + 1], s) - a0;
-                if (st != 1 && st != 8) return 0;
+    auto regular = [&](const std::vector<int> &bx, int c, int i0, int n) -> int {
+        if constexpr (std::is_same_v<Src, std::nullptr_t>) {
+            return 0;
+        } else {
+            if (nrhs != 1) return 0;
+            int stride = 0;
+            for (int s = 0; s < nslots; s++) {
+                if (class_ops[c * nslots + s] < 0) continue;
+                const int a0 = src(bx[i0], s);
+                if (a0 < 0) return 0;
+                int st = 0;
+                if (n > 1) {
+                    st = src(bx[i0 + 1], s) - a0;
+                    if (st != 1 && st != 8) return 0;
+                }
+                for (int i = 2; i < n; i++)
+                    if (src(bx[i0 + i], s) != a0 + st * i) return 0;
+                if (n > 1) {
+                    if (stride && st != stride) return 0;
+                    stride = st;
+                }
             }
-            for (int i = 2; i < n; i++)
-                if (src(bx[i0 + i], s) != a0 + st * i) return 0;
-            if (n > 1) {
-                if (stride && st != stride) return 0;
-                stride = st;
-            }
+            return stride ? stride : 1;
         }
-        return stride ? stride : 1;
     };
     for (int c = 0; c < t.nclass; c++) {
         int row0 = (int)t.h_boxes.size() * nrhs;
@@ -470,10 +473,14 @@ void build_tasks(Plan &P, cudaStream_t s) {
     const int *xptr = (const int *)(dh + b_x);
     Uploads up;
     const int nr = P.nrhs;
+    std::vector<char> isleaf(nb);
+    for (int b = 0; b < nb; b++) isleaf[b] = H.leaf(b);
     std::vector<int> leaves_src, leaves_trg;
+    leaves_src.reserve(nb);
+    leaves_trg.reserve(nb);
     t.nleaf = 0;
     for (int b = 0; b < nb; b++) {
-        if (!H.leaf(b)) continue;
+        if (!isleaf[b]) continue;
         t.nleaf++;
         if (H.has_src(b)) leaves_src.push_back(b);
         if (H.has_trg(b)) leaves_trg.push_back(b);
@@ -502,7 +509,7 @@ void build_tasks(Plan &P, cudaStream_t s) {
     for (int l = 0; l < depth; l++) {
         std::vector<int> v;
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
-            if (!H.leaf(b) && H.has_src(b)) v.push_back(b);
+            if (!isleaf[b] && H.has_src(b)) v.push_back(b);
         make_task(P.t_m2m[l], {v}, 8, ops8, nr, up, bm, [&](int b, int sl) { return H.child[8 * (size_t)b + sl]; });
     }
     // M2L: boxes of level >= 1 with targets, by octant class

@@ -82,23 +82,39 @@ __global__ void k_scan_fix_total(int *out, const int *in, int n) {
 
 // Exclusive scan of in[0..n) into out[0..n], out[n] = total.  Returns the
 // total (synchronises the stream) when `want_total`, else 0 without waiting.
-int exclusive_scan(const int *in, int *out, int n, cudaStream_t s, bool want_total = true) {
+// Scratch the scan needs for n values: block sums and their offsets at every
+// level of the recursion.
+static size_t scan_scratch(long long n) {
+    size_t t = 2;
+    while (n > 1024) {
+        const long long nb = (n + 1023) / 1024;
+        t += 2 * (size_t)(nb + 1);
+        n = nb;
+    }
+    return t;
+}
+
+static void scan_into(const int *in, int *out, int n, cudaStream_t s, int *tmp) {
     if (n <= 0) {
         PK_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
-        return 0;
+        return;
     }
-    int nb = (n + 1023) / 1024;
-    int *bsum = nullptr, *boff = nullptr;
-    PK_CUDA(cudaMallocAsync(&bsum, sizeof(int) * (nb + 1), s));
-    PK_CUDA(cudaMallocAsync(&boff, sizeof(int) * (nb + 1), s));
+    const int nb = (n + 1023) / 1024;
+    int *bsum = tmp, *boff = tmp + nb + 1;
     count_launch(), k_scan_block<<<nb, 1024, 0, s>>>(in, out, bsum, n);
     if (nb > 1) {
-        exclusive_scan(bsum, boff, nb, s, false);
+        scan_into(bsum, boff, nb, s, tmp + 2 * (nb + 1));
         count_launch(), k_scan_add<<<nb, 1024, 0, s>>>(out, boff, n, nullptr);
     }
     count_launch(), k_scan_fix_total<<<1, 1, 0, s>>>(out, in, n);
-    PK_CUDA(cudaFreeAsync(bsum, s));
-    PK_CUDA(cudaFreeAsync(boff, s));
+}
+
+// out[0..n] = exclusive prefix sums of in[0..n-1], out[n] the total (also
+// returned, after a stream synchronisation, when want_total); tmp: scratch owned
+// by the caller, grown as needed.
+int exclusive_scan(const int *in, int *out, int n, cudaStream_t s, DBuf<int> &tmp, bool want_total = false) {
+    tmp.reserve(scan_scratch(n));
+    scan_into(in, out, n, s, tmp.p);
     if (!want_total) return 0;
     int total = 0;
     PK_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -209,7 +225,7 @@ __global__ void k_rs_scatter(const unsigned long long *__restrict__ kin, const i
 
 // Sort (key, idx) by key (bits [0, bits)), stable.  Result in (k, v).
 static void radix_sort(DBuf<unsigned long long> &k, DBuf<int> &v, DBuf<unsigned long long> &k2, DBuf<int> &v2,
-                       DBuf<int> &hist, int n, int bits, cudaStream_t s) {
+                       DBuf<int> &hist, DBuf<int> &scan_tmp, int n, int bits, cudaStream_t s) {
     if (n <= 1) return;
     int nb = (n + RS_TILE - 1) / RS_TILE;
     hist.reserve((size_t)16 * nb * 2 + 2);
@@ -220,7 +236,7 @@ static void radix_sort(DBuf<unsigned long long> &k, DBuf<int> &v, DBuf<unsigned 
     int *h = hist.p, *ho = hist.p + 16 * nb + 1;
     for (int sh = 0; sh < bits; sh += 4) {
         count_launch(), k_rs_count<<<nb, RS_T, 0, s>>>(ka, n, sh, h, nb);
-        exclusive_scan(h, ho, 16 * nb, s, false);  // the radix sort needs no total
+        exclusive_scan(h, ho, 16 * nb, s, scan_tmp);  // the radix sort needs no total
         count_launch(), k_rs_scatter<<<nb, RS_T, 0, s>>>(ka, va, kb, vb, n, sh, ho, nb);
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -265,8 +281,12 @@ __device__ inline int lower_bound_key(const unsigned long long *key, int lo, int
 // one root per problem; its points are the problem's CSR range (the sort
 // keeps problems contiguous and in order)
 __global__ void k_roots(int nprob, const long long *__restrict__ soff, const long long *__restrict__ toff,
-                        unsigned long long *key, int4 *bpos, int *parent, int2 *sr, int2 *tr) {
+                        unsigned long long *key, int4 *bpos, int *parent, int2 *sr, int2 *tr, int *lvl) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0) {  // level 0 holds the roots, boxes 0 .. nprob - 1
+        lvl[0] = 0;
+        lvl[1] = nprob;
+    }
     if (j >= nprob) return;
     key[j] = (unsigned long long)j;
     bpos[j] = make_int4(0, 0, 0, 0);
@@ -278,50 +298,64 @@ __global__ void k_roots(int nprob, const long long *__restrict__ soff, const lon
 // One warp per box: lanes 0-7 find where child c's sources start, lanes
 // 8-15 where its targets start (all 16 binary searches at once); child c ends
 // where child c + 1 starts, the last child at the box's end.
-__global__ void k_split(int lb, int le, int level, int D, int smax, const unsigned long long *__restrict__ bkey,
-                        const int2 *__restrict__ srange, const int2 *__restrict__ trange,
-                        const unsigned long long *__restrict__ keyS, const unsigned long long *__restrict__ keyT,
-                        int2 *csr, int2 *ctr, int *cnt) {
-    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int b = lb + (int)(gt >> 5), lane = threadIdx.x & 31;
-    if (b >= le) return;  // the whole warp shares b
-    const int2 sr = srange[b], tr = trange[b];
-    const bool split = (sr.y - sr.x > smax || tr.y - tr.x > smax) && level < D;
-    const int c = lane & 7;
-    int start = 0;
-    if (split && lane < 16) {
-        const unsigned long long lo = (bkey[b] * 8 + c) << (3 * (D - level - 1));
-        start = lane < 8 ? lower_bound_key(keyS, sr.x, sr.y, lo) : lower_bound_key(keyT, tr.x, tr.y, lo);
+// Level `level` holds boxes lvl[level] .. lvl[level + 1] - 1; at most `bound`
+// of them.  One warp per box, striding over the bound; cnt[w] = 0 for the
+// positions past the level.
+__global__ void k_split(const int *__restrict__ lvl, int level, int bound, int D, int smax,
+                        const unsigned long long *__restrict__ bkey, const int2 *__restrict__ srange,
+                        const int2 *__restrict__ trange, const unsigned long long *__restrict__ keyS,
+                        const unsigned long long *__restrict__ keyT, int2 *csr, int2 *ctr, int *cnt) {
+    const int lb = lvl[level], le = lvl[level + 1], lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * blockDim.x >> 5;
+    for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < bound; w += nw) {
+        const int b = lb + (int)w;
+        if (b >= le) {  // the whole warp shares b
+            if (lane == 0) cnt[w] = 0;
+            continue;
+        }
+        const int2 sr = srange[b], tr = trange[b];
+        const bool split = (sr.y - sr.x > smax || tr.y - tr.x > smax) && level < D;
+        const int c = lane & 7;
+        int start = 0;
+        if (split && lane < 16) {
+            const unsigned long long lo = (bkey[b] * 8 + c) << (3 * (D - level - 1));
+            start = lane < 8 ? lower_bound_key(keyS, sr.x, sr.y, lo) : lower_bound_key(keyT, tr.x, tr.y, lo);
+        }
+        const int nxt = __shfl_down_sync(0xffffffffu, start, 1);
+        const int end = c == 7 ? (lane < 8 ? sr.y : tr.y) : nxt;
+        if (split && lane < 8) csr[w * 8 + c] = make_int2(start, end);
+        if (split && lane >= 8 && lane < 16) ctr[w * 8 + c] = make_int2(start, end);
+        const int nonempty = lane < 16 && end > start;
+        const int t_nonempty = __shfl_down_sync(0xffffffffu, nonempty, 8);  // lane c: child c's targets
+        const unsigned m = __ballot_sync(0xffffffffu, split && lane < 8 && (nonempty || t_nonempty));
+        if (lane == 0) cnt[w] = __popc(m);
     }
-    const int nxt = __shfl_down_sync(0xffffffffu, start, 1);
-    const int end = c == 7 ? (lane < 8 ? sr.y : tr.y) : nxt;
-    if (split && lane < 8) csr[(b - lb) * 8 + c] = make_int2(start, end);
-    if (split && lane >= 8 && lane < 16) ctr[(b - lb) * 8 + c] = make_int2(start, end);
-    const int nonempty = lane < 16 && end > start;
-    const int t_nonempty = __shfl_down_sync(0xffffffffu, nonempty, 8);  // lane c: child c's targets
-    const unsigned m = __ballot_sync(0xffffffffu, split && lane < 8 && (nonempty || t_nonempty));
-    if (lane == 0) cnt[b - lb] = __popc(m);
 }
-
-__global__ void k_emit(int lb, int le, const int *__restrict__ cnt, const int *__restrict__ off,
+// The children of level `level`'s boxes become level level + 1, from
+// lvl[level + 1] on, in order; lvl[level + 2] = the end of that level.
+__global__ void k_emit(int *lvl, int level, int bound, const int *__restrict__ cnt, const int *__restrict__ off,
                        const int2 *__restrict__ csr, const int2 *__restrict__ ctr, unsigned long long *bkey,
                        int4 *bpos, int *parent, int *child, int2 *srange, int2 *trange) {
-    int b = lb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= le) return;
-    for (int c = 0; c < 8; c++) child[(long long)b * 8 + c] = -1;
-    if (cnt[b - lb] == 0) return;
-    int j = le + off[b - lb];
-    int4 p = bpos[b];
-    for (int c = 0; c < 8; c++) {
-        int2 s = csr[(b - lb) * 8 + c], t = ctr[(b - lb) * 8 + c];
-        if (s.y <= s.x && t.y <= t.x) continue;
-        bkey[j] = bkey[b] * 8 + c;
-        bpos[j] = make_int4(2 * p.x + (c & 1), 2 * p.y + (c >> 1 & 1), 2 * p.z + (c >> 2 & 1), p.w + 1);
-        parent[j] = b;
-        srange[j] = s;
-        trange[j] = t;
-        child[(long long)b * 8 + c] = j;
-        j++;
+    const int lb = lvl[level], le = lvl[level + 1], nl = min(le - lb, bound);
+    if (blockIdx.x == 0 && threadIdx.x == 0) lvl[level + 2] = le + off[bound];
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < nl;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int b = lb + (int)w;
+        for (int c = 0; c < 8; c++) child[(long long)b * 8 + c] = -1;
+        if (cnt[w] == 0) continue;
+        int j = le + off[w];
+        int4 p = bpos[b];
+        for (int c = 0; c < 8; c++) {
+            int2 s = csr[w * 8 + c], t = ctr[w * 8 + c];
+            if (s.y <= s.x && t.y <= t.x) continue;
+            bkey[j] = bkey[b] * 8 + c;
+            bpos[j] = make_int4(2 * p.x + (c & 1), 2 * p.y + (c >> 1 & 1), 2 * p.z + (c >> 2 & 1), p.w + 1);
+            parent[j] = b;
+            srange[j] = s;
+            trange[j] = t;
+            child[(long long)b * 8 + c] = j;
+            j++;
+        }
     }
 }
 
@@ -329,44 +363,57 @@ void build_tree(Plan &P, cudaStream_t s) {
     Tree &t = P.tree;
     const int D = P.depth_max;
     const int np = P.nprob;
-    size_t cap = std::max<size_t>(1024, (size_t)np);
-    t.key.grow_keep(cap, 0, s);
-    t.bpos.grow_keep(cap, 0, s);
-    t.parent.grow_keep(cap, 0, s);
-    t.child.grow_keep(cap * 8, 0, s);
-    t.srange.grow_keep(cap, 0, s);
-    t.trange.grow_keep(cap, 0, s);
+    // Boxes per level, bounded in advance so the levels are built without a
+    // round trip to the host: level 0 holds the roots; a box splits only while
+    // it holds more than s sources or more than s targets, so at most
+    // S/(s+1) + T/(s+1) boxes of a level split (S/(s+1) when the targets are
+    // the sources), into at most 8 children each.
+    const long long s1 = P.leaf_max + 1;
+    const long long split_max = P.S / s1 + (P.same_points ? 0 : P.T / s1) + np;
+    std::vector<long long> ub(D + 1);
+    ub[0] = np;
+    long long tot = np, ubmax = np;
+    for (int l = 1; l <= D; l++) {
+        ub[l] = std::min(8 * ub[l - 1], 8 * split_max);
+        tot += ub[l];
+        ubmax = std::max(ubmax, ub[l]);
+    }
+    if (tot > (1LL << 31) / 9) throw Error(PKIFMM_ERR_INVALID_ARG, "octree too large for 32-bit box indices");
+    t.key.reserve(tot);
+    t.bpos.reserve(tot);
+    t.parent.reserve(tot);
+    t.child.reserve(tot * 8);
+    t.srange.reserve(tot);
+    t.trange.reserve(tot);
+    t.lvl_begin_d.reserve(D + 3);
+    P.csr.reserve((size_t)ubmax * 8);
+    P.ctr.reserve((size_t)ubmax * 8);
+    P.cnt.reserve(ubmax + 1);
+    P.off.reserve(ubmax + 1);
+    int *lvl = t.lvl_begin_d.p;
     count_launch(), k_roots<<<blocks(np, 128), 128, 0, s>>>(np, P.soff.p, P.toff.p, t.key.p, t.bpos.p, t.parent.p,
-                                                             t.srange.p, t.trange.p);
-    t.lvl_begin.assign({0, np});
+                                                             t.srange.p, t.trange.p, lvl);
+    const unsigned gmax = 152u * 16u;  // grid-stride kernels: about 16 blocks per SM at most
+    for (int l = 0; l <= D; l++) {  // level D boxes get no children (the split test checks the level)
+        const int b = (int)ub[l];
+        count_launch(), k_split<<<std::min<unsigned>(gmax, blocks((long long)b * 32, 128)), 128, 0, s>>>(
+            lvl, l, b, D, P.leaf_max, t.key.p, t.srange.p, t.trange.p, P.keyS.p, P.keyT.p, P.csr.p, P.ctr.p, P.cnt.p);
+        exclusive_scan(P.cnt.p, P.off.p, b, s, P.scan_tmp);
+        count_launch(), k_emit<<<std::min<unsigned>(gmax, blocks(b, 128)), 128, 0, s>>>(
+            lvl, l, b, P.cnt.p, P.off.p, P.csr.p, P.ctr.p, t.key.p, t.bpos.p, t.parent.p, t.child.p, t.srange.p,
+            t.trange.p);
+    }
+    std::vector<int> h(D + 3);
+    PK_CUDA(cudaMemcpyAsync(h.data(), lvl, sizeof(int) * (D + 3), cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaStreamSynchronize(s));
+    t.lvl_begin.assign({h[0], h[1]});
     int level = 0;
-    for (;; level++) {
-        int lb = t.lvl_begin[level], le = t.lvl_begin[level + 1], nl = le - lb;
-        P.csr.reserve((size_t)nl * 8);
-        P.ctr.reserve((size_t)nl * 8);
-        P.cnt.reserve(nl + 1);
-        P.off.reserve(nl + 1);
-        count_launch(), k_split<<<blocks((long long)nl * 32, 128), 128, 0, s>>>(
-            lb, le, level, D, P.leaf_max, t.key.p, t.srange.p, t.trange.p, P.keyS.p, P.keyT.p, P.csr.p, P.ctr.p,
-            P.cnt.p);
-        int total = exclusive_scan(P.cnt.p, P.off.p, nl, s);
-        size_t need = (size_t)le + total;
-        t.key.grow_keep(need, le, s);
-        t.bpos.grow_keep(need, le, s);
-        t.parent.grow_keep(need, le, s);
-        t.child.grow_keep(need * 8, (size_t)le * 8, s);
-        t.srange.grow_keep(need, le, s);
-        t.trange.grow_keep(need, le, s);
-        count_launch(), k_emit<<<blocks(nl, 128), 128, 0, s>>>(lb, le, P.cnt.p, P.off.p, P.csr.p, P.ctr.p, t.key.p, t.bpos.p,
-                                                t.parent.p, t.child.p, t.srange.p, t.trange.p);
-        if (total == 0) break;
-        t.lvl_begin.push_back(le + total);
+    while (level + 2 <= D + 2 && h[level + 2] > h[level + 1]) {
+        t.lvl_begin.push_back(h[level + 2]);
+        level++;
     }
     t.depth = level;
     t.nbox = t.lvl_begin.back();
-    t.lvl_begin_d.reserve(t.lvl_begin.size());
-    PK_CUDA(cudaMemcpyAsync(t.lvl_begin_d.p, t.lvl_begin.data(), sizeof(int) * t.lvl_begin.size(),
-                            cudaMemcpyHostToDevice, s));
 }
 
 // ---------------- lists ----------------
@@ -628,9 +675,9 @@ void build_lists(Plan &P, cudaStream_t s) {
     o.slot_of = P.slot_of.p;
     count_launch(), k_lists<<<blocks(nb, 128), 128, 0, s>>>(tv, nb, 0, o);
     // the three scans, then one read of their totals
-    exclusive_scan(o.u_cnt, t.u_ptr.p, nb, s, false);
-    exclusive_scan(o.w_cnt, t.w_ptr.p, nb, s, false);
-    exclusive_scan(o.x_cnt, t.x_ptr.p, nb, s, false);
+    exclusive_scan(o.u_cnt, t.u_ptr.p, nb, s, P.scan_tmp);
+    exclusive_scan(o.w_cnt, t.w_ptr.p, nb, s, P.scan_tmp);
+    exclusive_scan(o.x_cnt, t.x_ptr.p, nb, s, P.scan_tmp);
     {
         int tot[3] = {0, 0, 0};
         PK_CUDA(cudaMemcpyAsync(&tot[0], t.u_ptr.p + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -692,13 +739,14 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
         count_launch(), k_keys<<<blocks(S, 256), 256, 0, s>>>(src, S, P.lo[0], P.lo[1], P.lo[2], P.L, wrap, D, xn.p,
                                               P.keyS.p, P.idxS.p, P.err.p, P.nprob > 1 ? P.soff.p : nullptr,
                                               P.nprob);
-        radix_sort(P.keyS, P.idxS, P.keyS2, P.idxS2, P.hist, (int)S, key_bits, s);
+        radix_sort(P.keyS, P.idxS, P.keyS2, P.idxS2, P.hist, P.scan_tmp, (int)S, key_bits, s);
         count_launch(), k_gather3<<<blocks(S, 256), 256, 0, s>>>(xn.p, P.idxS.p, S, P.xs.p);
         int nk = P.nrhs * P.ks;
         P.dens_s.reserve((size_t)S * nk);
         count_launch(), k_gather_dens<<<blocks(S * nk, 256), 256, 0, s>>>(dens, P.idxS.p, S, P.nrhs, P.ks, P.dens_s.p);
     }
-    if (T && trg == src && T == S && P.same_offsets) {
+    P.same_points = T && trg == src && T == S && P.same_offsets;
+    if (P.same_points) {
         // targets are the sources: same keys, order and coordinates
         PK_CUDA(cudaMemcpyAsync(P.keyT.p, P.keyS.p, sizeof(unsigned long long) * T, cudaMemcpyDeviceToDevice, s));
         PK_CUDA(cudaMemcpyAsync(P.idxT.p, P.idxS.p, sizeof(int) * T, cudaMemcpyDeviceToDevice, s));
@@ -707,7 +755,7 @@ void sort_points(Plan &P, const double *src, const double *dens, const double *t
         count_launch(), k_keys<<<blocks(T, 256), 256, 0, s>>>(trg, T, P.lo[0], P.lo[1], P.lo[2], P.L, wrap, D, xn.p,
                                               P.keyT.p, P.idxT.p, P.err.p, P.nprob > 1 ? P.toff.p : nullptr,
                                               P.nprob);
-        radix_sort(P.keyT, P.idxT, P.keyT2, P.idxT2, P.hist, (int)T, key_bits, s);
+        radix_sort(P.keyT, P.idxT, P.keyT2, P.idxT2, P.hist, P.scan_tmp, (int)T, key_bits, s);
         count_launch(), k_gather3<<<blocks(T, 256), 256, 0, s>>>(xn.p, P.idxT.p, T, P.xt.p);
     }
 }
