@@ -709,9 +709,33 @@ static void gemm(const Task &t, const int *slot_table, int slot_stride, const T 
 template <typename T>
 struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };  // one 16-byte (binary32) access
 
-// 1/sqrt(r2) for r2 > 0 known (no coincidence test)
-__device__ __forceinline__ float rsqrt_nz(float r2) { return rsqrtf(r2); }
+// 1/sqrt(r2) for a normal r2 > 0: binary32 by the PTX approximate reciprocal
+// square root (relative error below 2^-22.9, subnormal inputs flushed),
+// binary64 by a correctly rounded square root and division
+__device__ __forceinline__ float rsqrt_nz(float r2) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
+    return y;
+}
 __device__ __forceinline__ double rsqrt_nz(double r2) { return 1.0 / sqrt(r2); }
+// smallest normal number of each type
+__device__ __forceinline__ float tiny_normal(float) { return 1.17549435e-38f; }
+__device__ __forceinline__ double tiny_normal(double) { return 2.2250738585072014e-308; }
+
+// How a kernel sum treats the distance r of a pair:
+//   kFar   r > 0 known (equivalent and check surfaces, distinct boxes' surfaces);
+//   kSelf  a source may coincide with the target: r below the smallest
+//          normal number drops the pair (the self-interaction is excluded);
+//   kNear  distinct points of different boxes: r^2 is clamped to the
+//          smallest normal number, so a pair that rounding made coincide
+//          stays finite.
+enum PairMode { kFar = 0, kSelf = 1, kNear = 2 };
+template <int MODE, typename T>
+__device__ __forceinline__ T inv_r(T r2) {
+    if constexpr (MODE == kSelf) return r2 >= tiny_normal(r2) ? rsqrt_nz(r2) : (T)0;
+    else if constexpr (MODE == kNear) return rsqrt_nz(fmax(r2, tiny_normal(r2)));
+    else return rsqrt_nz(r2);
+}
 
 __device__ __forceinline__ double exp2i(int l) { return ldexp(1.0, -l); }
 
@@ -770,14 +794,11 @@ struct LeafAcc {
                 acc[r][a] = 0;
             }
     }
-    // one source at offset d = x - y with densities f[r][a]; SELF: the source
-    // may coincide with the target (then it contributes nothing)
-    template <bool SELF>
+    // one source at offset d = x - y with densities f[r][a]; MODE: PairMode
+    template <int MODE>
     __device__ __forceinline__ void add(T dx, T dy, T dz, const T (*f)[K]) {
         const T r2 = dx * dx + dy * dy + dz * dz;
-        T ir;
-        if constexpr (SELF) ir = inv_sqrt(r2);
-        else ir = rsqrt_nz(r2);
+        const T ir = inv_r<MODE>(r2);
         if constexpr (KT == 4) {
             const T ir3 = ir * ir * ir;
 #pragma unroll
@@ -804,15 +825,13 @@ struct LeafAcc {
         }
     }
     // one source of the source kernel (KS components) at offset d = x - y
-    template <bool SELF>
+    template <int MODE>
     __device__ __forceinline__ void add_src(T dx, T dy, T dz, const T (*f)[KS]) {
         if constexpr (KS == K) {
-            add<SELF>(dx, dy, dz, f);
+            add<MODE>(dx, dy, dz, f);
         } else {
             const T r2 = dx * dx + dy * dy + dz * dz;
-            T ir;
-            if constexpr (SELF) ir = inv_sqrt(r2);
-            else ir = rsqrt_nz(r2);
+            const T ir = inv_r<MODE>(r2);
             const T ir3 = ir * ir * ir;
 #pragma unroll
             for (int r = 0; r < R; r++) acc[r][0] += (f[r][0] * dx + f[r][1] * dy + f[r][2] * dz) * ir3;
@@ -857,7 +876,7 @@ __global__ void __launch_bounds__(KS_T) k_s2m(const int *__restrict__ leaves, co
             int m = min(KS_T, r.y - s0);
             for (int j = 0; j < m; j++) {
                 const V4<T> y = sy[j];
-                L.template add_src<false>(x0 - y.x, x1 - y.y, x2 - y.z, sphi[j]);
+                L.template add_src<kFar>(x0 - y.x, x1 - y.y, x2 - y.z, sphi[j]);
             }
         }
         if (i < n) {
@@ -931,7 +950,7 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
                 int m = min(KS_T, r.y - s0);
                 for (int j = 0; j < m; j++) {
                     const V4<T> y = sy[j];
-                    L.template add_src<false>(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
+                    L.template add_src<kFar>(xo0 - y.x, xo1 - y.y, xo2 - y.z, sphi[j]);
                 }
             }
         }
@@ -946,190 +965,244 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
     }
 }
 
-// Kernel sums at a target leaf for up to R density vectors at once (the
-// geometry and 1/r are shared): L2T from the downward equivalent surface,
-// W-list M2T from upward equivalent surfaces, U-list P2P with periodic images.
-// One thread per target; sources staged in shared memory NT at a time as
-// (x, y, z) and R x K densities; the image offset of a source box is added to
-// the target once.  Each staged tile is summed in registers and added to the
-// running total with Kahan compensation.
-template <typename T, int K, int NT, int R, int TPT, int KT, int KS = K>
-__global__ void __launch_bounds__(NT) k_leaf(
+// Kernel sums at a target leaf B for up to R density vectors at once (the
+// geometry and 1/r are shared): L2T from B's downward equivalent surface,
+// M2T from the upward equivalent surfaces of W(B), and the U-list direct sums
+// with the periodic images (Sec. 2.2, the near field of Eq. 3).
+// One warp per block; blockIdx.y takes chunks of at most (32 / G) QMAX
+// targets.  The warp's G groups of lanes split each staged tile of LT sources
+// (slot j to group j mod G) over the same targets, Q targets per lane in
+// registers, so one shared load of a source serves Q pairs; the groups' sums
+// are added at the end.  The
+// sources of every box of a list are staged already moved into B's frame
+// (y + p - c_B), so a tile runs across box boundaries, and the global loads of
+// the next tile are in flight while the current one is summed.  Each tile's
+// sum joins the running total with Kahan compensation.
+constexpr int LT = 64;  // sources per staged tile (two per lane)
+
+// blocks per SM the register budget is sized for: 16 (128 registers a thread)
+// for binary32 sums of up to 6 words a target, else 8
+template <typename T, int R, int KT>
+constexpr int leaf_min_blocks() { return sizeof(T) == 4 && R * KT <= 6 ? 16 : 8; }
+
+template <typename T, int K, int R, int QMAX, int G, int KT, int KS = K>
+__global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT>())) k_leaf(
     const int *__restrict__ leaves, const int4 *__restrict__ bpos, const int2 *__restrict__ srange,
     const int2 *__restrict__ trange, const int *__restrict__ uptr, const int *__restrict__ ubox,
     const unsigned char *__restrict__ ush, const int *__restrict__ wptr, const int *__restrict__ wbox,
     const unsigned char *__restrict__ wsh, const V4<T> *__restrict__ yrel, const V4<T> *__restrict__ xrel,
     const T *__restrict__ dens, const T *__restrict__ up, const T *__restrict__ dn, int nrhs, int rhs0,
     const T *__restrict__ g, int n, double *__restrict__ pot) {
-    // one block per target leaf; up to TPT targets per thread (NT * TPT per
-    // pass) while more than NT remain, so each staged source serves them all
-    __shared__ V4<T> sy[NT];
-    __shared__ T sphi[NT][R][K];
-    __shared__ T sphs[KS == K ? 1 : NT][R][KS];  // U-list source densities when they differ from K
-    const unsigned tid = threadIdx.x;
-    // one density value per source (Laplace, one vector): it rides in the source's fourth lane
-    constexpr bool PACK = K == 1 && R == 1;
-    constexpr bool PACK_SRC = PACK && KS == 1;
+    using Acc = LeafAcc<T, K, R, KT, KS>;
+    constexpr int ND = R * (K > KS ? K : KS);  // densities of a staged source
+    constexpr int EP = ND & ~1 ? ND & ~1 : 1;   // beyond the first (in the fourth lane), padded to even
+    __shared__ V4<T> sy[LT];
+    __shared__ __align__(16) T sd[LT][EP];
+    __shared__ int s_start[33], s_idx[32];
+    __shared__ V4<T> s_off[32];
+    constexpr int LW = 32 / G;  // lanes of a source group
+    const int lane = threadIdx.x, grp = lane / LW, lg = lane % LW;
     const int b = leaves[blockIdx.x];
     const int4 B = bpos[b];
-    const T h = (T)exp2i(B.w);
+    const double hB = exp2i(B.w);
     const int2 tr = trange[b];
     const int kn = n * K, nv = min(R, nrhs - rhs0);
-    // stage surface points of a box of half-width sc around the origin, densities from phi rows
-    auto stage_surface = [&](int j0, T sc, const T *phi) {
-        int j = j0 + tid;
-        if (j < n) {
-            sy[tid] = V4<T>{sc * g[3 * j], sc * g[3 * j + 1], sc * g[3 * j + 2], PACK ? phi[j] : (T)0};
-            if constexpr (!PACK) {
-#pragma unroll
-                for (int r = 0; r < R; r++)
-#pragma unroll
-                    for (int a = 0; a < K; a++)
-                        sphi[tid][r][a] = r < nv ? phi[(long long)r * kn + j * K + a] : (T)0;
-            }
-        }
-    };
-    // one pass over the sources for NT * Q targets (Q = 1 or 2)
-    auto pass = [&](auto q_tag, int t0) {
-        constexpr int Q = decltype(q_tag)::value;
+    const int u0 = uptr[b], nu = uptr[b + 1] - u0, w0 = wptr[b], nw = wptr[b + 1] - w0;
+    const T pad = (T)(4.0 * hB);  // a staged slot past the end: zero density, far from every target of B
+
+    // one chunk of at most LW QMAX targets, nq = ceil(targets / LW) of the Q
+    // slots of a lane in use (the tile sums are compiled for each nq)
+    auto chunk = [&](int t0, int nq) {
+        constexpr int Q = QMAX;
         T xs[Q][3];
 #pragma unroll
         for (int q = 0; q < Q; q++) {
-            const int t = t0 + (int)tid + q * NT;
+            const int t = t0 + lg + LW * q;
             xs[q][0] = xs[q][1] = xs[q][2] = 0;
             if (t < tr.y) {
-                V4<T> v = xrel[t];
+                const V4<T> v = xrel[t];
                 xs[q][0] = v.x;
                 xs[q][1] = v.y;
                 xs[q][2] = v.z;
             }
         }
-        LeafAcc<T, K, R, KT, KS> L[Q];
+        Acc L[Q];
 #pragma unroll
         for (int q = 0; q < Q; q++) L[q].init();
-        // L2T from the downward equivalent surface (edge 2.95 h)
-        {
-            const T *phi = dn + ((long long)b * nrhs + rhs0) * kn;
-            for (int j0 = 0; j0 < n; j0 += NT) {
-                __syncthreads();
-                stage_surface(j0, (T)1.475 * h, phi);
-                __syncthreads();
-                const int m = min(NT, n - j0);
-#pragma unroll 4
-                for (int jj = 0; jj < m; jj++) {
-                    const V4<T> y = sy[jj];
-                    const T fw[1][1] = {{y.w}};
+
+        // F staged sources of one list; fetch(f, y, d) reads source f of the
+        // list in B's frame with its densities d[r * CP + a]
+        auto run = [&](auto mode_tag, auto u_tag, int F, auto fetch) {
+            constexpr int MODE = decltype(mode_tag)::value;
+            constexpr bool U = decltype(u_tag)::value;
+            constexpr int CP = U ? KS : K, NP = R * CP;
+            V4<T> ry[2];
+            T rd[2][NP];
+            auto load = [&](int base) {
 #pragma unroll
-                    for (int q = 0; q < Q; q++)
-                        L[q].template add<false>(xs[q][0] - y.x, xs[q][1] - y.y, xs[q][2] - y.z,
-                                                 PACK ? (const T(*)[K])fw : sphi[jj]);
+                for (int s = 0; s < 2; s++) {
+                    const int f = base + lane + 32 * s;
+                    if (f < F) fetch(f, ry[s], rd[s]);
                 }
+            };
+            load(0);
+            for (int base = 0; base < F; base += LT) {
+                const int m = min(LT, F - base);
+                __syncwarp();
 #pragma unroll
-                for (int q = 0; q < Q; q++) L[q].flush();
-            }
-        }
-        // W list: upward equivalent surfaces (edge 1.05 h_A) of finer boxes
-        for (int e = wptr[b]; e < wptr[b + 1]; e++) {
-            int A = wbox[e], sh[3];
-            decode_shift(wsh[e], sh);
-            int4 Ap = bpos[A];
-            double off[3];
-            centre_offset(B, Ap, sh, off);
-            T xo[Q][3];
+                for (int s = 0; s < 2; s++) {
+                    const int j = lane + 32 * s;
+                    if (j < m) {
+                        V4<T> y = ry[s];
+                        y.w = rd[s][0];
+                        sy[j] = y;
 #pragma unroll
-            for (int q = 0; q < Q; q++)
-                for (int c = 0; c < 3; c++) xo[q][c] = xs[q][c] + (T)off[c];
-            const T *phi = up + ((long long)A * nrhs + rhs0) * kn;
-            for (int j0 = 0; j0 < n; j0 += NT) {
-                __syncthreads();
-                stage_surface(j0, (T)(0.525 * exp2i(Ap.w)), phi);
-                __syncthreads();
-                const int m = min(NT, n - j0);
-#pragma unroll 4
-                for (int jj = 0; jj < m; jj++) {
-                    const V4<T> y = sy[jj];
-                    const T fw[1][1] = {{y.w}};
+                        for (int i = 1; i < NP; i++) sd[j][i - 1] = rd[s][i];
+                    } else if (j < (m + G - 1) / G * G) {
+                        sy[j] = V4<T>{pad, pad, pad, (T)0};
 #pragma unroll
-                    for (int q = 0; q < Q; q++)
-                        L[q].template add<false>(xo[q][0] - y.x, xo[q][1] - y.y, xo[q][2] - y.z,
-                                                 PACK ? (const T(*)[K])fw : sphi[jj]);
-                }
-#pragma unroll
-                for (int q = 0; q < Q; q++) L[q].flush();
-            }
-        }
-        // U list: direct sums, periodic images through the shift
-        for (int e = uptr[b]; e < uptr[b + 1]; e++) {
-            int A = ubox[e], sh[3];
-            decode_shift(ush[e], sh);
-            double off[3];
-            centre_offset(B, bpos[A], sh, off);
-            T xo[Q][3];
-#pragma unroll
-            for (int q = 0; q < Q; q++)
-                for (int c = 0; c < 3; c++) xo[q][c] = xs[q][c] + (T)off[c];
-            const int2 rg = srange[A];
-            for (int s0 = rg.x; s0 < rg.y; s0 += NT) {
-                __syncthreads();
-                const int sidx = s0 + tid;
-                if (sidx < rg.y) {
-                    V4<T> v = yrel[sidx];
-                    if constexpr (PACK_SRC) {
-                        v.w = dens[(long long)sidx * nrhs + rhs0];
-                    } else {
-                        T(*dst)[KS] = [&]() -> T(*)[KS] {
-                            if constexpr (KS == K) return sphi[tid];
-                            else return sphs[tid];
-                        }();
-#pragma unroll
-                        for (int r = 0; r < R; r++)
-#pragma unroll
-                            for (int a = 0; a < KS; a++)
-                                dst[r][a] = r < nv ? dens[(long long)sidx * nrhs * KS + (rhs0 + r) * KS + a] : (T)0;
+                        for (int i = 1; i < NP; i++) sd[j][i - 1] = (T)0;
                     }
-                    sy[tid] = v;
                 }
-                __syncthreads();
-                const int m = min(NT, rg.y - s0);
-#pragma unroll 4
-                for (int j = 0; j < m; j++) {
-                    const V4<T> y = sy[j];
-                    [[maybe_unused]] const T fw[1][1] = {{y.w}};
-                    const T(*src)[KS] = [&]() -> const T(*)[KS] {
-                        if constexpr (PACK_SRC) return (const T(*)[KS])fw;
-                        else if constexpr (KS == K) return sphi[j];
-                        else return sphs[j];
-                    }();
+                __syncwarp();
+                if (base + LT < F) load(base + LT);
+                const int n2 = (m + G - 1) / G;
+                auto sum_tile = [&](auto nq_tag) {
+                    constexpr int NQ = decltype(nq_tag)::value;
+#pragma unroll 2
+                    for (int i = 0; i < n2; i++) {
+                        const int j = G * i + grp;
+                        const V4<T> y = sy[j];
+                        T f[R][CP];
+                        f[0][0] = y.w;
 #pragma unroll
-                    for (int q = 0; q < Q; q++)
-                        L[q].template add_src<true>(xo[q][0] - y.x, xo[q][1] - y.y, xo[q][2] - y.z, src);
-                }
+                        for (int k = 1; k < NP; k++) f[k / CP][k % CP] = sd[j][k - 1];
+#pragma unroll
+                        for (int q = 0; q < NQ; q++) {
+                            if constexpr (U)
+                                L[q].template add_src<MODE>(xs[q][0] - y.x, xs[q][1] - y.y, xs[q][2] - y.z, f);
+                            else
+                                L[q].template add<MODE>(xs[q][0] - y.x, xs[q][1] - y.y, xs[q][2] - y.z, f);
+                        }
+                    }
+                };
+                if (nq <= 1) sum_tile(std::integral_constant<int, 1>{});
+                else if (nq == 2) sum_tile(std::integral_constant<int, (Q < 2 ? Q : 2)>{});
+                else if (nq == 3) sum_tile(std::integral_constant<int, (Q < 3 ? Q : 3)>{});
+                else sum_tile(std::integral_constant<int, Q>{});
 #pragma unroll
                 for (int q = 0; q < Q; q++) L[q].flush();
             }
-        }
-#pragma unroll
-        for (int q = 0; q < Q; q++) {
-            const int t = t0 + (int)tid + q * NT;
-            if (t < tr.y) {
+        };
+
+        // L2T and W: n points of an equivalent surface per entry; entry 0 is
+        // B's downward surface (half-width 1.475 h_B), entry e > 0 the upward
+        // surface (half-width 0.525 h_A) of the W box e - 1, moved into B's frame
+        for (int c0 = 0; c0 < 1 + nw; c0 += 32) {
+            const int e = c0 + lane, ne = min(32, 1 + nw - c0);
+            __syncwarp();
+            if (e == 0) {
+                s_idx[lane] = -1 - b;
+                s_off[lane] = V4<T>{(T)0, (T)0, (T)0, (T)(1.475 * hB)};
+            } else if (e < 1 + nw) {
+                const int A = wbox[w0 + e - 1];
+                int sh[3];
+                decode_shift(wsh[w0 + e - 1], sh);
+                const int4 Ap = bpos[A];
+                double off[3];
+                centre_offset(B, Ap, sh, off);
+                s_idx[lane] = A;
+                s_off[lane] = V4<T>{(T)off[0], (T)off[1], (T)off[2], (T)(0.525 * exp2i(Ap.w))};
+            }
+            __syncwarp();
+            run(std::integral_constant<int, kFar>{}, std::false_type{}, ne * n, [&](int f, V4<T> &y, T(&d)[R * K]) {
+                const int ei = f / n, j = f - ei * n, idx = s_idx[ei];
+                const V4<T> o = s_off[ei];
+                const T *phi = idx < 0 ? dn + ((long long)(-1 - idx) * nrhs + rhs0) * kn
+                                       : up + ((long long)idx * nrhs + rhs0) * kn;
+                y.x = o.w * g[3 * j] - o.x;
+                y.y = o.w * g[3 * j + 1] - o.y;
+                y.z = o.w * g[3 * j + 2] - o.z;
 #pragma unroll
                 for (int r = 0; r < R; r++)
-                    if (r < nv)
 #pragma unroll
-                        for (int a = 0; a < KT; a++)
-                            pot[(long long)t * nrhs * KT + (rhs0 + r) * KT + a] =
-                                ((double)L[q].tot[r][a] - (double)L[q].cmp[r][a]) * LeafAcc<T, K, R, KT, KS>::kScale;
+                    for (int a = 0; a < K; a++) d[r * K + a] = r < nv ? phi[(long long)r * kn + j * K + a] : (T)0;
+            });
+        }
+
+        // U list: B itself (coincident points drop out), then the adjacent
+        // leaves and images; entries of a chunk are laid end to end
+        auto u_list = [&](auto mode_tag, bool self) {
+            for (int c0 = 0; c0 < nu; c0 += 32) {
+                const int e = c0 + lane;
+                int cnt = 0, i0 = 0;
+                V4<T> o{(T)0, (T)0, (T)0, (T)0};
+                if (e < nu) {
+                    const int A = ubox[u0 + e];
+                    const unsigned char code = ush[u0 + e];
+                    if ((A == b && code == 13) == self) {  // code 13: shift (0, 0, 0)
+                        const int2 rg = srange[A];
+                        cnt = rg.y - rg.x;
+                        i0 = rg.x;
+                        int sh[3];
+                        decode_shift(code, sh);
+                        double off[3];
+                        centre_offset(B, bpos[A], sh, off);
+                        o = V4<T>{(T)off[0], (T)off[1], (T)off[2], (T)0};
+                    }
+                }
+                int inc = cnt;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, inc, d);
+                    if (lane >= d) inc += v;
+                }
+                const int F = __shfl_sync(0xffffffffu, inc, 31);
+                __syncwarp();
+                s_start[lane] = inc - cnt;
+                s_idx[lane] = i0;
+                s_off[lane] = o;
+                if (lane == 31) s_start[32] = inc;
+                __syncwarp();
+                run(mode_tag, std::true_type{}, F, [&](int f, V4<T> &y, T(&d)[R * KS]) {
+                    int ei = 0;  // the last entry starting at or before f
+#pragma unroll
+                    for (int st = 16; st; st >>= 1)
+                        if (s_start[ei + st] <= f) ei += st;
+                    const int i = s_idx[ei] + f - s_start[ei];
+                    const V4<T> o = s_off[ei], v = yrel[i];
+                    y.x = v.x - o.x;
+                    y.y = v.y - o.y;
+                    y.z = v.z - o.z;
+#pragma unroll
+                    for (int r = 0; r < R; r++)
+#pragma unroll
+                        for (int a = 0; a < KS; a++)
+                            d[r * KS + a] = r < nv ? dens[(long long)i * nrhs * KS + (rhs0 + r) * KS + a] : (T)0;
+                });
             }
+        };
+        u_list(std::integral_constant<int, kSelf>{}, true);
+        u_list(std::integral_constant<int, kNear>{}, false);
+
+        // the G groups' sums of each target, added in binary64
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            const int t = t0 + lg + LW * q;
+#pragma unroll
+            for (int r = 0; r < R; r++)
+#pragma unroll
+                for (int a = 0; a < KT; a++) {
+                    double v = (double)L[q].tot[r][a] - (double)L[q].cmp[r][a];
+#pragma unroll
+                    for (int o = LW; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (grp == 0 && t < tr.y && r < nv)
+                        pot[(long long)t * nrhs * KT + (rhs0 + r) * KT + a] = v * Acc::kScale;
+                }
         }
     };
-    for (int t0 = tr.x; t0 < tr.y;) {
-        if (TPT > 1 && tr.y - t0 > NT) {  // block-uniform: more than NT targets left
-            pass(std::integral_constant<int, TPT>{}, t0);
-            t0 += NT * TPT;
-        } else {
-            pass(std::integral_constant<int, 1>{}, t0);
-            t0 += NT;
-        }
+    for (int t0 = tr.x + (int)blockIdx.y * LW * QMAX; t0 < tr.y; t0 += (int)gridDim.y * LW * QMAX) {
+        chunk(t0, (min(tr.y - t0, LW * QMAX) + LW - 1) / LW);  // block-uniform
     }
 }
 
@@ -1375,30 +1448,26 @@ static void leaves_t(Plan &P, cudaStream_t s) {
     P.pot_s.reserve((size_t)P.T * nr * KT + 1);
     auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
     auto *xr = reinterpret_cast<const V4<T> *>(B::xrel(P).p);
-    // one block per target leaf; block size near the leaf size (most leaves
-    // hold about s/2 targets); up to 4 density vectors per pass
-    auto launch = [&](auto nt_tag, auto r_tag, int r0) {
-        constexpr int NT = decltype(nt_tag)::value, R = decltype(r_tag)::value;
-        // one leaf per block (several leaves per block, one warp each, was measured
-        // slower: a block holds its slot until its slowest leaf is done); two
-        // targets per thread for up to two vectors, so a leaf of up to 2 NT
-        // targets takes one pass over its sources
-        constexpr int TPT = R <= 2 ? 2 : 1;
-        count_launch(), k_leaf<T, K, NT, R, TPT, KT, KS><<<P.n_leaves_trg, NT, 0, s>>>(
+    // one warp per target leaf and chunk of (32 / G) QMAX targets (QMAX from
+    // the outputs a target carries); up to 4 density vectors per launch
+    auto launch = [&](auto r_tag, int r0) {
+        constexpr int R = decltype(r_tag)::value, W = R * KT * (int)(sizeof(T) / 4);
+        constexpr int QMAX = W <= 3 ? 4 : (W <= 6 ? 2 : 1);  // registers: three sums per output
+        // source groups: four for Laplace (a cheap pair: one staged source serving
+        // more targets pays), two for Stokes (measured faster than four: a leaf
+        // of up to 64 targets stays in one block); targets per chunk
+        constexpr int G = K == 1 && QMAX == 4 ? 4 : (QMAX >= 2 ? 2 : 1), CH = 32 / G * QMAX;
+        const dim3 grid(P.n_leaves_trg, std::max(1, (P.leaf_max + CH - 1) / CH));
+        count_launch(), k_leaf<T, K, R, QMAX, G, KT, KS><<<grid, 32, 0, s>>>(
                 P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
                 P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
                 B::dn(P).p, nr, r0, B::g(P).p, P.n, P.pot_s.p);
     };
-    auto launch_r = [&](auto nt_tag, int r0) {
-        if (nr - r0 == 1) launch(nt_tag, std::integral_constant<int, 1>{}, r0);
-        else if (nr - r0 == 2) launch(nt_tag, std::integral_constant<int, 2>{}, r0);
-        else launch(nt_tag, std::integral_constant<int, 4>{}, r0);
-    };
     if (P.n_leaves_trg)
         for (int r0 = 0; r0 < nr; r0 += 4) {
-            if (P.leaf_max <= 64) launch_r(std::integral_constant<int, 32>{}, r0);
-            else if (P.leaf_max <= 128) launch_r(std::integral_constant<int, 64>{}, r0);
-            else launch_r(std::integral_constant<int, 128>{}, r0);
+            if (nr - r0 == 1) launch(std::integral_constant<int, 1>{}, r0);
+            else if (nr - r0 == 2) launch(std::integral_constant<int, 2>{}, r0);
+            else launch(std::integral_constant<int, 4>{}, r0);
         }
 }
 
