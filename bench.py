@@ -166,6 +166,32 @@ def oracle_sample(wl, x, d, off, nsample, rng):
     return np.concatenate(idx), np.concatenate(ref)
 
 
+def oracle_sample_cached(cache_dir, wl, x, d, off, nsample, rng):
+    """oracle_sample, kept on disk under cache_dir (when given) by a digest of
+    the kernel, periodicity, points, first density vector and sample size, with
+    the oracle's own time for it.  Returns (idx, ref, seconds, cached)."""
+    key = None
+    if cache_dir:
+        import hashlib
+        h = hashlib.sha1()
+        h.update(repr((wl["kernel"], wl["periodic"], nsample)).encode())
+        h.update(np.ascontiguousarray(x).tobytes())
+        h.update(np.ascontiguousarray(d[0]).tobytes())
+        if off is not None:
+            h.update(np.asarray(off).tobytes())
+        key = os.path.join(cache_dir, f"oracle_{h.hexdigest()}.npz")
+        if os.path.exists(key):
+            z = np.load(key)
+            return z["idx"], z["ref"], float(z["seconds"]), True
+    t0 = time.perf_counter()
+    idx, ref = oracle_sample(wl, x, d, off, nsample, rng)
+    t_cpu = time.perf_counter() - t0
+    if key:
+        os.makedirs(cache_dir, exist_ok=True)
+        np.savez(key, idx=idx, ref=ref, seconds=t_cpu)
+    return idx, ref, t_cpu, False
+
+
 def workload_name(name, wl, n, p, leaf):
     if name == "laplace_tp_multi":
         return f"laplace_tp_multi_{n}problems_p{p}"
@@ -247,6 +273,10 @@ def main():
                     help="image layers summed directly in the root operator (Sec. 3.6 varies 1..3)")
     ap.add_argument("--leaf", type=int, default=None)
     ap.add_argument("--sample", type=int, default=None, help="oracle targets for accuracy / cpu_baseline")
+    ap.add_argument("--cpu-kifmm-n", type=int, default=1 << 17,
+                    help="points of the instance the plain CPU KIFMM baseline runs on (0: skip it)")
+    ap.add_argument("--oracle-cache", default=None,
+                    help="directory keeping the oracle's sampled values between runs on the same inputs")
     ap.add_argument("--ref-sample", type=int, default=64, help="oracle targets per reference step")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison step")
     ap.add_argument("--precompute-host", action="store_true", help="also time Stage 1 built on the host")
@@ -400,10 +430,9 @@ def main():
                 "issued_tensor_frac": achieved * 3 / peak}
         # accuracy and the CPU baseline: the FP64 oracle on a seeded target sample
         rng = np.random.default_rng(123)
-        t0 = time.perf_counter()
-        idx, ref = oracle_sample(wl, x, d, off, args.sample, rng)
-        t_cpu = time.perf_counter() - t0
+        idx, ref, t_cpu, cached = oracle_sample_cached(args.oracle_cache, wl, x, d, off, args.sample, rng)
         err = __import__("oracle").error_metrics(u[0][idx], ref)
+        kifmm_cpu = cpu_kifmm_block(args, wl, pk, dev, cache) if args.cpu_kifmm_n > 0 else None
         fp64 = None
         if not args.no_fp64:
             p64 = pk.PeriodicKIFMM(kernel, periodic, p=args.p, ell=args.ell, leaf_max=args.leaf,
@@ -460,7 +489,8 @@ def main():
             "cpu_baseline": {"value": len(idx) / t_cpu, "unit": "targets/s", "cores": os.cpu_count(),
                              "kind": "oracle",
                              "sample": f"{len(idx)} seeded targets of the workload, all sources of their problem, "
-                                       f"first density vector"},
+                                       f"first density vector" + (" (time of the cached oracle run)" if cached else "")},
+            "cpu_kifmm": kifmm_cpu,
             "accuracy": {"vs": "FP64 Ewald oracle", "targets": int(len(idx)), "density_vector": 0, **err},
             "fp64_path": fp64,
             "precompute": pre,
@@ -478,6 +508,49 @@ def main():
         dist.destroy_process_group()
     if result is not None:
         print(json.dumps(result), flush=True)
+
+
+def cpu_kifmm_block(args, wl, pk, dev, cache):
+    """The plain binary64 KIFMM on the host cores (baseline/cpu_kifmm, C++/OpenMP,
+    sharing no code with the library or the oracle) on a smaller instance of the
+    same workload (same point and density distribution, p and leaf size), with
+    the GPU library timed on that same instance and both checked against the
+    oracle on a target sample.  Kernels Laplace/Stokes, free or triply periodic,
+    one density vector, one problem; else None."""
+    kernel, periodic = wl["kernel"], wl["periodic"]
+    if kernel not in (0, 1) or periodic not in (0, 7) or wl["nrhs"] != 1 or args.workload == "laplace_tp_multi":
+        return None
+    import torch
+    from baseline import cpu_kifmm
+    n = min(args.n, args.cpu_kifmm_n)
+    x, d, _, _ = workload(args.workload, n, 0)
+    u, t, depth = cpu_kifmm.evaluate(kernel, periodic, args.p, args.leaf, x, d[0].reshape(n, -1))
+    idx = np.sort(np.random.default_rng(7).choice(n, min(64, n), replace=False))
+    ref = oracle_sum(kernel, periodic, x, d[0], x[idx]).reshape(len(idx), -1)
+    rel = lambda a: float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+    # the GPU library (MIXED) on the same instance, device time per evaluation
+    plan = pk.PeriodicKIFMM(kernel, periodic, p=args.p, ell=args.ell, leaf_max=args.leaf, depth_max=wl["depth"],
+                            precision=pk.MIXED, nrhs=1, cache_dir=cache)
+    tx, td = torch.tensor(x, device=dev), torch.tensor(np.ascontiguousarray(d), device=dev)
+    out = torch.empty((1, n, 1 if kernel == 0 else 3), dtype=torch.float64, device=dev)
+    for _ in range(3):
+        plan.evaluate(tx, td, tx, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        plan.evaluate(tx, td, tx, out)
+    e1.record()
+    torch.cuda.synchronize()
+    gpu_ms = e0.elapsed_time(e1) / 5
+    ug = out[0].cpu().numpy()[idx]
+    plan.close()
+    return {"value": n / (t[1] + t[2]), "unit": "targets/s", "cores": cpu_kifmm.threads(),
+            "kind": "plain FP64 KIFMM, C++/OpenMP (uniform octree, dense operators)",
+            "N": n, "p": args.p, "leaf_max": args.leaf, "depth": depth,
+            "tree_s": float(t[1]), "eval_s": float(t[2]), "operator_setup_s": float(t[0]),
+            "rel_l2": rel(u[idx].reshape(len(idx), -1)), "targets_checked": int(len(idx)),
+            "gpu_same_instance": {"value": n / (gpu_ms / 1e3), "ms": gpu_ms, "precision": "mixed",
+                                  "rel_l2": rel(ug.reshape(len(idx), -1))}}
 
 
 def p2p_block(kernel, p, ntrg, nrhs, stats, leaves_ms, clocks, pk_, sms):
