@@ -978,7 +978,7 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
 // (y + p - c_B), so a tile runs across box boundaries, and the global loads of
 // the next tile are in flight while the current one is summed.  Each tile's
 // sum joins the running total with Kahan compensation.
-constexpr int LT = 64;  // sources per staged tile (two per lane)
+constexpr int LT = 64;  // sources per staged tile (LT / 32 per lane)
 
 // blocks per SM the register budget is sized for: 16 (128 registers a thread)
 // for binary32 sums of up to 6 words a target, else 8
@@ -1036,11 +1036,11 @@ __global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT>())) k_leaf(
             constexpr int MODE = decltype(mode_tag)::value;
             constexpr bool U = decltype(u_tag)::value;
             constexpr int CP = U ? KS : K, NP = R * CP;
-            V4<T> ry[2];
-            T rd[2][NP];
+            V4<T> ry[LT / 32];
+            T rd[LT / 32][NP];
             auto load = [&](int base) {
 #pragma unroll
-                for (int s = 0; s < 2; s++) {
+                for (int s = 0; s < LT / 32; s++) {
                     const int f = base + lane + 32 * s;
                     if (f < F) fetch(f, ry[s], rd[s]);
                 }
@@ -1050,7 +1050,7 @@ __global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT>())) k_leaf(
                 const int m = min(LT, F - base);
                 __syncwarp();
 #pragma unroll
-                for (int s = 0; s < 2; s++) {
+                for (int s = 0; s < LT / 32; s++) {
                     const int j = lane + 32 * s;
                     if (j < m) {
                         V4<T> y = ry[s];
