@@ -904,16 +904,20 @@ __device__ __forceinline__ void centre_offset(int4 B, int4 A, const int sh[3], d
     off[2] = (B.z + 0.5) * hb - (A.z + 0.5) * ha - sh[2];
 }
 
-// X list: q~d[B][rhs][i] += h_B sum_{(A,p) in X(B)} sum_{s in A} K(0.525 h_B g_i - yrel_s + off) phi_s
+// X list: q~d[B][rhs][i] += h_B sum_{(A,p) in X(B)} sum_{s in A} K(0.525 h_B g_i - yrel_s + off) phi_s,
+// for the boxes B holding more targets than a surface has points; the targets of
+// the others take X(B)'s sources directly in the leaf kernel (exact, and cheaper)
 template <typename T, int K, int R, int KS = K>
 __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, const int4 *__restrict__ bpos,
-                                              const int2 *__restrict__ srange, const int *__restrict__ xptr,
+                                              const int2 *__restrict__ srange, const int2 *__restrict__ trange,
+                                              const int *__restrict__ xptr,
                                               const int *__restrict__ xbox, const unsigned char *__restrict__ xsh,
                                               const V4<T> *__restrict__ yrel, const T *__restrict__ dens, int nrhs,
                                               int rhs0, const T *__restrict__ g, int n, T *__restrict__ chk) {
     __shared__ V4<T> sy[KS_T];
     __shared__ T sphi[KS_T][R][KS];
     const int b = boxes[blockIdx.x];
+    if (trange[b].y - trange[b].x <= n) return;  // block-uniform
     const int4 B = bpos[b];
     const T h = (T)exp2i(B.w), sc = (T)0.525 * h;
     const int kn = n * K, nv = min(R, nrhs - rhs0);
@@ -980,19 +984,24 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
 // sum joins the running total with Kahan compensation.
 constexpr int LT = 64;  // sources per staged tile (LT / 32 per lane)
 
-// blocks per SM the register budget is sized for: 16 (128 registers a thread)
-// for binary32 sums of up to 6 words a target, else 8
-template <typename T, int R, int KT>
-constexpr int leaf_min_blocks() { return sizeof(T) == 4 && R * KT <= 6 ? 16 : 8; }
+// blocks per SM the register budget is sized for: 24 (85 registers a thread)
+// for one binary32 sum a target from one-component sources, 16 (128 registers)
+// for up to 3, else 8 (measured: Laplace at 24 blocks 18% faster than at 16,
+// Stokes slower at 20)
+template <typename T, int R, int KT, int KS>
+constexpr int leaf_min_blocks() {
+    return sizeof(T) == 4 && R * KT <= 1 && KS == 1 ? 24 : (sizeof(T) == 4 && R * KT <= 3 ? 16 : 8);
+}
 
 template <typename T, int K, int R, int QMAX, int G, int KT, int KS = K>
-__global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT>())) k_leaf(
+__global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT, KS>())) k_leaf(
     const int *__restrict__ leaves, const int4 *__restrict__ bpos, const int2 *__restrict__ srange,
     const int2 *__restrict__ trange, const int *__restrict__ uptr, const int *__restrict__ ubox,
     const unsigned char *__restrict__ ush, const int *__restrict__ wptr, const int *__restrict__ wbox,
-    const unsigned char *__restrict__ wsh, const V4<T> *__restrict__ yrel, const V4<T> *__restrict__ xrel,
-    const T *__restrict__ dens, const T *__restrict__ up, const T *__restrict__ dn, int nrhs, int rhs0,
-    const T *__restrict__ g, int n, double *__restrict__ pot) {
+    const unsigned char *__restrict__ wsh, const int *__restrict__ parent, const int *__restrict__ xptr,
+    const int *__restrict__ xbox, const unsigned char *__restrict__ xsh, const V4<T> *__restrict__ yrel,
+    const V4<T> *__restrict__ xrel, const T *__restrict__ dens, const double *__restrict__ xsrc, const T *__restrict__ up,
+    const T *__restrict__ dn, int nrhs, int rhs0, const T *__restrict__ g, int n, double *__restrict__ pot) {
     using Acc = LeafAcc<T, K, R, KT, KS>;
     constexpr int ND = R * (K > KS ? K : KS);  // densities of a staged source
     constexpr int EP = ND & ~1 ? ND & ~1 : 1;   // beyond the first (in the fourth lane), padded to even
@@ -1000,6 +1009,7 @@ __global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT>())) k_leaf(
     __shared__ __align__(16) T sd[LT][EP];
     __shared__ int s_start[33], s_idx[32];
     __shared__ V4<T> s_off[32];
+    __shared__ int s_xbeg[24], s_xpre[25], s_nx;  // X lists summed here: their first entries, prefix
     constexpr int LW = 32 / G;  // lanes of a source group
     const int lane = threadIdx.x, grp = lane / LW, lg = lane % LW;
     const int b = leaves[blockIdx.x];
@@ -1009,6 +1019,27 @@ __global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT>())) k_leaf(
     const int kn = n * K, nv = min(R, nrhs - rhs0);
     const int u0 = uptr[b], nu = uptr[b + 1] - u0, w0 = wptr[b], nw = wptr[b + 1] - w0;
     const T pad = (T)(4.0 * hB);  // a staged slot past the end: zero density, far from every target of B
+    if (tr.x + (int)blockIdx.y * (32 / G) * QMAX >= tr.y) return;  // no targets in this block's chunks
+    // the X lists of B and its ancestors whose box holds no more targets than a
+    // surface has points (k_s2l leaves those out): at most 22 levels of boxes
+    if (lane == 0) {
+        int k = 0, tot = 0;
+        for (int Bx = b; Bx >= 0 && k < 24; Bx = parent[Bx]) {
+            const int x0 = xptr[Bx], x1 = xptr[Bx + 1];
+            if (x1 == x0) continue;
+            const int2 tb = trange[Bx];
+            if (tb.y - tb.x <= n) {
+                s_xbeg[k] = x0;
+                s_xpre[k] = tot;
+                tot += x1 - x0;
+                k++;
+            }
+        }
+        s_xpre[k] = tot;
+        s_nx = k;
+    }
+    __syncwarp();
+    const int nxa = s_nx, nx = s_xpre[nxa];
 
     // one chunk of at most LW QMAX targets, nq = ceil(targets / LW) of the Q
     // slots of a lane in use (the tile sums are compiled for each nq)
@@ -1095,34 +1126,73 @@ __global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT>())) k_leaf(
             }
         };
 
+        // entry table of a chunk of up to 32 list entries, one per lane: the
+        // exclusive prefix of the entries' source counts, their first index and
+        // offset; returns the chunk's source count
+        auto publish = [&](int cnt, int idx, V4<T> o) {
+            int inc = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += v;
+            }
+            const int F = __shfl_sync(0xffffffffu, inc, 31);
+            __syncwarp();  // the last chunk's sources are all staged
+            s_start[lane] = inc - cnt;
+            s_idx[lane] = idx;
+            s_off[lane] = o;
+            if (lane == 31) s_start[32] = inc;
+            __syncwarp();
+            return F;
+        };
+        auto entry_of = [&](int f) {  // the last entry starting at or before f
+            int ei = 0;
+#pragma unroll
+            for (int st = 16; st; st >>= 1)
+                if (s_start[ei + st] <= f) ei += st;
+            return ei;
+        };
+        // a W box holding no more sources than a surface has points is summed
+        // from its sources (exactly, and at no more cost) instead of its
+        // upward equivalent surface
+        auto w_direct = [&](int A) {
+            const int2 rg = srange[A];
+            return rg.y - rg.x <= n;
+        };
+
         // L2T and W: n points of an equivalent surface per entry; entry 0 is
         // B's downward surface (half-width 1.475 h_B), entry e > 0 the upward
         // surface (half-width 0.525 h_A) of the W box e - 1, moved into B's frame
         for (int c0 = 0; c0 < 1 + nw; c0 += 32) {
-            const int e = c0 + lane, ne = min(32, 1 + nw - c0);
-            __syncwarp();
+            const int e = c0 + lane;
+            int cnt = 0, idx = 0;
+            V4<T> o{(T)0, (T)0, (T)0, (T)0};
             if (e == 0) {
-                s_idx[lane] = -1 - b;
-                s_off[lane] = V4<T>{(T)0, (T)0, (T)0, (T)(1.475 * hB)};
+                cnt = n;
+                idx = -1 - b;
+                o.w = (T)(1.475 * hB);
             } else if (e < 1 + nw) {
                 const int A = wbox[w0 + e - 1];
-                int sh[3];
-                decode_shift(wsh[w0 + e - 1], sh);
-                const int4 Ap = bpos[A];
-                double off[3];
-                centre_offset(B, Ap, sh, off);
-                s_idx[lane] = A;
-                s_off[lane] = V4<T>{(T)off[0], (T)off[1], (T)off[2], (T)(0.525 * exp2i(Ap.w))};
+                if (!w_direct(A)) {
+                    int sh[3];
+                    decode_shift(wsh[w0 + e - 1], sh);
+                    const int4 Ap = bpos[A];
+                    double off[3];
+                    centre_offset(B, Ap, sh, off);
+                    cnt = n;
+                    idx = A;
+                    o = V4<T>{(T)off[0], (T)off[1], (T)off[2], (T)(0.525 * exp2i(Ap.w))};
+                }
             }
-            __syncwarp();
-            run(std::integral_constant<int, kFar>{}, std::false_type{}, ne * n, [&](int f, V4<T> &y, T(&d)[R * K]) {
-                const int ei = f / n, j = f - ei * n, idx = s_idx[ei];
-                const V4<T> o = s_off[ei];
-                const T *phi = idx < 0 ? dn + ((long long)(-1 - idx) * nrhs + rhs0) * kn
-                                       : up + ((long long)idx * nrhs + rhs0) * kn;
-                y.x = o.w * g[3 * j] - o.x;
-                y.y = o.w * g[3 * j + 1] - o.y;
-                y.z = o.w * g[3 * j + 2] - o.z;
+            const int F = publish(cnt, idx, o);
+            run(std::integral_constant<int, kFar>{}, std::false_type{}, F, [&](int f, V4<T> &y, T(&d)[R * K]) {
+                const int ei = nw ? entry_of(f) : 0, j = f - s_start[ei], id = s_idx[ei];  // one entry: no search
+                const V4<T> oe = s_off[ei];
+                const T *phi = id < 0 ? dn + ((long long)(-1 - id) * nrhs + rhs0) * kn
+                                      : up + ((long long)id * nrhs + rhs0) * kn;
+                y.x = oe.w * g[3 * j] - oe.x;
+                y.y = oe.w * g[3 * j + 1] - oe.y;
+                y.z = oe.w * g[3 * j + 2] - oe.z;
 #pragma unroll
                 for (int r = 0; r < R; r++)
 #pragma unroll
@@ -1131,7 +1201,8 @@ __global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT>())) k_leaf(
         }
 
         // U list: B itself (coincident points drop out), then the adjacent
-        // leaves and images; entries of a chunk are laid end to end
+        // leaves and images, read relative to their leaf's centre (offset
+        // c_B - c_A - p); the entries of a chunk are laid end to end
         auto u_list = [&](auto mode_tag, bool self) {
             for (int c0 = 0; c0 < nu; c0 += 32) {
                 const int e = c0 + lane;
@@ -1151,29 +1222,13 @@ __global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT>())) k_leaf(
                         o = V4<T>{(T)off[0], (T)off[1], (T)off[2], (T)0};
                     }
                 }
-                int inc = cnt;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, inc, d);
-                    if (lane >= d) inc += v;
-                }
-                const int F = __shfl_sync(0xffffffffu, inc, 31);
-                __syncwarp();
-                s_start[lane] = inc - cnt;
-                s_idx[lane] = i0;
-                s_off[lane] = o;
-                if (lane == 31) s_start[32] = inc;
-                __syncwarp();
+                const int F = publish(cnt, i0, o);
                 run(mode_tag, std::true_type{}, F, [&](int f, V4<T> &y, T(&d)[R * KS]) {
-                    int ei = 0;  // the last entry starting at or before f
-#pragma unroll
-                    for (int st = 16; st; st >>= 1)
-                        if (s_start[ei + st] <= f) ei += st;
-                    const int i = s_idx[ei] + f - s_start[ei];
-                    const V4<T> o = s_off[ei], v = yrel[i];
-                    y.x = v.x - o.x;
-                    y.y = v.y - o.y;
-                    y.z = v.z - o.z;
+                    const int ei = entry_of(f), i = s_idx[ei] + f - s_start[ei];
+                    const V4<T> oe = s_off[ei], v = yrel[i];
+                    y.x = v.x - oe.x;
+                    y.y = v.y - oe.y;
+                    y.z = v.z - oe.z;
 #pragma unroll
                     for (int r = 0; r < R; r++)
 #pragma unroll
@@ -1184,6 +1239,49 @@ __global__ void __launch_bounds__(32, (leaf_min_blocks<T, R, KT>())) k_leaf(
         };
         u_list(std::integral_constant<int, kSelf>{}, true);
         u_list(std::integral_constant<int, kNear>{}, false);
+
+        // the W boxes and X lists summed from their sources, read from their
+        // binary64 coordinates (a W box may span several leaves) moved by the
+        // image shift p into B's frame (a pass of its own, so that the U
+        // pass's code stays lean)
+        for (int c0 = 0; c0 < nw + nx; c0 += 32) {
+            const int e = c0 + lane;
+            int cnt = 0, i0 = 0;
+            V4<T> o{(T)0, (T)0, (T)0, (T)0};
+            int xi = -1;
+            if (e < nw) {
+                if (w_direct(wbox[w0 + e])) xi = -2 - (w0 + e);  // a W entry
+            } else if (e < nw + nx) {  // an X-list entry of B or of an ancestor
+                const int k = e - nw;
+                int a = 0;
+                while (a + 1 < nxa && s_xpre[a + 1] <= k) a++;
+                xi = s_xbeg[a] + k - s_xpre[a];
+            }
+            if (xi != -1) {
+                const bool isw = xi < -1;
+                const int idx = isw ? -2 - xi : xi, A = isw ? wbox[idx] : xbox[idx];
+                const int2 rg = srange[A];
+                cnt = rg.y - rg.x;
+                i0 = rg.x;
+                int sh[3];
+                decode_shift(isw ? wsh[idx] : xsh[idx], sh);
+                o = V4<T>{(T)sh[0], (T)sh[1], (T)sh[2], (T)0};
+            }
+            const int F = publish(cnt, i0, o);
+            run(std::integral_constant<int, kNear>{}, std::true_type{}, F, [&](int f, V4<T> &y, T(&d)[R * KS]) {
+                const int ei = entry_of(f), i = s_idx[ei] + f - s_start[ei];
+                const V4<T> oe = s_off[ei];
+                const double h = exp2i(B.w);
+                y.x = (T)((xsrc[3 * (long long)i] - (B.x + 0.5) * h) + (double)oe.x);
+                y.y = (T)((xsrc[3 * (long long)i + 1] - (B.y + 0.5) * h) + (double)oe.y);
+                y.z = (T)((xsrc[3 * (long long)i + 2] - (B.z + 0.5) * h) + (double)oe.z);
+#pragma unroll
+                for (int r = 0; r < R; r++)
+#pragma unroll
+                    for (int a = 0; a < KS; a++)
+                        d[r * KS + a] = r < nv ? dens[(long long)i * nrhs * KS + (rhs0 + r) * KS + a] : (T)0;
+            });
+        }
 
         // the G groups' sums of each target, added in binary64
 #pragma unroll
@@ -1390,7 +1488,8 @@ static void downward_t(Plan &P, cudaStream_t s) {
             auto go = [&](auto rt) {
                 constexpr int R = decltype(rt)::value;
                 count_launch(), k_s2l<T, K, R, KS><<<P.n_xboxes, KS_T, 0, s>>>(
-                    P.xboxes.p, P.tree.bpos.p, P.tree.srange.p, P.tree.x_ptr.p, P.tree.x_box.p, P.tree.x_sh.p, yr,
+                    P.xboxes.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.x_ptr.p, P.tree.x_box.p,
+                    P.tree.x_sh.p, yr,
                     B::dens(P), nr, r, B::g(P).p, P.n, B::chk(P).p);
             };
             if (nr - r == 1) go(std::integral_constant<int, 1>{});
@@ -1452,7 +1551,7 @@ static void leaves_t(Plan &P, cudaStream_t s) {
     // the outputs a target carries); up to 4 density vectors per launch
     auto launch = [&](auto r_tag, int r0) {
         constexpr int R = decltype(r_tag)::value, W = R * KT * (int)(sizeof(T) / 4);
-        constexpr int QMAX = W <= 3 ? 4 : (W <= 6 ? 2 : 1);  // registers: three sums per output
+        constexpr int QMAX = W <= 1 ? 4 : (W <= 3 ? 3 : (W <= 6 ? 2 : 1));  // registers: three sums per output
         // source groups: four for Laplace (a cheap pair: one staged source serving
         // more targets pays), two for Stokes (measured faster than four: a leaf
         // of up to 64 targets stays in one block); targets per chunk
@@ -1460,8 +1559,9 @@ static void leaves_t(Plan &P, cudaStream_t s) {
         const dim3 grid(P.n_leaves_trg, std::max(1, (P.leaf_max + CH - 1) / CH));
         count_launch(), k_leaf<T, K, R, QMAX, G, KT, KS><<<grid, 32, 0, s>>>(
                 P.leaves_trg.p, P.tree.bpos.p, P.tree.srange.p, P.tree.trange.p, P.tree.u_ptr.p, P.tree.u_box.p,
-                P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, yr, xr, B::dens(P), B::up(P).p,
-                B::dn(P).p, nr, r0, B::g(P).p, P.n, P.pot_s.p);
+                P.tree.u_sh.p, P.tree.w_ptr.p, P.tree.w_box.p, P.tree.w_sh.p, P.tree.parent.p, P.tree.x_ptr.p,
+                P.tree.x_box.p, P.tree.x_sh.p, yr, xr, B::dens(P), P.xs.p,
+                B::up(P).p, B::dn(P).p, nr, r0, B::g(P).p, P.n, P.pot_s.p);
     };
     if (P.n_leaves_trg)
         for (int r0 = 0; r0 < nr; r0 += 4) {
