@@ -133,6 +133,8 @@ struct Plan {
     bool stage_ev_live = false;
     char *down_h = nullptr;                     // pinned buffer for the tree read back each evaluation
     size_t down_cap = 0;
+    const int4 *h_bpos = nullptr;               // views into down_h of this evaluation's boxes (null
+    const int2 *h_trange = nullptr;             // until the tasks are built)
     DBuf<double> far64;                         // roots' downward equivalent densities (step d)
     DBuf<long long> soff, toff;                 // [nprob+1] CSR offsets of their points
     bool same_offsets = true;                   // soff == toff element by element

@@ -942,7 +942,7 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         const int start = (int)gbox.size();
         for (int i = 0; i < task.class_count[c]; i++) {
             const int b = task.h_boxes[b0 + i];
-            const int l = (int)(std::upper_bound(lb.begin(), lb.end(), b) - lb.begin()) - 1;
+            const int l = P.h_bpos ? P.h_bpos[b].w : (int)(std::upper_bound(lb.begin(), lb.end(), b) - lb.begin()) - 1;
             if (!is_grid[l]) gbox.push_back(b);
         }
         b0 += task.class_count[c];
@@ -960,11 +960,22 @@ bool m2l_tc_run(Plan &P, cudaStream_t s) {
         const int bxn = h / g.bx, byn = h / g.by, bzn = h / g.bz;
         if (g.map_off >= 0) {
             const int cnt = lb[g.level + 1] - lb[g.level];
-            std::vector<int4> bp(cnt);
-            std::vector<int2> tr(cnt);
-            PK_CUDA(cudaMemcpyAsync(bp.data(), P.tree.bpos.p + lb[g.level], sizeof(int4) * cnt, cudaMemcpyDeviceToHost, s));
-            PK_CUDA(cudaMemcpyAsync(tr.data(), P.tree.trange.p + lb[g.level], sizeof(int2) * cnt, cudaMemcpyDeviceToHost, s));
-            PK_CUDA(cudaStreamSynchronize(s));
+            // the level's boxes: from the tree read back for the tasks, else read here
+            std::vector<int4> bpv;
+            std::vector<int2> trv;
+            const int4 *bp = P.h_bpos ? P.h_bpos + lb[g.level] : nullptr;
+            const int2 *tr = P.h_trange ? P.h_trange + lb[g.level] : nullptr;
+            if (!bp || !tr) {
+                bpv.resize(cnt);
+                trv.resize(cnt);
+                PK_CUDA(cudaMemcpyAsync(bpv.data(), P.tree.bpos.p + lb[g.level], sizeof(int4) * cnt,
+                                        cudaMemcpyDeviceToHost, s));
+                PK_CUDA(cudaMemcpyAsync(trv.data(), P.tree.trange.p + lb[g.level], sizeof(int2) * cnt,
+                                        cudaMemcpyDeviceToHost, s));
+                PK_CUDA(cudaStreamSynchronize(s));
+                bp = bpv.data();
+                tr = trv.data();
+            }
             occ.assign((size_t)8 * bxn * byn * bzn, 0);
             for (int i = 0; i < cnt; i++) {
                 if (tr[i].y <= tr[i].x) continue;

@@ -471,19 +471,28 @@ void build_tasks(Plan &P, cudaStream_t s) {
     H.sr = (const int2 *)(dh + b_sr);
     H.tr = (const int2 *)(dh + b_tr);
     const int *xptr = (const int *)(dh + b_x);
+    P.h_bpos = H.bpos;
+    P.h_trange = H.tr;
     Uploads up;
+    up.pack.reserve((size_t)nb * 48 + 4096);  // the box lists and tiles below, without regrowth
     const int nr = P.nrhs;
-    std::vector<char> isleaf(nb);
-    for (int b = 0; b < nb; b++) isleaf[b] = H.leaf(b);
+    // per box, in one parallel pass over the read-back tree: bit 0 leaf, bit 1
+    // sources, bit 2 targets, bits 3-5 the octant class
+    std::vector<unsigned char> fl(nb);
+#pragma omp parallel for schedule(static) if (nb > 65536)
+    for (int b = 0; b < nb; b++)
+        fl[b] = (unsigned char)((H.leaf(b) ? 1 : 0) | (H.has_src(b) ? 2 : 0) | (H.has_trg(b) ? 4 : 0) | H.octant(b) << 3);
+    constexpr unsigned char kLeaf = 1, kSrc = 2, kTrg = 4;
     std::vector<int> leaves_src, leaves_trg;
     leaves_src.reserve(nb);
     leaves_trg.reserve(nb);
     t.nleaf = 0;
     for (int b = 0; b < nb; b++) {
-        if (!isleaf[b]) continue;
+        const unsigned char f = fl[b];
+        if (!(f & kLeaf)) continue;
         t.nleaf++;
-        if (H.has_src(b)) leaves_src.push_back(b);
-        if (H.has_trg(b)) leaves_trg.push_back(b);
+        if (f & kSrc) leaves_src.push_back(b);
+        if (f & kTrg) leaves_trg.push_back(b);
     }
     P.n_leaves_src = (int)leaves_src.size();
     P.n_leaves_trg = (int)leaves_trg.size();
@@ -492,7 +501,7 @@ void build_tasks(Plan &P, cudaStream_t s) {
     // X-list boxes (with targets and a non-empty X list)
     std::vector<int> xb;
     for (int b = 0; b < nb; b++)
-        if (xptr[b + 1] > xptr[b] && H.has_trg(b)) xb.push_back(b);
+        if (xptr[b + 1] > xptr[b] && (fl[b] & kTrg)) xb.push_back(b);
     P.n_xboxes = (int)xb.size();
     upload_list(P.xboxes, xb, up);
 
@@ -509,18 +518,19 @@ void build_tasks(Plan &P, cudaStream_t s) {
     for (int l = 0; l < depth; l++) {
         std::vector<int> v;
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
-            if (!isleaf[b] && H.has_src(b)) v.push_back(b);
+            if ((fl[b] & (kLeaf | kSrc)) == kSrc) v.push_back(b);
         make_task(P.t_m2m[l], {v}, 8, ops8, nr, up, bm, [&](int b, int sl) { return H.child[8 * (size_t)b + sl]; });
     }
     // M2L: boxes of level >= 1 with targets, by octant class
     std::vector<std::vector<int>> byc(8);
     for (int b = P.nprob; b < nb; b++)  // boxes 0..nprob-1 are the problems' roots
-        if (H.has_trg(b)) byc[H.octant(b)].push_back(b);
+        if (fl[b] & kTrg) byc[fl[b] >> 3].push_back(b);
     make_task(P.t_m2l, byc, kVSlots, P.h_class_slot_op, nr, up, bm);
     // DC2E over boxes with targets (roots separately in binary64 for MIXED)
     std::vector<int> dc;
+    dc.reserve(nb);
     for (int b = (mixed ? P.nprob : 0); b < nb; b++)
-        if (H.has_trg(b)) dc.push_back(b);
+        if (fl[b] & kTrg) dc.push_back(b);
     make_task(P.t_dc2e, {dc}, 1, {0}, nr, up, bm, self);
     // MIXED with a shared M2L basis: the X-list part of the check potential is solved separately
     if (P.basis) make_task(P.t_dcx, {xb}, 1, {0}, nr, up, bm, self);
@@ -529,7 +539,7 @@ void build_tasks(Plan &P, cudaStream_t s) {
     for (int l = 1; l < depth; l++) {
         std::vector<std::vector<int>> bc(8);
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
-            if (H.has_trg(b)) bc[H.octant(b)].push_back(b);
+            if (fl[b] & kTrg) bc[fl[b] >> 3].push_back(b);
         make_task(P.t_l2l[l], bc, 1, ops8, nr, up, bm, [&](int b, int) { return H.parent[b]; });
     }
     up.flush(P, s);
