@@ -68,6 +68,9 @@ struct TrState {
     float *amax = nullptr;
     int *err = nullptr;
     int *err_host = nullptr;
+    float *part = nullptr;     // slot-group partial sums of small launches (k_trans_reduce)
+    size_t part_cap = 0;
+    int sms = 0;
 };
 
 namespace {
@@ -86,6 +89,8 @@ struct TrArgs {
     const float *amax;              // max |source| over the rows the task reads
     int mrows, msplit, KM, KK, nrhs, kexp, drain;
     int *err;
+    float *part;                    // non-null: slot group blockIdx.y of nsplit writes its partial sum (as dst)
+    int nsplit;
 };
 
 // Tiles marked regular (tile.w = 1: source rows src0 + i; 8: src0 + 8 i, with
@@ -139,7 +144,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int n = tid; n < TC_N; n += TC_THREADS) {
         if (n < nr) {
             const int row = row0 + n, tb = row / a.nrhs, rhs = row % a.nrhs, box = a.tboxes[tb];
-            drow[n] = (long long)box * a.nrhs + rhs;
+            // a split launch writes its slot group's partial sums (the host then
+            // passes the partial buffer as dst, msplit = mrows, beta = 0)
+            drow[n] = a.part ? ((long long)blockIdx.y * (gridDim.x / mtiles) + blockIdx.x / mtiles) * TC_N + n
+                             : (long long)box * a.nrhs + rhs;
             sbox[n] = box;
         } else {
             drow[n] = -1;
@@ -157,7 +165,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int any = 0;
             for (int n = 0; n < nr && !any; n++)
                 any = a.slot_table ? a.slot_table[(long long)sbox[n] * a.slot_stride + s] >= 0 : 1;
-            if (any) act[c++] = s;
+            if (any && (!a.part || s % a.nsplit == (int)blockIdx.y)) act[c++] = s;
         }
         *nact_s = c;
     }
@@ -359,6 +367,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// The slot groups' partial sums of a split launch, added in group order (the
+// result does not depend on scheduling): one thread per (tile, column, output
+// component), components fastest; dst (components < msplit, beta: added) and
+// dst2 (the rest) as in the epilogue of k_trans_tc.
+__global__ void k_trans_reduce(const float *__restrict__ part, int nsplit, int ntl, const int4 *__restrict__ tiles,
+                               const int *__restrict__ tboxes, int nrhs, int mrows, int msplit, float *dst,
+                               float *dst2, int beta) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)ntl * TC_N * mrows) return;
+    const int k = (int)(i % mrows);
+    const long long tcol = i / mrows;
+    const int c = (int)(tcol % TC_N), ti = (int)(tcol / TC_N);
+    const int4 tile = tiles[ti];
+    if (c >= tile.z) return;
+    const int row = tile.y + c, box = tboxes[row / nrhs];
+    const long long d = (long long)box * nrhs + row % nrhs;
+    float v = 0.f;
+    for (int g = 0; g < nsplit; g++) v += part[(((size_t)g * ntl + ti) * TC_N + c) * mrows + k];
+    if (k < msplit) {
+        float *o = dst + d * msplit + k;
+        *o = beta ? *o + v : v;
+    } else {
+        dst2[d * (mrows - msplit) + (k - msplit)] = v;
+    }
+}
+
 // op[o][i][j] (M x K each) * 2^kexp split into fp16 hi/lo, padded to KM x KK: out[h][o][i][j]
 __global__ void k_op_split(const double *__restrict__ op, int nops, int M, int K, int KM, int KK, int kexp,
                            __half *__restrict__ out) {
@@ -500,6 +534,7 @@ void trans_tc_release(Plan &P) {
     cudaFree(t->phi);
     cudaFree(t->amax);
     cudaFree(t->err);
+    cudaFree(t->part);
     cudaFreeHost(t->err_host);
     delete t;
     P.tr = nullptr;
@@ -645,8 +680,37 @@ void trans_tc_gemm(Plan &P, int set, const Task &task, const int *slot_table, in
     CUtensorMap b1[2], b8[2];
     phi_maps(hi, t->phi_rows, KK, b1[0], b8[0]);  // rows as k_task_split writes them: stride KK
     phi_maps(lo, t->phi_rows, KK, b1[1], b8[1]);
-    count_launch(), k_trans_tc<3><<<task.ntiles * mtiles, TC_THREADS, tc_smem(3), s>>>(o.tmap[0], o.tmap[1], b1[0],
-                                                                                       b1[1], b8[0], b8[1], a);
+    // A launch of few CTAs (the coarse levels of M2M) streams its long K range
+    // on a handful of SMs and waits on TMA latency: its slots are split over
+    // up to sms / CTAs groups, each CTA writing a partial sum, added after.
+    // The group count follows from the task's boxes, not its rows, so that a
+    // density vector is summed the same way whatever number of vectors rides along.
+    const int ctas = task.ntiles * mtiles;
+    if (!t->sms) PK_CUDA(cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, P.device));
+    const int ctas1 = (nbt + TC_N - 1) / TC_N * mtiles;  // the CTAs of the task with one vector
+    const int nsplit = task.nslots > 1 ? std::min(task.nslots, std::max(1, t->sms / ctas1)) : 1;
+    if (nsplit > 1) {
+        const size_t need = (size_t)nsplit * task.ntiles * TC_N * o.M;
+        if (need > t->part_cap) {
+            cudaFree(t->part);
+            t->part = nullptr;
+            t->part_cap = need;
+            PK_CUDA(cudaMalloc(&t->part, need * sizeof(float)));
+        }
+        a.part = t->part;
+        a.nsplit = nsplit;
+        a.dst = t->part;
+        a.dst2 = nullptr;
+        a.msplit = o.M;
+        a.beta = 0;
+    }
+    count_launch(), k_trans_tc<3><<<dim3(ctas, nsplit), TC_THREADS, tc_smem(3), s>>>(o.tmap[0], o.tmap[1], b1[0],
+                                                                                     b1[1], b8[0], b8[1], a);
+    if (nsplit > 1) {
+        const long long n = (long long)task.ntiles * TC_N * o.M;
+        count_launch(), k_trans_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+            t->part, nsplit, task.ntiles, task.tiles.p, task.boxes.p, nr, o.M, o.msplit, dst, dst2, beta);
+    }
     PK_CUDA(cudaGetLastError());
 }
 
