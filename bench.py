@@ -27,8 +27,15 @@ binary64 root operator).  A step is one evaluation: Morton sort, octree,
 lists, upward pass, root periodic operator, M2L, downward pass, leaves.
 Targets/s counts targets x density vectors.
 
-Prints one JSON line (rank 0).  `--impl reference` times the FP64 oracle
-(Ewald sum) instead, on a bounded sample of the same workload's targets.
+Prints one JSON line (rank 0): throughput, the device-timed step and the
+end-to-end one through the host entry point, the M2L roofline, accuracy
+against the FP64 oracle on sampled targets, the FP64 path beside the MIXED
+one, and two CPU baselines: the oracle on the sampled targets
+(``cpu_baseline``) and the plain binary64 KIFMM of ``baseline/cpu_kifmm`` on a
+2^17-point instance of the workload with the library timed on the same
+instance (``cpu_kifmm``; ``--cpu-kifmm-n 0`` skips it).  `--impl reference`
+times the FP64 oracle (Ewald sum) instead, on a bounded sample of the same
+workload's targets.
 Multi-GPU (torchrun): each rank evaluates its own independent problem of the
 same size (independent problems shard with no data-path collective); the
 value is the sum over ranks, the time the max over ranks.
