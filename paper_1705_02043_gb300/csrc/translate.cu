@@ -479,7 +479,7 @@ void build_tasks(Plan &P, cudaStream_t s) {
     // per box, in one parallel pass over the read-back tree: bit 0 leaf, bit 1
     // sources, bit 2 targets, bits 3-5 the octant class
     std::vector<unsigned char> fl(nb);
-#pragma omp parallel for schedule(static) if (nb > 65536)
+#pragma omp parallel for schedule(static) if (nb > 8192)
     for (int b = 0; b < nb; b++)
         fl[b] = (unsigned char)((H.leaf(b) ? 1 : 0) | (H.has_src(b) ? 2 : 0) | (H.has_trg(b) ? 4 : 0) | H.octant(b) << 3);
     constexpr unsigned char kLeaf = 1, kSrc = 2, kTrg = 4;
