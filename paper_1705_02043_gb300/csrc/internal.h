@@ -160,6 +160,7 @@ struct Plan {
     DBuf<double> xn;                            // normalised coordinates before the gather
     DBuf<int> lcnt;                             // [3][nbox] U / W / X list lengths
     DBuf<int> scan_tmp;                         // prefix-sum scratch
+    bool leaves_up = false;                     // the upward pass's leaf level is enqueued already
     bool same_points = false;                   // the targets are the sources (one sort)
     DBuf<unsigned long long> lpairs;            // [2] P2P pairs, V entries
     DBuf<int2> csr, ctr;                        // [nlevel boxes][8] child ranges

@@ -440,7 +440,10 @@ static void upload_list(DBuf<int> &d, const std::vector<int> &v, Uploads &up) {
     up.add(d.p, v.data(), v.size());
 }
 
+void upward_leaves(Plan &P, cudaStream_t s);
+
 void build_tasks(Plan &P, cudaStream_t s) {
+    P.leaves_up = false;
     Tree &t = P.tree;
     int nb = t.nbox;
     // the tree comes back through one pinned buffer (pageable copies are staged
@@ -504,12 +507,18 @@ void build_tasks(Plan &P, cudaStream_t s) {
         if (xptr[b + 1] > xptr[b] && (fl[b] & kTrg)) xb.push_back(b);
     P.n_xboxes = (int)xb.size();
     upload_list(P.xboxes, xb, up);
+    // the leaf level of the upward pass runs on the device while the host
+    // groups the other tasks (the second flush waits for these copies only)
+    up.flush(P, s);
+    upward_leaves(P, s);
+    Uploads up2;
+    up2.pack.reserve((size_t)nb * 40 + 4096);
 
     bool mixed = P.precision == PKIFMM_MIXED;
     const int bm = mixed ? GemmCfg<float>::BM : GemmCfg<double>::BM;
     // UC2E over leaves with sources
     const auto self = [](int b, int) { return b; };
-    make_task(P.t_uc2e, {leaves_src}, 1, {0}, nr, up, bm, self);
+    make_task(P.t_uc2e, {leaves_src}, 1, {0}, nr, up2, bm, self);
     // M2M per level: non-leaf boxes with sources
     int depth = (int)t.lvl_begin.size() - 1;
     P.t_m2m.resize(depth);
@@ -519,30 +528,30 @@ void build_tasks(Plan &P, cudaStream_t s) {
         std::vector<int> v;
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
             if ((fl[b] & (kLeaf | kSrc)) == kSrc) v.push_back(b);
-        make_task(P.t_m2m[l], {v}, 8, ops8, nr, up, bm, [&](int b, int sl) { return H.child[8 * (size_t)b + sl]; });
+        make_task(P.t_m2m[l], {v}, 8, ops8, nr, up2, bm, [&](int b, int sl) { return H.child[8 * (size_t)b + sl]; });
     }
     // M2L: boxes of level >= 1 with targets, by octant class
     std::vector<std::vector<int>> byc(8);
     for (int b = P.nprob; b < nb; b++)  // boxes 0..nprob-1 are the problems' roots
         if (fl[b] & kTrg) byc[fl[b] >> 3].push_back(b);
-    make_task(P.t_m2l, byc, kVSlots, P.h_class_slot_op, nr, up, bm);
+    make_task(P.t_m2l, byc, kVSlots, P.h_class_slot_op, nr, up2, bm);
     // DC2E over boxes with targets (roots separately in binary64 for MIXED)
     std::vector<int> dc;
     dc.reserve(nb);
     for (int b = (mixed ? P.nprob : 0); b < nb; b++)
         if (fl[b] & kTrg) dc.push_back(b);
-    make_task(P.t_dc2e, {dc}, 1, {0}, nr, up, bm, self);
+    make_task(P.t_dc2e, {dc}, 1, {0}, nr, up2, bm, self);
     // MIXED with a shared M2L basis: the X-list part of the check potential is solved separately
-    if (P.basis) make_task(P.t_dcx, {xb}, 1, {0}, nr, up, bm, self);
+    if (P.basis) make_task(P.t_dcx, {xb}, 1, {0}, nr, up2, bm, self);
     // L2L per level >= 1, by octant class
     P.t_l2l.resize(depth);
     for (int l = 1; l < depth; l++) {
         std::vector<std::vector<int>> bc(8);
         for (int b = t.lvl_begin[l]; b < t.lvl_begin[l + 1]; b++)
             if (fl[b] & kTrg) bc[fl[b] >> 3].push_back(b);
-        make_task(P.t_l2l[l], bc, 1, ops8, nr, up, bm, [&](int b, int) { return H.parent[b]; });
+        make_task(P.t_l2l[l], bc, 1, ops8, nr, up2, bm, [&](int b, int) { return H.parent[b]; });
     }
-    up.flush(P, s);
+    up2.flush(P, s);
 }
 
 // Large binary32 slot GEMM: a 128 x 128 output tile per CTA, 16 K per step,
@@ -1387,12 +1396,14 @@ static void prepare_points(Plan &P, cudaStream_t s) {
     }
 }
 
+// The leaf level of the upward pass: leaf-relative coordinates, densities in
+// the arithmetic of the path, S2M check values.  It needs only the leaf lists,
+// so the task grouping enqueues it before it builds the other tasks on the host.
 template <typename T, int K, int KS = K>
-static void upward_t(Plan &P, cudaStream_t s) {
+static void upward_leaves_t(Plan &P, cudaStream_t s) {
     using B = Bufs<T>;
     prepare_points<T>(P, s);
-    const int kn = P.kn, nr = P.nrhs;
-    const long long kn2 = (long long)kn * kn;
+    const int nr = P.nrhs;
     auto *yr = reinterpret_cast<const V4<T> *>(B::yrel(P).p);
     if (P.n_leaves_src)
         for (int r = 0; r < nr; r += 4) {  // up to 4 density vectors per pass
@@ -1406,6 +1417,28 @@ static void upward_t(Plan &P, cudaStream_t s) {
             else if (nr - r == 2) go(std::integral_constant<int, 2>{});
             else go(std::integral_constant<int, 4>{});
         }
+    P.leaves_up = true;
+}
+
+void upward_leaves(Plan &P, cudaStream_t s) {
+    if (P.precision == PKIFMM_FP64) {
+        if (P.ks == 3 && P.k == 1) upward_leaves_t<double, 1, 3>(P, s);
+        else if (P.k == 1) upward_leaves_t<double, 1>(P, s);
+        else upward_leaves_t<double, 3>(P, s);
+    } else {
+        if (P.ks == 3 && P.k == 1) upward_leaves_t<float, 1, 3>(P, s);
+        else if (P.k == 1) upward_leaves_t<float, 1>(P, s);
+        else upward_leaves_t<float, 3>(P, s);
+    }
+}
+
+template <typename T, int K, int KS = K>
+static void upward_t(Plan &P, cudaStream_t s) {
+    using B = Bufs<T>;
+    if (!P.leaves_up) upward_leaves_t<T, K, KS>(P, s);
+    P.leaves_up = false;
+    const int kn = P.kn, nr = P.nrhs;
+    const long long kn2 = (long long)kn * kn;
     if constexpr (std::is_same<T, float>::value) {
         if (P.tr) {  // tensor cores: tmp = S+ (U^T q~u), up = V tmp, then M2M level by level
             trans_tc_gemm(P, 0, P.t_uc2e, nullptr, 1, P.chk32.p, P.tmp32.p, 0, s);
