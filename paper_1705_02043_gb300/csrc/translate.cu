@@ -990,17 +990,19 @@ __global__ void __launch_bounds__(KS_T) k_s2l(const int *__restrict__ boxes, con
 
 // Kernel sums at a target leaf B for up to R density vectors at once (the
 // geometry and 1/r are shared): L2T from B's downward equivalent surface,
-// M2T from the upward equivalent surfaces of W(B), and the U-list direct sums
-// with the periodic images (Sec. 2.2, the near field of Eq. 3).
+// M2T from the upward equivalent surfaces of W(B), the U-list direct sums with
+// the periodic images (the near field of Sec. 2.2), and the direct sums that
+// replace a surface where that is cheaper: W boxes with at most n sources, and
+// the X lists of B and its ancestors holding at most n targets (k_s2l skips
+// those boxes).
 // One warp per block; blockIdx.y takes chunks of at most (32 / G) QMAX
 // targets.  The warp's G groups of lanes split each staged tile of LT sources
 // (slot j to group j mod G) over the same targets, Q targets per lane in
 // registers, so one shared load of a source serves Q pairs; the groups' sums
-// are added at the end.  The
-// sources of every box of a list are staged already moved into B's frame
-// (y + p - c_B), so a tile runs across box boundaries, and the global loads of
-// the next tile are in flight while the current one is summed.  Each tile's
-// sum joins the running total with Kahan compensation.
+// are added at the end.  The sources of every box of a list are staged already
+// moved into B's frame (y + p - c_B), so a tile runs across box boundaries, and
+// the global loads of the next tile are in flight while the current one is
+// summed.  Each tile's sum joins the running total with Kahan compensation.
 
 // blocks per SM the register budget is sized for: 24 (85 registers a thread)
 // for one binary32 sum a target from one-component sources, 16 (128 registers)
